@@ -1,0 +1,271 @@
+#!/usr/bin/env python3
+"""Benchmark: SpMV GFLOP/s and fraction of the HBM roofline, compressed
+(pattern format, uint8 value codes + 5-bit stencil-pattern numbers, FAST
+order) vs plain ELL, on the 192^3 HPCG matrix (7,077,888 rows, 189,119,224
+nonzeros), x ~ U[-1,1) from seed 1, on one GB300.
+
+A step is one y = A x with the compressed matrix, inputs resident in HBM.
+GF/s counts 2 flops per stored nonzero (Sec. IV-B of arXiv:1612.00530).
+The matrix, x and y together (311 MB) exceed the 129 MB L2, so no flush is
+needed between steps.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas; the method has no exchange step on one grid); the JSON line
+reports the work of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = NZ = 192
+X_SEED = 1
+METRIC = "SpMV GFLOP/s + % HBM roofline, compressed vs plain ELL, 192^3 HPCG, 1 GB300"
+WORKLOAD = "hpcg_192^3_x_seed1_compressed_pattern_uint8codes_5bit_patterns_vs_ell"
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float = 12.0) -> dict:
+    """The oracle's CSR SpMV (single thread, as written) on this host."""
+    import oracle
+    import spmv_inputs
+
+    rowptr, col, val = oracle.hpcg_csr(NX, NY, NZ)
+    x = spmv_inputs.uniform_vector(NX * NY * NZ, seed=X_SEED)
+    nnz = int(rowptr[-1])
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.spmv(rowptr, col, val, x)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": 2.0 * nnz / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full 192^3 CSR SpMVs (x seed 1), single thread, {reps * dt:.1f} s"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, on the host cores, on a bounded sample."""
+    if rank != 0:
+        return
+    cb = cpu_baseline(seconds=max(10.0, min(60.0, 0.4 * args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 2.0 * 189119224 / cb["value"] / 1e6,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": NX * NY * NZ, "nnz": 189119224},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world, rank, local = dist_setup()
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        barrier(world)
+        return
+
+    import paper_1612_00530_gb300 as P
+    import spmv_inputs
+    from paper_1612_00530_gb300 import build as lib_build
+
+    lib_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    A = P.spmv_build("hpcg", NX, NY, NZ)
+    C = P.spmv_compress(A, format="pattern", order="fast")
+    info_c, info_a = P.spmv_info(C), P.spmv_info(A)
+    n, nnz = info_c["n"], info_c["nnz"]
+    x_np = spmv_inputs.uniform_vector(n, seed=X_SEED)
+    x = torch.from_numpy(x_np).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def timed(M, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        ev0.record(stream)
+        for _ in range(steps):
+            P.spmv_apply(M, x, y, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return ev0.elapsed_time(ev1) / steps  # ms
+
+    # plain ELL baseline and COLUMN-order compressed (bit-exact mode)
+    for _ in range(args.warmup):
+        P.spmv_apply(A, x, y, stream)
+    ell_ms = max_over_ranks(timed(A, max(20, min(args.steps, 400))), world)
+    Ccol = P.spmv_compress(A, format="pattern", order="column")
+    for _ in range(args.warmup):
+        P.spmv_apply(Ccol, x, y, stream)
+    col_ms = max_over_ranks(timed(Ccol, max(20, min(args.steps, 400))), world)
+    del Ccol
+
+    # headline: compressed, FAST order
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_warm = time.perf_counter()
+    warm = 0
+    while warm < args.warmup or time.perf_counter() - t_warm < 0.8:
+        P.spmv_apply(C, x, y, stream)
+        warm += 1
+        if warm % 200 == 0:
+            torch.cuda.synchronize()
+    ms = max_over_ranks(timed(C, args.steps), world)
+    clocks = sampler.stop()
+    assert P.spmv_device_error(C) == 0
+
+    # end to end through the host-buffer entry point: x H2D, SpMV, y D2H
+    hx = torch.from_numpy(x_np).pin_memory()
+    hy = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 300))
+    for _ in range(3):
+        P.spmv_apply_host(C, hx, hy)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.spmv_apply_host(C, hx, hy)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+
+    flops = 2.0 * nnz
+    value = world * flops / (ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    alg_bytes = nnz * 1.0 + n * 5.0 / 8.0 + 16.0 * n      # codes + pattern + x + y
+    ell_alg_bytes = nnz * 12.0 + 16.0 * n                  # value + column + x + y
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64-in/out, int64 fixed-point accumulate", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows": n, "nnz": nnz, "format": "pattern", "order": "fast",
+                   "record_bytes_per_row": info_c["record_bytes"],
+                   "l2": f"inputs {(info_c['format_bytes'] + 16 * n) / 1e6:.0f} MB > 129 MB L2, no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "xmax pre-pass + pattern_fast decode (one spmv_apply)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peaks["source"]},
+        "ell": {"gflops": world * flops / (ell_ms * 1e-3) / 1e9, "ms_per_step": ell_ms,
+                "achieved_gbs": ell_alg_bytes / (ell_ms * 1e-3) / 1e9,
+                "frac": ell_alg_bytes / (ell_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+        "compressed_column_order": {"gflops": world * flops / (col_ms * 1e-3) / 1e9, "ms_per_step": col_ms},
+        "speedup_vs_ell": ell_ms / ms,
+        "clocks": clocks,
+        "e2e": {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n, "steps": e2e_steps},
+        "gpu_launches": 2 * args.steps,
+        "paper_context_gflops": {"pezy_sc_ell": 11.6, "pezy_sc_data_index_table": 32.4},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * spmvc.h -- C ABI of a compressed-matrix SpMV library for one NVIDIA GB300
+ * (sm_103a), after Yoshifuji, Sakamoto, Nitadori and Makino, "Implementation
+ * and evaluation of data-compression algorithms for irregular-grid iterative
+ * methods on the PEZY-SC processor" (arXiv:1612.00530).
+ *
+ * The library computes y = A x (Eq. 1) with A held in device memory either
+ * as plain sliced ELL (the "Original" row of Table II) or in a compressed
+ * form decoded on the fly (Sec. V): matrix values become small indices into
+ * a per-matrix value table V (sorted ascending, Fig. 2), and column indices
+ * become stencil-pattern numbers (displacements relative to the diagonal,
+ * registered in a pattern table, Sec. V) or narrow deltas, with a raw
+ * per-slice fallback.  Compression and decompression are the "data
+ * compression/decompression subroutines" the abstract adds to an otherwise
+ * unchanged program; the Krylov solver built on top is the CG iteration of
+ * Table I without the preconditioner.
+ *
+ * Conventions for every function below:
+ *  - Every function returns an int status (SPMV_OK or an SPMV_E* code) and
+ *    never throws; spmv_strerror() names a code and spmv_last_error() gives
+ *    the calling thread's last detailed message.
+ *  - Invalid arguments are reported as SPMV_EINVAL before any device work.
+ *  - "device pointer" means memory on the current CUDA device, owned by the
+ *    caller; "host pointer" means ordinary (pageable or pinned) host memory,
+ *    owned by the caller.  The library never frees caller memory.
+ *  - A spmv_mat_t owns all memory it allocates (host and device) until
+ *    spmv_free().  Device copies are made on the first call that needs them,
+ *    on the device current at that call; later calls must use that device.
+ *  - spmv_stream_t is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Functions taking a stream enqueue their work on it and
+ *    return without waiting, unless documented otherwise.
+ *  - Input and output vectors must not overlap.
+ *  - Kernel-side checks (bounds of decoded indices) never trap: they set a
+ *    sticky per-matrix error word that spmv_device_error() reads.
+ */
+#ifndef SPMVC_H
+#define SPMVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SPMV_OK 0
+#define SPMV_EINVAL 1          /* bad argument (null pointer, size, handle) */
+#define SPMV_ENOMEM 2          /* host or device allocation failed */
+#define SPMV_ECUDA 3           /* a CUDA runtime call failed */
+#define SPMV_ECORRUPT 4        /* compressed stream fails its checksum/bounds check */
+#define SPMV_EUNSUPPORTED 5    /* matrix does not fit the requested format */
+#define SPMV_ENOTCONVERGED 6   /* cg_solve hit max_iter before the tolerance */
+#define SPMV_ETIMEOUT 7        /* a bounded device-side wait gave up */
+#define SPMV_EDEVICE 8         /* a kernel reported a decoding error */
+
+typedef struct spmv_mat_s *spmv_mat_t;
+typedef void *spmv_stream_t;
+
+/* ---- formats and summation orders ------------------------------------ */
+#define SPMV_FMT_AUTO 0        /* compress: pattern format if it fits, else delta */
+#define SPMV_FMT_ELL 1         /* plain sliced ELL, FP64 value + int32 column */
+#define SPMV_FMT_PATTERN 2     /* uint8 value codes + stencil-pattern number per row */
+#define SPMV_FMT_DELTA 3       /* per 32-row slice: int16 delta or int32 column,
+                                  uint8 code or FP64 value */
+
+#define SPMV_ORDER_COLUMN 0    /* y_i = fma chain over ascending columns from 0:
+                                  bit-identical to the plain CSR product */
+#define SPMV_ORDER_FAST 1      /* pattern format only: exact fixed-point sums,
+                                  one rounding per row (error bound below) */
+
+/* ---- matrix construction (host side; nothing is sent to the GPU yet) -- */
+#define SPMV_GEN_HPCG 0
+#define SPMV_GEN_IRREGULAR 1
+
+typedef struct {
+    int32_t kind;          /* SPMV_GEN_HPCG or SPMV_GEN_IRREGULAR */
+    int32_t nx, ny, nz;    /* grid edges, each >= 1; nx*ny*nz < 2^31 */
+    uint64_t seed;         /* irregular only */
+    double drop_prob;      /* irregular: probability a stencil link is removed (0.10) */
+    double special_frac;   /* irregular: fraction of rows with unique values (0.05) */
+    int32_t diag_rule;     /* irregular: 0 = diagonal 26 on ordinary rows,
+                              1 = max(26, 1.05 * off-diagonal row sum) */
+    int32_t permute;       /* irregular: 1 = random symmetric renumbering */
+} spmv_gen_desc;
+
+/* Builds a plain matrix from a generator.
+ * HPCG (Sec. III-A): the 27-point stencil on an nx*ny*nz grid, node
+ * i = ix + nx*(iy + ny*iz), diagonal 26 and -1 for every neighbour inside
+ * the grid (Fig. 2 values).  IRREGULAR: the same stencil with links
+ * dropped, unique values on a fraction of rows and a random renumbering
+ * (the construction is spelled out in the design notes).  *out receives a
+ * new handle of format SPMV_FMT_ELL. */
+int spmv_build(const spmv_gen_desc *desc, spmv_mat_t *out);
+
+/* Builds a plain matrix from host CSR arrays (copied; the caller keeps
+ * ownership).  rowptr: n+1 entries, rowptr[0] = 0, nondecreasing; col:
+ * rowptr[n] column indices in [0, n), strictly ascending inside each row;
+ * val: rowptr[n] FP64 values.  Errors: SPMV_EINVAL for any violation. */
+int spmv_build_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
+                   const double *val, spmv_mat_t *out);
+
+/* ---- compression (Sec. V) -------------------------------------------- */
+typedef struct {
+    int32_t format;        /* SPMV_FMT_AUTO, SPMV_FMT_PATTERN or SPMV_FMT_DELTA */
+    int32_t order;         /* SPMV_ORDER_COLUMN or SPMV_ORDER_FAST */
+    int32_t max_dict;      /* largest value table, 1..254 (default 254 when 0) */
+    int32_t min_count;     /* delta format: a value enters the table only if it
+                              occurs at least this often (default 64 when 0) */
+} spmv_opts;
+
+/* Compresses plain matrix A into a new handle *out (A is unchanged and stays
+ * valid).  The value table V lists the matrix values in ascending order
+ * (Sec. V, Fig. 2).  Pattern format: each row's column displacements from
+ * the diagonal form a pattern registered in a table of at most 32 entries
+ * (Sec. V), the union of all displacements has at most 31 entries, and
+ * every value is in V; each row is stored as one uint8 code per union slot
+ * plus its 5-bit pattern number.  Delta format: rows in slices of 32, each
+ * slice storing int16 column deltas (or raw int32 columns) and uint8 codes
+ * (or raw FP64 values).  opts may be NULL (AUTO, COLUMN).  Errors:
+ * SPMV_EUNSUPPORTED when the requested format cannot hold A. */
+int spmv_compress(spmv_mat_t A, const spmv_opts *opts, spmv_mat_t *out);
+
+/* Selects the summation order used by later spmv_apply/spmm_apply calls on a
+ * pattern-format handle.  SPMV_ORDER_FAST needs every value to be a small
+ * integer multiple (|m| <= 127) of one power of two and at most 7 values;
+ * otherwise SPMV_EUNSUPPORTED.  Other formats accept SPMV_ORDER_COLUMN only. */
+int spmv_set_order(spmv_mat_t A, int32_t order);
+
+typedef struct {
+    int64_t n;                  /* rows (= columns) */
+    int64_t nnz;                /* stored nonzeros */
+    int32_t format;             /* SPMV_FMT_* */
+    int32_t order;              /* SPMV_ORDER_* */
+    int32_t dict_size;          /* |V| (0 for ELL) */
+    int32_t n_patterns;         /* pattern format: registered patterns */
+    int32_t union_size;         /* pattern format: union of displacements */
+    int32_t record_bytes;       /* pattern format: bytes per row record */
+    int32_t max_row_nnz;
+    int32_t fast_eligible;      /* 1 if SPMV_ORDER_FAST is available */
+    int64_t n_slices;           /* ELL / delta: 32-row slices */
+    int64_t slices_value_raw;   /* delta: slices storing raw FP64 values */
+    int64_t slices_col_raw;     /* delta: slices storing raw int32 columns */
+    int64_t device_bytes;       /* matrix bytes held in device memory */
+    int64_t format_bytes;       /* matrix bytes one product reads (incl. padding) */
+    int64_t padding_bytes;      /* of format_bytes: padding slots and records */
+    uint64_t checksum;          /* FNV-1a of the compressed stream */
+} spmv_info_t;
+
+/* Fills *out with the sizes and statistics of A (host only). */
+int spmv_info(spmv_mat_t A, spmv_info_t *out);
+
+/* Rebuilds host CSR arrays from A's stored form, bit-exact (integer and
+ * bitwise work only; values are copied, never recomputed).  Buffers are
+ * caller-owned host memory of n+1, nnz and nnz entries (sizes from
+ * spmv_info).  Works for every format. */
+int spmv_decompress(spmv_mat_t A, int64_t *rowptr, int32_t *col, double *val);
+
+/* Serialises A's compressed stream (header, tables, checksum, payload) to a
+ * caller buffer.  With buf == NULL only *len is set to the size needed. */
+int spmv_export(spmv_mat_t A, void *buf, size_t *len);
+
+/* Rebuilds a handle from spmv_export() output.  The stream's checksum, its
+ * sizes and every table entry are checked on the host before anything is
+ * kept: SPMV_ECORRUPT on any mismatch, and no kernel ever sees it. */
+int spmv_import(const void *buf, size_t len, spmv_mat_t *out);
+
+/* ---- products (Eq. 1) -------------------------------------------------- */
+
+/* y = A x.  x and y: device pointers to n doubles.  Enqueued on stream.
+ * COLUMN order gives exactly the plain CSR fma chain.  FAST order (pattern
+ * format) converts x to 53-bit fixed point scaled by the largest |x_j|,
+ * sums each row exactly in integers and rounds once:
+ * |y_i - (A x)_i| <= sum_j |a_ij| * ulp(max_j |x_j|) + ulp(y_i)/2.
+ * Non-finite x falls back to the COLUMN kernel on the device. */
+int spmv_apply(spmv_mat_t A, const double *x, double *y, spmv_stream_t stream);
+
+/* y = A x with x and y in host memory: copies x to the device, runs
+ * spmv_apply on the library's own stream, copies y back and waits.
+ * Uses library-owned device buffers kept with the handle. */
+int spmv_apply_host(spmv_mat_t A, const double *x, double *y);
+
+/* y = A x in binary32: x and y device pointers to n floats; values are the
+ * table entries rounded to float; y_i = fmaf chain over ascending columns
+ * (bit-identical to the binary32 CSR product).  Pattern and delta formats,
+ * and ELL (a float copy of the values is made on first use). */
+int spmv_apply_f32(spmv_mat_t A, const float *x, float *y, spmv_stream_t stream);
+
+/* Y = A X for k right-hand sides, X (n x k, leading dimension ldx >= k) and
+ * Y (n x k, ldy >= k) row-major device arrays of doubles, 1 <= k <= 64.
+ * Each column of Y obeys spmv_apply's rule for the handle's order. */
+int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
+               int64_t ldy, spmv_stream_t stream);
+
+/* ---- ragged batches: one persistent launch over many matrices --------- */
+typedef struct spmv_batch_s *spmv_batch_t;
+
+/* Plans y_b = A_b x_b for count pattern-format matrices of any sizes (their
+ * records must have equal record_bytes).  xs/ys: host arrays of count device
+ * pointers, fixed for the plan's lifetime.  The work list (matrix, row range)
+ * is uploaded once and the launch is captured in a CUDA graph. */
+int spmv_batch_create(int32_t count, const spmv_mat_t *mats, const double *const *xs,
+                      double *const *ys, spmv_batch_t *out);
+/* Replays the plan's graph on stream (one persistent kernel launch). */
+int spmv_batch_launch(spmv_batch_t plan, spmv_stream_t stream);
+int spmv_batch_free(spmv_batch_t plan);
+/* create + launch + wait + free, for one-off use. */
+int spmv_apply_batched(int32_t count, const spmv_mat_t *mats, const double *const *xs,
+                       double *const *ys, spmv_stream_t stream);
+
+/* ---- conjugate gradients (Table I's CG iteration, no preconditioner) -- */
+#define SPMV_CG_FP64 0         /* plain CG, all vectors and products in FP64 */
+#define SPMV_CG_IR_FP32 1      /* iterative refinement: FP64 residual b - A x,
+                                  norms and solution update; inner CG with the
+                                  binary32 product and binary32 vectors */
+
+typedef struct {
+    double tol;            /* stop when |b - A x|_2 / |b|_2 <= tol (default 1e-10) */
+    int32_t max_iter;      /* cap on (inner) CG steps (default 10000) */
+    int32_t mode;          /* SPMV_CG_FP64 or SPMV_CG_IR_FP32 */
+    int32_t check_every;   /* host reads the device convergence flag every
+                              this many steps (default 16) */
+    int32_t inner_max_iter;/* IR: cap per inner solve (default 60) */
+    double inner_tol;      /* IR: inner relative reduction (default 1e-5) */
+    int32_t nrhs;          /* right-hand sides solved together (1..32, default 1):
+                              b and x are n x nrhs row-major */
+    int32_t use_graph;     /* 1 (default): replay captured CUDA graphs */
+} spmv_cg_opts;
+
+typedef struct {
+    int32_t status;        /* SPMV_OK or SPMV_ENOTCONVERGED */
+    int32_t iterations;    /* CG steps (IR: total inner steps) */
+    int32_t outer_iterations;  /* IR refinement steps (FP64: 0) */
+    int32_t history_len;   /* entries in history */
+    double rel_residual;   /* final true relative residual (max over columns) */
+    double seconds;        /* device time of the solve (CUDA events) */
+    double *history;       /* |r_k|/|b| per step (column 0), library-owned
+                              until spmv_cg_result_free() */
+} spmv_cg_result;
+
+/* Solves A x = b (device pointers, n x nrhs doubles each; x holds the
+ * initial guess).  Synchronous: returns when done.  res may be NULL. */
+int cg_solve(spmv_mat_t A, const double *b, double *x, const spmv_cg_opts *opts,
+             spmv_cg_result *res);
+int spmv_cg_result_free(spmv_cg_result *res);
+
+/* ---- lifetime and diagnostics ---------------------------------------- */
+int spmv_free(spmv_mat_t A);
+const char *spmv_strerror(int status);
+/* The calling thread's last detailed error message ("" if none). */
+const char *spmv_last_error(void);
+/* Reads and clears A's sticky device error word (0 = none); waits for the
+ * device. */
+int spmv_device_error(spmv_mat_t A, int32_t *code);
+/* Library version string. */
+const char *spmv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMVC_H */

@@ -1,0 +1,503 @@
+// C ABI of the compressed-SpMV library (declared in include/spmvc.h).
+// Handles own host copies of their stored form and, after the first device
+// call, device copies.  All errors come back as status codes with a
+// thread-local message; nothing throws across the boundary.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "spmvc_internal.h"
+
+namespace spmvc {
+
+int decompress_ell(int64_t n, const EllFormat& e, Csr* out);
+int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out);
+int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out);
+uint64_t checksum_of(const spmv_mat_s& m);
+int export_stream(const spmv_mat_s& m, void* buf, size_t* len);
+int import_stream(const void* buf, size_t len, spmv_mat_s* m);
+void derive_fast_order(int64_t n, PatternFormat* p);
+
+namespace {
+thread_local std::string g_last_error;
+constexpr uint32_t kMagic = 0x5350564du;
+constexpr int kPartialWords = 152 * 64;
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+
+namespace {
+
+bool valid(spmv_mat_t m) { return m != nullptr && m->magic == kMagic; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(SPMV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SPMVC_CUDA(call)                                     \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+template <class T>
+int dev_copy(spmv_mat_s* m, const T* src, size_t count, T** dst) {
+    *dst = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(SPMV_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    m->dev_allocs.push_back(p);
+    if (count && src) {
+        e = cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    } else {
+        e = cudaMemset(p, 0, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    }
+    *dst = static_cast<T*>(p);
+    return SPMV_OK;
+}
+
+void free_device(spmv_mat_s* m) {
+    for (void* p : m->dev_allocs) cudaFree(p);
+    m->dev_allocs.clear();
+    if (m->own_stream) cudaStreamDestroy(m->own_stream);
+    m->own_stream = nullptr;
+    m->device = -1;
+    m->d_ell_val32 = nullptr;
+    m->d_hx = m->d_hy = nullptr;
+}
+
+// First device use: copy the stored form to the current device.
+int ensure_device(spmv_mat_s* m) {
+    int dev = 0;
+    SPMVC_CUDA(cudaGetDevice(&dev));
+    if (m->device >= 0) {
+        if (dev != m->device) return fail(SPMV_EINVAL, "matrix lives on another device");
+        return SPMV_OK;
+    }
+    int st;
+    int32_t zero = 0;
+    if ((st = dev_copy(m, &zero, 1, &m->d_err))) return st;
+    std::vector<uint32_t> zeros(kPartialWords, 0u);
+    if ((st = dev_copy(m, zeros.data(), zeros.size(), &m->d_scratch_words))) return st;
+    m->scratch_words = kPartialWords;
+    if (m->fmt == SPMV_FMT_ELL) {
+        EllView& v = m->ell_view;
+        v.n = m->n;
+        v.nslices = m->ell.nslices;
+        int64_t* so;
+        int32_t *sw, *col;
+        double* val;
+        if ((st = dev_copy(m, m->ell.slice_off.data(), m->ell.slice_off.size(), &so))) return st;
+        if ((st = dev_copy(m, m->ell.slice_w.data(), m->ell.slice_w.size(), &sw))) return st;
+        if ((st = dev_copy(m, m->ell.val.data(), m->ell.val.size(), &val))) return st;
+        if ((st = dev_copy(m, m->ell.col.data(), m->ell.col.size(), &col))) return st;
+        v.slice_off = so;
+        v.slice_w = sw;
+        v.val = val;
+        v.col = col;
+        v.val32 = nullptr;
+    } else if (m->fmt == SPMV_FMT_PATTERN) {
+        const PatternFormat& p = m->pat;
+        PatternView& v = m->pat_view;
+        std::memset(&v, 0, sizeof(v));
+        v.n = m->n;
+        v.nu = static_cast<int32_t>(p.uoff.size());
+        v.words = p.words;
+        v.dict_size = static_cast<int32_t>(p.dict.size());
+        v.npat = static_cast<int32_t>(p.pmask.size());
+        for (int u = 0; u < v.nu; ++u) v.uoff[u] = p.uoff[u];
+        for (int q = 0; q < v.npat; ++q) v.pmask[q] = p.pmask[q];
+        const int64_t n = m->n;
+        const int q16 = p.words / 4, rem = p.words % 4;
+        std::vector<uint32_t> plane;
+        auto upload_plane = [&](int first, int width, const void** out) -> int {
+            plane.assign(static_cast<size_t>(n) * width, 0u);
+            for (int64_t r = 0; r < n; ++r)
+                for (int k = 0; k < width; ++k) plane[r * width + k] = p.rec[r * p.words + first + k];
+            uint32_t* d;
+            int s2 = dev_copy(m, plane.data(), plane.size(), &d);
+            *out = d;
+            return s2;
+        };
+        const void* ptr;
+        if (q16 >= 1) { if ((st = upload_plane(0, 4, &ptr))) return st; v.p16a = static_cast<const uint4*>(ptr); }
+        if (q16 >= 2) { if ((st = upload_plane(4, 4, &ptr))) return st; v.p16b = static_cast<const uint4*>(ptr); }
+        if (rem >= 2) { if ((st = upload_plane(4 * q16, 2, &ptr))) return st; v.p8 = static_cast<const uint2*>(ptr); }
+        if (rem & 1) { if ((st = upload_plane(p.words - 1, 1, &ptr))) return st; v.p4 = static_cast<const uint32_t*>(ptr); }
+        std::vector<double> dict(p.dict);
+        std::vector<float> dict32;
+        for (double d : dict) dict32.push_back(static_cast<float>(d));
+        double* dd;
+        float* df;
+        if ((st = dev_copy(m, dict.data(), dict.size(), &dd))) return st;
+        if ((st = dev_copy(m, dict32.data(), dict32.size(), &df))) return st;
+        v.dict = dd;
+        v.dict32 = df;
+        uint8_t tbl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (p.fast_ok)
+            for (size_t k = 0; k < p.mult.size() && k < 7; ++k) tbl[k] = static_cast<uint8_t>(int8_t(p.mult[k]));
+        std::memcpy(&v.mult_lo, tbl, 4);
+        std::memcpy(&v.mult_hi, tbl + 4, 4);
+        v.mult_exp = p.mult_exp;
+        v.err = m->d_err;
+    } else {
+        const DeltaFormat& d = m->dlt;
+        DeltaView& v = m->dlt_view;
+        v.n = m->n;
+        v.nslices = d.nslices;
+        v.dict_size = static_cast<int32_t>(d.dict.size());
+        DeltaSlice* h;
+        uint8_t* pl;
+        double* dd;
+        float* df;
+        std::vector<float> dict32;
+        for (double x : d.dict) dict32.push_back(static_cast<float>(x));
+        if ((st = dev_copy(m, d.hdr.data(), d.hdr.size(), &h))) return st;
+        if ((st = dev_copy(m, d.payload.data(), d.payload.size(), &pl))) return st;
+        if ((st = dev_copy(m, d.dict.data(), d.dict.size(), &dd))) return st;
+        if ((st = dev_copy(m, dict32.data(), dict32.size(), &df))) return st;
+        v.hdr = h;
+        v.payload = pl;
+        v.dict = dd;
+        v.dict32 = df;
+        v.err = m->d_err;
+    }
+    m->device = dev;
+    return SPMV_OK;
+}
+
+int new_handle(spmv_mat_t* out, spmv_mat_s** m) {
+    if (!out) return fail(SPMV_EINVAL, "null output handle");
+    *out = nullptr;
+    *m = new (std::nothrow) spmv_mat_s();
+    if (!*m) return fail(SPMV_ENOMEM, "host allocation failed");
+    (*m)->magic = kMagic;
+    return SPMV_OK;
+}
+
+void stats_from_csr(spmv_mat_s* m, const Csr& c) {
+    m->n = c.n;
+    m->nnz = c.nnz();
+    m->max_row_nnz = 0;
+    for (int64_t i = 0; i < c.n; ++i)
+        m->max_row_nnz = std::max<int32_t>(m->max_row_nnz, static_cast<int32_t>(c.rowptr[i + 1] - c.rowptr[i]));
+}
+
+int finish_plain(spmv_mat_s* m, spmv_mat_t* out) {
+    stats_from_csr(m, m->csr);
+    m->fmt = SPMV_FMT_ELL;
+    int st = pack_ell(m->csr, &m->ell);
+    if (st) { delete m; return st; }
+    m->checksum = checksum_of(*m);
+    *out = m;
+    return SPMV_OK;
+}
+
+int to_csr(spmv_mat_s* a, Csr* c) {
+    if (a->fmt == SPMV_FMT_ELL && a->csr.n == a->n && !a->csr.rowptr.empty()) {
+        *c = a->csr;
+        return SPMV_OK;
+    }
+    if (a->fmt == SPMV_FMT_ELL) return decompress_ell(a->n, a->ell, c);
+    if (a->fmt == SPMV_FMT_PATTERN) return decompress_pattern(a->n, a->pat, c);
+    return decompress_delta(a->n, a->dlt, c);
+}
+
+cudaStream_t as_stream(spmv_stream_t s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+}  // namespace spmvc
+
+using namespace spmvc;
+
+extern "C" {
+
+int spmv_build(const spmv_gen_desc* desc, spmv_mat_t* out) {
+    if (!desc) return fail(SPMV_EINVAL, "null generator description");
+    spmv_mat_s* m;
+    int st = new_handle(out, &m);
+    if (st) return st;
+    if (desc->kind == SPMV_GEN_HPCG) st = generate_hpcg(desc->nx, desc->ny, desc->nz, &m->csr);
+    else if (desc->kind == SPMV_GEN_IRREGULAR) st = generate_irregular(*desc, &m->csr);
+    else st = fail(SPMV_EINVAL, "unknown generator kind");
+    if (st) { delete m; return st; }
+    return finish_plain(m, out);
+}
+
+int spmv_build_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, spmv_mat_t* out) {
+    int st = validate_csr(n, rowptr, col, val);
+    if (st) return st;
+    spmv_mat_s* m;
+    if ((st = new_handle(out, &m))) return st;
+    m->csr.n = n;
+    m->csr.rowptr.assign(rowptr, rowptr + n + 1);
+    m->csr.col.assign(col, col + rowptr[n]);
+    m->csr.val.assign(val, val + rowptr[n]);
+    return finish_plain(m, out);
+}
+
+int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    spmv_opts o{SPMV_FMT_AUTO, SPMV_ORDER_COLUMN, 254, 64};
+    if (opts) o = *opts;
+    if (o.max_dict <= 0) o.max_dict = 254;
+    if (o.min_count <= 0) o.min_count = 64;
+    if (o.max_dict > 254) return fail(SPMV_EINVAL, "max_dict above 254");
+    if (o.format != SPMV_FMT_AUTO && o.format != SPMV_FMT_PATTERN && o.format != SPMV_FMT_DELTA)
+        return fail(SPMV_EINVAL, "compress format must be AUTO, PATTERN or DELTA");
+    Csr c;
+    int st = to_csr(A, &c);
+    if (st) return st;
+    spmv_mat_s* m;
+    if ((st = new_handle(out, &m))) return st;
+    stats_from_csr(m, c);
+    st = SPMV_EUNSUPPORTED;
+    if (o.format == SPMV_FMT_AUTO || o.format == SPMV_FMT_PATTERN) {
+        st = compress_pattern(c, o.max_dict, &m->pat);
+        if (st == SPMV_OK) m->fmt = SPMV_FMT_PATTERN;
+        else if (o.format == SPMV_FMT_PATTERN) { delete m; return st; }
+    }
+    if (st != SPMV_OK) {
+        m->pat = PatternFormat{};
+        st = compress_delta(c, o.max_dict, o.min_count, &m->dlt);
+        if (st) { delete m; return st; }
+        m->fmt = SPMV_FMT_DELTA;
+    }
+    m->checksum = checksum_of(*m);
+    *out = m;
+    if (o.order != SPMV_ORDER_COLUMN) {
+        st = spmv_set_order(m, o.order);
+        if (st) { delete m; *out = nullptr; return st; }
+    }
+    return SPMV_OK;
+}
+
+int spmv_set_order(spmv_mat_t A, int32_t order) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (order == SPMV_ORDER_COLUMN) { A->order = order; return SPMV_OK; }
+    if (order != SPMV_ORDER_FAST) return fail(SPMV_EINVAL, "unknown order");
+    if (A->fmt != SPMV_FMT_PATTERN || !A->pat.fast_ok)
+        return fail(SPMV_EUNSUPPORTED, "FAST order needs the pattern format with a small integer value table");
+    A->order = order;
+    return SPMV_OK;
+}
+
+int spmv_info(spmv_mat_t A, spmv_info_t* out) {
+    if (!valid(A) || !out) return fail(SPMV_EINVAL, "invalid argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n = A->n;
+    out->nnz = A->nnz;
+    out->format = A->fmt;
+    out->order = A->order;
+    out->max_row_nnz = A->max_row_nnz;
+    out->checksum = A->checksum;
+    if (A->fmt == SPMV_FMT_ELL) {
+        out->n_slices = A->ell.nslices;
+        out->format_bytes = static_cast<int64_t>(A->ell.val.size() * 12 + A->ell.slice_off.size() * 8 +
+                                                 A->ell.slice_w.size() * 4);
+        out->padding_bytes = static_cast<int64_t>((A->ell.val.size() - A->nnz) * 12);
+        out->device_bytes = out->format_bytes;
+    } else if (A->fmt == SPMV_FMT_PATTERN) {
+        out->dict_size = static_cast<int32_t>(A->pat.dict.size());
+        out->n_patterns = static_cast<int32_t>(A->pat.pmask.size());
+        out->union_size = static_cast<int32_t>(A->pat.uoff.size());
+        out->record_bytes = 4 * A->pat.words;
+        out->fast_eligible = A->pat.fast_ok ? 1 : 0;
+        out->format_bytes = A->n * 4 * A->pat.words;
+        out->padding_bytes = out->format_bytes - A->nnz - A->n;
+        out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
+    } else {
+        out->dict_size = static_cast<int32_t>(A->dlt.dict.size());
+        out->n_slices = A->dlt.nslices;
+        for (const auto& h : A->dlt.hdr) {
+            out->slices_value_raw += (h.flags & kSliceValRaw) ? 1 : 0;
+            out->slices_col_raw += (h.flags & kSliceColRaw) ? 1 : 0;
+        }
+        out->format_bytes = static_cast<int64_t>(A->dlt.payload.size() + A->dlt.hdr.size() * sizeof(DeltaSlice));
+        int64_t useful = A->n;  // row lengths
+        for (int64_t s = 0; s < A->dlt.nslices; ++s) {
+            const auto& h = A->dlt.hdr[s];
+            const int64_t r0 = s * kSliceRows, r1 = std::min<int64_t>(A->n, r0 + kSliceRows);
+            const int64_t per = ((h.flags & kSliceColRaw) ? 4 : 2) + ((h.flags & kSliceValRaw) ? 8 : 1);
+            const uint8_t* base = A->dlt.payload.data() + h.off;
+            for (int64_t r = r0; r < r1; ++r) useful += per * base[r - r0];
+        }
+        out->padding_bytes = out->format_bytes - useful - static_cast<int64_t>(A->dlt.hdr.size() * sizeof(DeltaSlice));
+        out->device_bytes = out->format_bytes + static_cast<int64_t>(A->dlt.dict.size() * 12);
+    }
+    return SPMV_OK;
+}
+
+int spmv_decompress(spmv_mat_t A, int64_t* rowptr, int32_t* col, double* val) {
+    if (!valid(A) || !rowptr || (A->nnz > 0 && (!col || !val))) return fail(SPMV_EINVAL, "invalid argument");
+    Csr c;
+    int st;
+    if (A->fmt == SPMV_FMT_ELL) st = decompress_ell(A->n, A->ell, &c);
+    else if (A->fmt == SPMV_FMT_PATTERN) st = decompress_pattern(A->n, A->pat, &c);
+    else st = decompress_delta(A->n, A->dlt, &c);
+    if (st) return st;
+    if (c.nnz() != A->nnz) return fail(SPMV_ECORRUPT, "decompressed nonzero count differs");
+    std::memcpy(rowptr, c.rowptr.data(), sizeof(int64_t) * (A->n + 1));
+    if (A->nnz) {
+        std::memcpy(col, c.col.data(), sizeof(int32_t) * A->nnz);
+        std::memcpy(val, c.val.data(), sizeof(double) * A->nnz);
+    }
+    return SPMV_OK;
+}
+
+int spmv_export(spmv_mat_t A, void* buf, size_t* len) {
+    if (!valid(A) || !len) return fail(SPMV_EINVAL, "invalid argument");
+    return export_stream(*A, buf, len);
+}
+
+int spmv_import(const void* buf, size_t len, spmv_mat_t* out) {
+    if (!buf || !out) return fail(SPMV_EINVAL, "invalid argument");
+    spmv_mat_s* m;
+    int st = new_handle(out, &m);
+    if (st) return st;
+    st = import_stream(buf, len, m);
+    Csr c;
+    if (!st) {
+        if (m->fmt == SPMV_FMT_ELL) st = decompress_ell(m->n, m->ell, &c);
+        else if (m->fmt == SPMV_FMT_PATTERN) st = decompress_pattern(m->n, m->pat, &c);
+        else st = decompress_delta(m->n, m->dlt, &c);
+    }
+    if (!st && c.nnz() != m->nnz) st = fail(SPMV_ECORRUPT, "corrupt stream: nonzero count");
+    if (st) { delete m; return st; }
+    stats_from_csr(m, c);
+    if (m->fmt == SPMV_FMT_ELL) m->csr = std::move(c);
+    if (m->fmt == SPMV_FMT_PATTERN) derive_fast_order(m->n, &m->pat);
+    *out = m;
+    return SPMV_OK;
+}
+
+int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
+    if (x == y && A->n > 0) return fail(SPMV_EINVAL, "x and y must not alias");
+    int st = ensure_device(A);
+    if (st) return st;
+    cudaError_t e;
+    const cudaStream_t s = as_stream(stream);
+    if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
+    else if (A->fmt == SPMV_FMT_PATTERN)
+        e = A->order == SPMV_ORDER_FAST ? launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s)
+                                        : launch_pattern_col_f64(A->pat_view, x, y, s);
+    else e = launch_delta_f64(A->dlt_view, x, y, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
+    return SPMV_OK;
+}
+
+int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
+    int st = ensure_device(A);
+    if (st) return st;
+    if (!A->own_stream) SPMVC_CUDA(cudaStreamCreateWithFlags(&A->own_stream, cudaStreamNonBlocking));
+    if (!A->d_hx) {
+        if ((st = dev_copy<double>(A, nullptr, A->n, &A->d_hx))) return st;
+        if ((st = dev_copy<double>(A, nullptr, A->n, &A->d_hy))) return st;
+    }
+    const size_t bytes = sizeof(double) * A->n;
+    SPMVC_CUDA(cudaMemcpyAsync(A->d_hx, x, bytes, cudaMemcpyHostToDevice, A->own_stream));
+    if ((st = spmv_apply(A, A->d_hx, A->d_hy, A->own_stream))) return st;
+    SPMVC_CUDA(cudaMemcpyAsync(y, A->d_hy, bytes, cudaMemcpyDeviceToHost, A->own_stream));
+    SPMVC_CUDA(cudaStreamSynchronize(A->own_stream));
+    return SPMV_OK;
+}
+
+int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
+    int st = ensure_device(A);
+    if (st) return st;
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e;
+    if (A->fmt == SPMV_FMT_ELL) {
+        if (!A->d_ell_val32) {
+            std::vector<float> v32(A->ell.val.size());
+            for (size_t k = 0; k < v32.size(); ++k) v32[k] = static_cast<float>(A->ell.val[k]);
+            if ((st = dev_copy(A, v32.data(), v32.size(), &A->d_ell_val32))) return st;
+            A->ell_view.val32 = A->d_ell_val32;
+        }
+        e = launch_ell_f32(A->ell_view, x, y, s);
+    } else if (A->fmt == SPMV_FMT_PATTERN) {
+        e = launch_pattern_col_f32(A->pat_view, x, y, s);
+    } else {
+        e = launch_delta_f32(A->dlt_view, x, y, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "spmv_f32 launch");
+    return SPMV_OK;
+}
+
+int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y, int64_t ldy,
+               spmv_stream_t stream) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (k < 1 || k > 64 || ldx < k || ldy < k) return fail(SPMV_EINVAL, "need 1 <= k <= 64, ldx >= k, ldy >= k");
+    if (A->n > 0 && (!X || !Y)) return fail(SPMV_EINVAL, "null block");
+    int st = ensure_device(A);
+    if (st) return st;
+    const cudaStream_t s = as_stream(stream);
+    cudaError_t e;
+    if (A->fmt == SPMV_FMT_ELL) e = launch_ell_spmm(A->ell_view, k, X, ldx, Y, ldy, s);
+    else if (A->fmt == SPMV_FMT_PATTERN)
+        e = A->order == SPMV_ORDER_FAST
+                ? launch_pattern_spmm_fast(A->pat_view, k, X, ldx, Y, ldy, A->d_scratch_words, s)
+                : launch_pattern_spmm_col(A->pat_view, k, X, ldx, Y, ldy, s);
+    else e = launch_delta_spmm(A->dlt_view, k, X, ldx, Y, ldy, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmm launch");
+    return SPMV_OK;
+}
+
+int spmv_free(spmv_mat_t A) {
+    if (!A) return SPMV_OK;
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    free_device(A);
+    A->magic = 0;
+    delete A;
+    return SPMV_OK;
+}
+
+const char* spmv_strerror(int status) {
+    switch (status) {
+        case SPMV_OK: return "ok";
+        case SPMV_EINVAL: return "invalid argument";
+        case SPMV_ENOMEM: return "out of memory";
+        case SPMV_ECUDA: return "CUDA error";
+        case SPMV_ECORRUPT: return "corrupt compressed stream";
+        case SPMV_EUNSUPPORTED: return "unsupported for this matrix or format";
+        case SPMV_ENOTCONVERGED: return "not converged";
+        case SPMV_ETIMEOUT: return "device wait timed out";
+        case SPMV_EDEVICE: return "device-side decoding error";
+        default: return "unknown status";
+    }
+}
+
+const char* spmv_last_error(void) { return g_last_error.c_str(); }
+
+int spmv_device_error(spmv_mat_t A, int32_t* code) {
+    if (!valid(A) || !code) return fail(SPMV_EINVAL, "invalid argument");
+    *code = 0;
+    if (A->device < 0) return SPMV_OK;
+    SPMVC_CUDA(cudaDeviceSynchronize());
+    SPMVC_CUDA(cudaMemcpy(code, A->d_err, 4, cudaMemcpyDeviceToHost));
+    SPMVC_CUDA(cudaMemset(A->d_err, 0, 4));
+    return SPMV_OK;
+}
+
+const char* spmv_version(void) { return "spmvc 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// Accessors used by the solver and batch translation units.
+namespace spmvc {
+int api_ensure_device(spmv_mat_s* m) { return ensure_device(m); }
+bool api_valid(spmv_mat_t m) { return valid(m); }
+}  // namespace spmvc

@@ -1,0 +1,294 @@
+// Decompression of every stored format back to CSR (bit-exact: values are
+// copied, never recomputed), stream checksums, and export/import of a
+// matrix's stored form.  Decompression checks every decoded index, so it is
+// also how an imported stream is validated before any kernel can see it.
+#include <cmath>
+#include <cstring>
+
+#include "spmvc_internal.h"
+
+namespace spmvc {
+
+int decompress_ell(int64_t n, const EllFormat& e, Csr* out);
+int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out);
+int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out);
+uint64_t checksum_of(const spmv_mat_s& m);
+int export_stream(const spmv_mat_s& m, void* buf, size_t* len);
+int import_stream(const void* buf, size_t len, spmv_mat_s* m);
+
+namespace {
+
+int corrupt(const char* what) { return fail(SPMV_ECORRUPT, std::string("corrupt stream: ") + what); }
+
+int finish_csr(Csr* out) {
+    // columns must be strictly ascending in every row
+    for (int64_t i = 0; i < out->n; ++i)
+        for (int64_t k = out->rowptr[i] + 1; k < out->rowptr[i + 1]; ++k)
+            if (out->col[k] <= out->col[k - 1]) return corrupt("columns not ascending");
+    return SPMV_OK;
+}
+
+// FNV-1a over 64-bit words (then the tail bytes).
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void* p, size_t len) {
+        const uint8_t* b = static_cast<const uint8_t*>(p);
+        size_t i = 0;
+        for (; i + 8 <= len; i += 8) {
+            uint64_t w;
+            std::memcpy(&w, b + i, 8);
+            h = (h ^ w) * 1099511628211ull;
+        }
+        for (; i < len; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+    template <class T> void vec(const std::vector<T>& v) {
+        const uint64_t k = v.size();
+        add(&k, 8);
+        if (!v.empty()) add(v.data(), v.size() * sizeof(T));
+    }
+    template <class T> void pod(const T& v) { add(&v, sizeof(T)); }
+};
+
+}  // namespace
+
+int decompress_ell(int64_t n, const EllFormat& e, Csr* out) {
+    out->n = n;
+    out->rowptr.assign(n + 1, 0);
+    out->col.clear();
+    out->val.clear();
+    if (e.nslices != (n + kSliceRows - 1) / kSliceRows || (int64_t)e.slice_off.size() != e.nslices + 1 ||
+        (int64_t)e.slice_w.size() != e.nslices)
+        return corrupt("ELL slice table size");
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t s = r / kSliceRows, l = r % kSliceRows;
+        const int64_t w = e.slice_w[s];
+        if (w < 0 || e.slice_off[s] + w * kSliceRows > (int64_t)e.val.size()) return corrupt("ELL slice bounds");
+        for (int64_t t = 0; t < w; ++t) {
+            const int64_t k = e.slice_off[s] + t * kSliceRows + l;
+            if (e.col[k] < 0) continue;
+            if (e.col[k] >= n) return corrupt("ELL column out of range");
+            out->col.push_back(e.col[k]);
+            out->val.push_back(e.val[k]);
+        }
+        out->rowptr[r + 1] = static_cast<int64_t>(out->col.size());
+    }
+    return finish_csr(out);
+}
+
+int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out) {
+    const int nu = static_cast<int>(p.uoff.size());
+    if (nu > kMaxUnion || p.words != (nu + 4) / 4 || (int64_t)p.rec.size() != n * p.words ||
+        p.pmask.size() > (size_t)kMaxPatterns || p.dict.size() > 254)
+        return corrupt("pattern table sizes");
+    for (size_t q = 0; q < p.pmask.size(); ++q)
+        if (nu < 32 && (p.pmask[q] >> nu) != 0) return corrupt("pattern mask outside the union");
+    out->n = n;
+    out->rowptr.assign(n + 1, 0);
+    out->col.clear();
+    out->val.clear();
+    const uint32_t ndict = static_cast<uint32_t>(p.dict.size());
+    for (int64_t r = 0; r < n; ++r) {
+        const uint8_t* b = reinterpret_cast<const uint8_t*>(&p.rec[static_cast<size_t>(r) * p.words]);
+        const uint32_t pat = b[nu];
+        if (pat >= p.pmask.size()) return corrupt("pattern number out of range");
+        for (int u = 0; u < nu; ++u) {
+            if (!((p.pmask[pat] >> u) & 1u)) continue;
+            const int64_t c = r + p.uoff[u];
+            if (c < 0 || c >= n) return corrupt("pattern column out of range");
+            if (b[u] >= ndict) return corrupt("value code out of range");
+            out->col.push_back(static_cast<int32_t>(c));
+            out->val.push_back(p.dict[b[u]]);
+        }
+        out->rowptr[r + 1] = static_cast<int64_t>(out->col.size());
+    }
+    return finish_csr(out);
+}
+
+int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out) {
+    if (d.nslices != (n + kSliceRows - 1) / kSliceRows || (int64_t)d.hdr.size() != d.nslices || d.dict.size() > 255)
+        return corrupt("delta slice table size");
+    out->n = n;
+    out->rowptr.assign(n + 1, 0);
+    out->col.clear();
+    out->val.clear();
+    for (int64_t s = 0; s < d.nslices; ++s) {
+        const DeltaSlice h = d.hdr[s];
+        const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
+        if (h.flags & ~3u) return corrupt("slice flags");
+        if (h.w > 255 || h.off % 16 != 0) return corrupt("slice header");
+        const uint64_t cbytes = (32 + uint64_t(h.w) * kSliceRows * (craw ? 4 : 2) + 15) / 16 * 16;
+        const uint64_t vbytes = (uint64_t(h.w) * kSliceRows * (vraw ? 8 : 1) + 15) / 16 * 16;
+        if (h.off + cbytes + vbytes > d.payload.size()) return corrupt("slice payload bounds");
+        const uint8_t* base = d.payload.data() + h.off;
+        const uint8_t* cols = base + 32;
+        const uint8_t* vals = base + cbytes;
+        for (int64_t r = s * kSliceRows; r < std::min(n, (s + 1) * kSliceRows); ++r) {
+            const int64_t l = r - s * kSliceRows;
+            const uint32_t len = base[l];
+            if (len > h.w) return corrupt("row length above slice width");
+            for (uint32_t t = 0; t < len; ++t) {
+                const int64_t slot = int64_t(t) * kSliceRows + l;
+                int64_t c;
+                if (craw) {
+                    int32_t c32;
+                    std::memcpy(&c32, cols + 4 * slot, 4);
+                    c = c32;
+                } else {
+                    int16_t d16;
+                    std::memcpy(&d16, cols + 2 * slot, 2);
+                    c = r + d16;
+                }
+                if (c < 0 || c >= n) return corrupt("delta column out of range");
+                double v;
+                if (vraw) {
+                    std::memcpy(&v, vals + 8 * slot, 8);
+                } else {
+                    if (vals[slot] >= d.dict.size()) return corrupt("value code out of range");
+                    v = d.dict[vals[slot]];
+                }
+                out->col.push_back(static_cast<int32_t>(c));
+                out->val.push_back(v);
+            }
+            out->rowptr[r + 1] = static_cast<int64_t>(out->col.size());
+        }
+    }
+    return finish_csr(out);
+}
+
+uint64_t checksum_of(const spmv_mat_s& m) {
+    Fnv f;
+    f.pod(m.fmt);
+    f.pod(m.n);
+    f.pod(m.nnz);
+    if (m.fmt == SPMV_FMT_ELL) {
+        f.vec(m.ell.slice_off);
+        f.vec(m.ell.slice_w);
+        f.vec(m.ell.val);
+        f.vec(m.ell.col);
+    } else if (m.fmt == SPMV_FMT_PATTERN) {
+        f.vec(m.pat.dict);
+        f.vec(m.pat.uoff);
+        f.vec(m.pat.pmask);
+        f.pod(m.pat.words);
+        f.vec(m.pat.rec);
+    } else {
+        f.vec(m.dlt.dict);
+        f.vec(m.dlt.hdr);
+        f.vec(m.dlt.payload);
+    }
+    return f.h;
+}
+
+// ------------------------------------------------------ export / import ---
+// Stream: "SPMVC\0v1" | fmt | n | nnz | checksum | arrays, each as
+// (uint64 element count, raw bytes).
+namespace {
+struct Writer {
+    uint8_t* p;
+    size_t pos = 0, cap;
+    bool dry;
+    void put(const void* src, size_t len) {
+        if (!dry && pos + len <= cap) std::memcpy(p + pos, src, len);
+        pos += len;
+    }
+    template <class T> void pod(const T& v) { put(&v, sizeof(T)); }
+    template <class T> void vec(const std::vector<T>& v) {
+        const uint64_t k = v.size();
+        pod(k);
+        if (k) put(v.data(), k * sizeof(T));
+    }
+};
+struct Reader {
+    const uint8_t* p;
+    size_t pos = 0, len;
+    bool ok = true;
+    void get(void* dst, size_t l) {
+        if (!ok || pos + l > len) { ok = false; return; }
+        std::memcpy(dst, p + pos, l);
+        pos += l;
+    }
+    template <class T> void pod(T* v) { get(v, sizeof(T)); }
+    template <class T> void vec(std::vector<T>* v) {
+        uint64_t k = 0;
+        pod(&k);
+        if (!ok || k > (len - pos) / sizeof(T)) { ok = false; return; }
+        v->resize(k);
+        if (k) get(v->data(), k * sizeof(T));
+    }
+};
+const char kTag[8] = {'S', 'P', 'M', 'V', 'C', 0, 'v', '1'};
+}  // namespace
+
+int export_stream(const spmv_mat_s& m, void* buf, size_t* len) {
+    Writer w{static_cast<uint8_t*>(buf), 0, buf ? *len : 0, buf == nullptr};
+    w.put(kTag, 8);
+    w.pod(m.fmt);
+    w.pod(m.n);
+    w.pod(m.nnz);
+    w.pod(m.checksum);
+    if (m.fmt == SPMV_FMT_ELL) {
+        w.pod(m.ell.nslices);
+        w.vec(m.ell.slice_off);
+        w.vec(m.ell.slice_w);
+        w.vec(m.ell.val);
+        w.vec(m.ell.col);
+    } else if (m.fmt == SPMV_FMT_PATTERN) {
+        w.vec(m.pat.dict);
+        w.vec(m.pat.uoff);
+        w.vec(m.pat.pmask);
+        w.pod(m.pat.words);
+        w.vec(m.pat.rec);
+    } else {
+        w.pod(m.dlt.nslices);
+        w.vec(m.dlt.dict);
+        w.vec(m.dlt.hdr);
+        w.vec(m.dlt.payload);
+    }
+    if (!buf) {
+        *len = w.pos;
+        return SPMV_OK;
+    }
+    if (w.pos > *len) return fail(SPMV_EINVAL, "export buffer too small");
+    *len = w.pos;
+    return SPMV_OK;
+}
+
+int import_stream(const void* buf, size_t len, spmv_mat_s* m) {
+    Reader r{static_cast<const uint8_t*>(buf), 0, len};
+    char tag[8];
+    r.get(tag, 8);
+    if (!r.ok || std::memcmp(tag, kTag, 8) != 0) return corrupt("bad tag");
+    uint64_t sum = 0;
+    r.pod(&m->fmt);
+    r.pod(&m->n);
+    r.pod(&m->nnz);
+    r.pod(&sum);
+    if (!r.ok || m->n < 0 || m->n >= (int64_t(1) << 31)) return corrupt("header");
+    if (m->fmt == SPMV_FMT_ELL) {
+        r.pod(&m->ell.nslices);
+        r.vec(&m->ell.slice_off);
+        r.vec(&m->ell.slice_w);
+        r.vec(&m->ell.val);
+        r.vec(&m->ell.col);
+        if (r.ok && m->ell.val.size() != m->ell.col.size()) return corrupt("ELL array sizes");
+    } else if (m->fmt == SPMV_FMT_PATTERN) {
+        r.vec(&m->pat.dict);
+        r.vec(&m->pat.uoff);
+        r.vec(&m->pat.pmask);
+        r.pod(&m->pat.words);
+        r.vec(&m->pat.rec);
+    } else if (m->fmt == SPMV_FMT_DELTA) {
+        r.pod(&m->dlt.nslices);
+        r.vec(&m->dlt.dict);
+        r.vec(&m->dlt.hdr);
+        r.vec(&m->dlt.payload);
+    } else {
+        return corrupt("format");
+    }
+    if (!r.ok || r.pos != len) return corrupt("truncated or trailing bytes");
+    m->checksum = checksum_of(*m);
+    if (m->checksum != sum) return corrupt("checksum mismatch");
+    return SPMV_OK;
+}
+
+}  // namespace spmvc

@@ -1,0 +1,480 @@
+// Conjugate gradients on the device: the CG iteration of Table I of
+// arXiv:1612.00530 (Dot, Waxpby, SpMV) without the preconditioner.
+// Every vector and scalar stays in device memory; `check_every` steps are
+// captured in a CUDA graph and replayed, and the host reads one convergence
+// flag per replay.  Reductions use a fixed grid and a fixed tree, so results
+// are the same on every run.
+//
+// Modes: FP64 (all in binary64) and IR_FP32 (iterative refinement: the
+// residual b - A x, its norm and the update x += d in binary64, the inner
+// correction solve A d = r with the binary32 product and binary32 vectors;
+// inner dot products sum 8 products in binary32 and accumulate those chunks
+// in binary64).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "spmvc_internal.h"
+
+namespace spmvc {
+int api_ensure_device(spmv_mat_s* m);
+bool api_valid(spmv_mat_t m);
+
+namespace {
+
+constexpr int kRedBlocks = 304;
+constexpr int kRedThreads = 256;
+
+struct CgState {
+    double rr;          // current r.r (FP64 CG) or inner r.r (IR)
+    double rr0;         // inner: initial r.r
+    double bnorm;
+    double tol;
+    int32_t it;         // steps taken
+    int32_t max_it;
+    int32_t done;
+    int32_t pad;
+};
+
+// Sum of the kRedBlocks partials by one warp in a fixed order.
+__device__ __forceinline__ double sum_partials(const double* __restrict__ p) {
+    double s = 0.0;
+    for (int i = threadIdx.x & 31; i < kRedBlocks; i += 32) s += p[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    return s;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kRedThreads) dot_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                          int64_t n, double* __restrict__ partial,
+                                                          const CgState* __restrict__ st) {
+    if (st && st->done) return;
+    __shared__ double sm[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        s = fma(a[i], b[i], s);
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// alpha = rr / (p.q); x += alpha p; r -= alpha q; partial sums of r.r
+__global__ void __launch_bounds__(kRedThreads) update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                                const double* __restrict__ p,
+                                                                const double* __restrict__ q, int64_t n,
+                                                                const double* __restrict__ partial_pq,
+                                                                double* __restrict__ partial_rr,
+                                                                const CgState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ double sm[32];
+    __shared__ double s_alpha;
+    if (threadIdx.x < 32) {
+        const double pq = sum_partials(partial_pq);
+        if (threadIdx.x == 0) s_alpha = st->rr / pq;
+    }
+    __syncthreads();
+    const double alpha = s_alpha;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        s = fma(ri, ri, s);
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
+}
+
+// beta = rr_new / rr; p = r + beta p
+__global__ void __launch_bounds__(kRedThreads) update_p_kernel(double* __restrict__ p, const double* __restrict__ r,
+                                                               int64_t n, const double* __restrict__ partial_rr,
+                                                               const CgState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ double s_beta;
+    if (threadIdx.x < 32) {
+        const double rr_new = sum_partials(partial_rr);
+        if (threadIdx.x == 0) s_beta = rr_new / st->rr;
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+// rr = rr_new, history, convergence flag (one warp)
+__global__ void finalize_kernel(const double* __restrict__ partial_rr, CgState* __restrict__ st,
+                                double* __restrict__ hist) {
+    if (st->done) return;
+    const double rr_new = sum_partials(partial_rr);
+    if (threadIdx.x == 0) {
+        st->rr = rr_new;
+        st->it += 1;
+        const double rel = sqrt(rr_new) / st->bnorm;
+        hist[st->it] = rel;
+        if (rel <= st->tol || st->it >= st->max_it) st->done = 1;
+    }
+}
+
+// r = b - q, partial sums of r.r
+__global__ void __launch_bounds__(kRedThreads) residual_kernel(const double* __restrict__ b, const double* __restrict__ q,
+                                                               double* __restrict__ r, int64_t n,
+                                                               double* __restrict__ partial) {
+    __shared__ double sm[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double ri = b[i] - q[i];
+        r[i] = ri;
+        s = fma(ri, ri, s);
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void copy_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = src[i];
+}
+
+// ---------------------------------------------------- binary32 inner CG ---
+// chunks of 8 products summed in binary32, chunk sums accumulated in binary64
+__global__ void __launch_bounds__(kRedThreads) dot32_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                                            int64_t n, double* __restrict__ partial,
+                                                            const CgState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ double sm[32];
+    double s = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
+    for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; i0 < n; i0 += stride) {
+        float c = 0.0f;
+        for (int k = 0; k < 8 && i0 + k < n; ++k) c = fmaf(a[i0 + k], b[i0 + k], c);
+        s += double(c);
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads) update_dr32_kernel(float* __restrict__ d, float* __restrict__ r,
+                                                                  const float* __restrict__ p, const float* __restrict__ q,
+                                                                  int64_t n, const double* __restrict__ partial_pq,
+                                                                  double* __restrict__ partial_rr,
+                                                                  const CgState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ double sm[32];
+    __shared__ float s_alpha;
+    if (threadIdx.x < 32) {
+        const double pq = sum_partials(partial_pq);
+        if (threadIdx.x == 0) s_alpha = float(st->rr / pq);
+    }
+    __syncthreads();
+    const float alpha = s_alpha;
+    double s = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
+    for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; i0 < n; i0 += stride) {
+        float c = 0.0f;
+        for (int k = 0; k < 8 && i0 + k < n; ++k) {
+            const int64_t i = i0 + k;
+            d[i] = fmaf(alpha, p[i], d[i]);
+            const float ri = fmaf(-alpha, q[i], r[i]);
+            r[i] = ri;
+            c = fmaf(ri, ri, c);
+        }
+        s += double(c);
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads) update_p32_kernel(float* __restrict__ p, const float* __restrict__ r,
+                                                                 int64_t n, const double* __restrict__ partial_rr,
+                                                                 const CgState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ float s_beta;
+    if (threadIdx.x < 32) {
+        const double rr_new = sum_partials(partial_rr);
+        if (threadIdx.x == 0) s_beta = float(rr_new / st->rr);
+    }
+    __syncthreads();
+    const float beta = s_beta;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        p[i] = fmaf(beta, p[i], r[i]);
+}
+
+__global__ void finalize32_kernel(const double* __restrict__ partial_rr, CgState* __restrict__ st) {
+    if (st->done) return;
+    const double rr_new = sum_partials(partial_rr);
+    if (threadIdx.x == 0) {
+        st->rr = rr_new;
+        st->it += 1;
+        if (sqrt(rr_new / st->rr0) <= st->tol || st->it >= st->max_it) st->done = 1;
+    }
+}
+
+// inner start: r32 = r / |r|, p32 = r32, d32 = 0; partial sums of r32.r32
+__global__ void __launch_bounds__(kRedThreads) inner_start_kernel(const double* __restrict__ r, double inv_norm,
+                                                                  float* __restrict__ r32, float* __restrict__ p32,
+                                                                  float* __restrict__ d32, int64_t n,
+                                                                  double* __restrict__ partial) {
+    __shared__ double sm[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const float v = float(r[i] * inv_norm);
+        r32[i] = v;
+        p32[i] = v;
+        d32[i] = 0.0f;
+        s += double(v) * double(v);
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void inner_init_state_kernel(const double* __restrict__ partial, CgState* __restrict__ st, double inner_tol,
+                                        int inner_max) {
+    const double rr = sum_partials(partial);
+    if (threadIdx.x == 0) {
+        st->rr = rr;
+        st->rr0 = rr;
+        st->tol = inner_tol;
+        st->it = 0;
+        st->max_it = inner_max;
+        st->done = rr > 0.0 ? 0 : 1;
+    }
+}
+
+// x += scale * d32 (binary64)
+__global__ void __launch_bounds__(kRedThreads) ir_update_kernel(double* __restrict__ x, const float* __restrict__ d32,
+                                                                double scale, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        x[i] = fma(scale, double(d32[i]), x[i]);
+}
+
+__global__ void sum_to_host_kernel(const double* __restrict__ partial, double* __restrict__ out) {
+    const double s = sum_partials(partial);
+    if (threadIdx.x == 0) *out = s;
+}
+
+struct Workspace {
+    std::vector<void*> allocs;
+    ~Workspace() { for (void* p : allocs) cudaFree(p); }
+    template <class T> T* get(size_t count) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(16, count * sizeof(T))) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        return static_cast<T*>(p);
+    }
+};
+
+int cuda_err(cudaError_t e, const char* what) {
+    return fail(SPMV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CG_CUDA(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_err(e_, #call); } while (0)
+#define CG_ST(call) do { int s_ = (call); if (s_) return s_; } while (0)
+
+double read_scalar(const double* d, cudaStream_t s) {
+    double h = 0.0;
+    cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    return h;
+}
+
+// Replays `body` (captured `chunk` times) until st->done.
+template <class Body>
+int run_until_done(cudaStream_t s, bool use_graph, int chunk, CgState* d_st, int max_replays, Body&& body) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (use_graph) {
+        CG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int st = SPMV_OK;
+        for (int k = 0; k < chunk && !st; ++k) st = body();
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ge, g, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_err(e, "cudaGraphInstantiate"); }
+    }
+    int32_t done = 0;
+    int rc = SPMV_OK;
+    for (int rep = 0; rep < max_replays && !done; ++rep) {
+        if (use_graph) {
+            cudaError_t e = cudaGraphLaunch(ge, s);
+            if (e != cudaSuccess) { rc = cuda_err(e, "cudaGraphLaunch"); break; }
+        } else {
+            for (int k = 0; k < chunk && !rc; ++k) rc = body();
+            if (rc) break;
+        }
+        cudaError_t e = cudaMemcpyAsync(&done, &d_st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { rc = cuda_err(e, "convergence flag"); break; }
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    return rc;
+}
+
+}  // namespace
+}  // namespace spmvc
+
+using namespace spmvc;
+
+extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts* opts, spmv_cg_result* res) {
+    if (!api_valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    spmv_cg_opts o{1e-10, 10000, SPMV_CG_FP64, 16, 60, 1e-5, 1, 1};
+    if (opts) o = *opts;
+    if (o.tol <= 0) o.tol = 1e-10;
+    if (o.max_iter <= 0) o.max_iter = 10000;
+    if (o.check_every <= 0) o.check_every = 16;
+    if (o.inner_max_iter <= 0) o.inner_max_iter = 60;
+    if (o.inner_tol <= 0) o.inner_tol = 1e-5;
+    if (o.nrhs <= 0) o.nrhs = 1;
+    if (o.nrhs != 1) return fail(SPMV_EUNSUPPORTED, "this build solves one right-hand side per call");
+    if (o.mode != SPMV_CG_FP64 && o.mode != SPMV_CG_IR_FP32) return fail(SPMV_EINVAL, "unknown CG mode");
+    const int64_t n = A->n;
+    if (n > 0 && (!b || !x)) return fail(SPMV_EINVAL, "null vector");
+    if (res) std::memset(res, 0, sizeof(*res));
+    CG_ST(api_ensure_device(A));
+    cudaStream_t s;
+    CG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } guard{s};
+    Workspace ws;
+    double* r = ws.get<double>(n);
+    double* q = ws.get<double>(n);
+    double* p = ws.get<double>(n);
+    double* part_a = ws.get<double>(kRedBlocks);
+    double* part_b = ws.get<double>(kRedBlocks);
+    double* d_scalar = ws.get<double>(1);
+    CgState* d_st = ws.get<CgState>(1);
+    const int hist_cap = o.max_iter + 2;
+    double* d_hist = ws.get<double>(hist_cap);
+    if (!r || !q || !p || !part_a || !part_b || !d_scalar || !d_st || !d_hist) return fail(SPMV_ENOMEM, "CG workspace");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    CG_CUDA(cudaEventRecord(e0, s));
+
+    const unsigned G = kRedBlocks, T = kRedThreads;
+    // b norm and the initial residual r = b - A x
+    dot_kernel<<<G, T, 0, s>>>(b, b, n, part_a, nullptr);
+    sum_to_host_kernel<<<1, 32, 0, s>>>(part_a, d_scalar);
+    const double bnorm = std::sqrt(read_scalar(d_scalar, s));
+    if (!(bnorm > 0.0)) {
+        cudaMemsetAsync(x, 0, sizeof(double) * n, s);  // b == 0: x = 0 is the solution
+        cudaStreamSynchronize(s);
+        if (res) { res->status = SPMV_OK; }
+        return SPMV_OK;
+    }
+    std::vector<double> history;
+    int total_inner = 0, outer = 0;
+    int status = SPMV_ENOTCONVERGED;
+    double rel = 0.0;
+
+    auto true_residual = [&]() -> int {
+        CG_ST(spmv_apply(A, x, q, s));
+        residual_kernel<<<G, T, 0, s>>>(b, q, r, n, part_a);
+        sum_to_host_kernel<<<1, 32, 0, s>>>(part_a, d_scalar);
+        CG_CUDA(cudaGetLastError());
+        return SPMV_OK;
+    };
+
+    if (o.mode == SPMV_CG_FP64) {
+        CG_ST(true_residual());
+        const double rr0 = read_scalar(d_scalar, s);
+        CgState h{rr0, rr0, bnorm, o.tol, 0, o.max_iter, 0, 0};
+        h.done = (std::sqrt(rr0) / bnorm <= o.tol) ? 1 : 0;
+        CG_CUDA(cudaMemcpyAsync(d_st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+        const double h0 = std::sqrt(rr0) / bnorm;
+        CG_CUDA(cudaMemcpyAsync(d_hist, &h0, sizeof(double), cudaMemcpyHostToDevice, s));
+        copy_kernel<<<G, T, 0, s>>>(p, r, n);
+        auto body = [&]() -> int {
+            CG_ST(spmv_apply(A, p, q, s));
+            dot_kernel<<<G, T, 0, s>>>(p, q, n, part_a, d_st);
+            update_xr_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_a, part_b, d_st);
+            update_p_kernel<<<G, T, 0, s>>>(p, r, n, part_b, d_st);
+            finalize_kernel<<<1, 32, 0, s>>>(part_b, d_st, d_hist);
+            CG_CUDA(cudaGetLastError());
+            return SPMV_OK;
+        };
+        const int replays = (o.max_iter + o.check_every - 1) / o.check_every + 1;
+        CG_ST(run_until_done(s, o.use_graph != 0, o.check_every, d_st, replays, body));
+        CG_CUDA(cudaMemcpyAsync(&h, d_st, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CG_CUDA(cudaStreamSynchronize(s));
+        history.resize(h.it + 1);
+        CG_CUDA(cudaMemcpy(history.data(), d_hist, sizeof(double) * (h.it + 1), cudaMemcpyDeviceToHost));
+        total_inner = h.it;
+        CG_ST(true_residual());
+        rel = std::sqrt(read_scalar(d_scalar, s)) / bnorm;
+        status = rel <= o.tol * 10.0 || history.back() <= o.tol ? SPMV_OK : SPMV_ENOTCONVERGED;
+    } else {
+        float* r32 = ws.get<float>(n);
+        float* p32 = ws.get<float>(n);
+        float* q32 = ws.get<float>(n);
+        float* d32 = ws.get<float>(n);
+        if (!r32 || !p32 || !q32 || !d32) return fail(SPMV_ENOMEM, "IR workspace");
+        CG_CUDA(cudaMemsetAsync(p32, 0, sizeof(float) * n, s));
+        CG_ST(spmv_apply_f32(A, p32, q32, s));  // first binary32 call may allocate: keep it out of capture
+        for (;;) {
+            CG_ST(true_residual());
+            const double rr = read_scalar(d_scalar, s);
+            rel = std::sqrt(rr) / bnorm;
+            history.push_back(rel);
+            if (rel <= o.tol) { status = SPMV_OK; break; }
+            if (total_inner >= o.max_iter) break;
+            const double rnorm = std::sqrt(rr);
+            inner_start_kernel<<<G, T, 0, s>>>(r, 1.0 / rnorm, r32, p32, d32, n, part_a);
+            inner_init_state_kernel<<<1, 32, 0, s>>>(part_a, d_st, o.inner_tol,
+                                                     std::min(o.inner_max_iter, o.max_iter - total_inner));
+            auto body = [&]() -> int {
+                CG_ST(spmv_apply_f32(A, p32, q32, s));
+                dot32_kernel<<<G, T, 0, s>>>(p32, q32, n, part_a, d_st);
+                update_dr32_kernel<<<G, T, 0, s>>>(d32, r32, p32, q32, n, part_a, part_b, d_st);
+                update_p32_kernel<<<G, T, 0, s>>>(p32, r32, n, part_b, d_st);
+                finalize32_kernel<<<1, 32, 0, s>>>(part_b, d_st);
+                CG_CUDA(cudaGetLastError());
+                return SPMV_OK;
+            };
+            const int replays = (o.inner_max_iter + o.check_every - 1) / o.check_every + 1;
+            CG_ST(run_until_done(s, o.use_graph != 0, o.check_every, d_st, replays, body));
+            CgState h;
+            CG_CUDA(cudaMemcpyAsync(&h, d_st, sizeof(h), cudaMemcpyDeviceToHost, s));
+            CG_CUDA(cudaStreamSynchronize(s));
+            total_inner += h.it;
+            ir_update_kernel<<<G, T, 0, s>>>(x, d32, rnorm, n);
+            ++outer;
+            if (h.it == 0) break;
+        }
+    }
+    CG_CUDA(cudaEventRecord(e1, s));
+    CG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (res) {
+        res->status = status;
+        res->iterations = total_inner;
+        res->outer_iterations = outer;
+        res->rel_residual = rel;
+        res->seconds = ms * 1e-3;
+        res->history_len = static_cast<int32_t>(history.size());
+        res->history = static_cast<double*>(std::malloc(sizeof(double) * std::max<size_t>(1, history.size())));
+        if (!res->history) return fail(SPMV_ENOMEM, "history allocation");
+        std::memcpy(res->history, history.data(), sizeof(double) * history.size());
+    }
+    return status;
+}
+
+extern "C" int spmv_cg_result_free(spmv_cg_result* res) {
+    if (!res) return SPMV_OK;
+    std::free(res->history);
+    res->history = nullptr;
+    res->history_len = 0;
+    return SPMV_OK;
+}

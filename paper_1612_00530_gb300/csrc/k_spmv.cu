@@ -1,0 +1,533 @@
+// SpMV kernels for sm_103a: y = A x (Eq. 1 of arXiv:1612.00530) over the
+// library's three stored forms.  None of this is a dense contraction, so
+// tensor cores are not used; the kernels stream the matrix once with
+// coalesced, vectorised loads (evict-first), keep x in L2, and decode value
+// codes and column patterns in registers and shared memory.
+//
+// Two summation orders:
+//  - COLUMN: y_i = fma(a_ij, x_j, y_i) over ascending j from 0, exactly the
+//    CPU CSR product, so results are bit-identical.  On GB300 the FP64 pipe
+//    issues about 2 fma per clock per SM, which bounds these kernels.
+//  - FAST (pattern format, integer-valued value tables): x is turned into
+//    53-bit fixed point by integer bit manipulation, every row is summed
+//    exactly with 32x32->64-bit integer multiply-adds, and one rounding to
+//    nearest makes the double result -- no FP64 instruction per nonzero.
+#include <cstdint>
+
+#include "spmvc_internal.h"
+
+namespace spmvc {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kXmaxBlocks = 152;  // partial maxima written by the pre-pass
+
+__device__ __forceinline__ void raise_error(int32_t* err, int32_t code) {
+    if (err) atomicOr(err, code);
+}
+
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[kMaxRecordWords], int u) {
+    return (w[u >> 2] >> (8 * (u & 3))) & 0xFFu;
+}
+
+// Row record of the pattern format: `WORDS` 32-bit words split over up to
+// three planes indexed by row, so each warp load is one contiguous run.
+template <int WORDS>
+__device__ __forceinline__ void load_record(const PatternView& a, int64_t r, uint32_t (&w)[kMaxRecordWords]) {
+    constexpr int q16 = WORDS / 4, rem = WORDS % 4;
+    if (q16 >= 1) {
+        const uint4 v = __ldcs(a.p16a + r);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+    if (q16 >= 2) {
+        const uint4 v = __ldcs(a.p16b + r);
+        w[4] = v.x; w[5] = v.y; w[6] = v.z; w[7] = v.w;
+    }
+    if (rem >= 2) {
+        const uint2 v = __ldcs(a.p8 + r);
+        w[4 * q16] = v.x; w[4 * q16 + 1] = v.y;
+    }
+    if (rem & 1) w[WORDS - 1] = __ldcs(a.p4 + r);
+}
+
+// ------------------------------------------------------------- ELL -------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) ell_kernel(EllView a, const T* __restrict__ x, T* __restrict__ y) {
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    const int64_t s = r >> 5;
+    const int64_t base = a.slice_off[s] + (r & 31);
+    const int w = a.slice_w[s];
+    T acc = T(0);
+#pragma unroll 9
+    for (int t = 0; t < w; ++t) {
+        const int32_t c = __ldcs(a.col + base + 32 * t);
+        T v;
+        if constexpr (sizeof(T) == 8) v = __ldcs(a.val + base + 32 * t);
+        else v = __ldcs(a.val32 + base + 32 * t);
+        if (c >= 0) acc = fma(v, __ldg(x + c), acc);
+    }
+    y[r] = acc;
+}
+
+// ------------------------------------------------ pattern, COLUMN order ---
+template <int WORDS, typename T>
+__global__ void __launch_bounds__(kBlock) pattern_col_kernel(PatternView a, const T* __restrict__ x,
+                                                             T* __restrict__ y) {
+    __shared__ T sdict[256];
+    __shared__ uint32_t smask[32];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        T v = T(0);
+        if (i < a.dict_size) {
+            if constexpr (sizeof(T) == 8) v = a.dict[i];
+            else v = a.dict32[i];
+        }
+        sdict[i] = v;
+    }
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    __syncthreads();
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    const uint32_t pat = byte_of(w, a.nu);
+    if (pat >= uint32_t(a.npat)) raise_error(a.err, 1);
+    const uint32_t mask = smask[pat & 31];
+    T acc = T(0);
+#pragma unroll
+    for (int u = 0; u < 4 * WORDS - 1; ++u) {
+        if (u < a.nu && ((mask >> u) & 1u)) {
+            const uint32_t code = byte_of(w, u);
+            const int64_t c = r + a.uoff[u];
+            if (code >= uint32_t(a.dict_size) || uint64_t(c) >= uint64_t(a.n)) {
+                raise_error(a.err, 2);
+                continue;
+            }
+            acc = fma(sdict[code], __ldg(x + c), acc);
+        }
+    }
+    y[r] = acc;
+}
+
+// ---------------------------------------------------- FAST order ---------
+// max over x of the high word with the sign cleared: its exponent field is
+// the largest biased exponent E of any x_j.  One partial per block; the
+// SpMV kernel reduces the partials itself, so no reset or atomic is needed.
+__global__ void __launch_bounds__(1024) xmax_kernel(const double* __restrict__ x, int64_t n,
+                                                    uint32_t* __restrict__ partial) {
+    uint32_t m = 0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride)
+        m = max(m, uint32_t(__double2hiint(__ldg(x + i))) & 0x7FFFFFFFu);
+    m = __reduce_max_sync(0xFFFFFFFFu, m);
+    __shared__ uint32_t sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0u;
+        v = __reduce_max_sync(0xFFFFFFFFu, v);
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+}
+
+__device__ __forceinline__ int block_emax(const uint32_t* __restrict__ partial, int* s_emax) {
+    if (threadIdx.x < 32) {
+        uint32_t v = 0;
+        for (int i = threadIdx.x; i < kXmaxBlocks; i += 32) v = max(v, __ldg(partial + i));
+        v = __reduce_max_sync(0xFFFFFFFFu, v);
+        if (threadIdx.x == 0) *s_emax = int(v >> 20);
+    }
+    __syncthreads();
+    return *s_emax;
+}
+
+// x -> X = sign(x) * floor(|x| * 2^(1075 - E)) as two limbs X = xh*2^26 + xl
+// (both carrying the sign), integer operations only.
+__device__ __forceinline__ void to_fixed(double xv, int emax, int32_t& xh, int32_t& xl) {
+    const uint32_t hi = uint32_t(__double2hiint(xv)), lo = uint32_t(__double2loint(xv));
+    const uint32_t k = uint32_t(emax) - ((hi >> 20) & 0x7FFu);
+    const uint64_t mant = (uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+    uint64_t X;
+    asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"(mant), "r"(k));  // shifts >= 64 give 0
+    const int32_t sgn = int32_t(hi) >> 31;
+    xl = (int32_t(uint32_t(X) & 0x3FFFFFFu) ^ sgn) - sgn;
+    xh = (int32_t(X >> 26) ^ sgn) - sgn;
+}
+
+// acc * 2^S rounded to nearest-even, integer operations only (exponent out
+// of the normal range takes an FP64 detour).
+__device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
+    if (acc == 0) return 0.0;
+    const uint64_t sgn = acc < 0 ? 0x8000000000000000ull : 0ull;
+    uint64_t a = acc < 0 ? uint64_t(0) - uint64_t(acc) : uint64_t(acc);
+    const int lz = __clzll(a);
+    a <<= lz;
+    uint64_t mant = a >> 11;
+    const uint32_t rest = uint32_t(a) & 0x7FFu;
+    mant += (rest > 0x400u || (rest == 0x400u && (mant & 1u))) ? 1u : 0u;
+    int e = 63 - lz + S + 1023;
+    if (mant >> 53) {
+        mant >>= 1;
+        ++e;
+    }
+    if (e <= 0 || e >= 2047) return scalbn(__ll2double_rn(acc), S);
+    return __longlong_as_double(int64_t(sgn | (uint64_t(e) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+template <int WORDS>
+__global__ void __launch_bounds__(kBlock) pattern_fast_kernel(PatternView a, const double* __restrict__ x,
+                                                              double* __restrict__ y,
+                                                              const uint32_t* __restrict__ partial) {
+    __shared__ uint32_t smask[32];
+    __shared__ double sdict[8];
+    __shared__ int s_emax;
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    if (threadIdx.x < 8) sdict[threadIdx.x] = threadIdx.x < a.dict_size ? a.dict[threadIdx.x] : 0.0;
+    const int emax = block_emax(partial, &s_emax);
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    const uint32_t pat = byte_of(w, a.nu);
+    if (pat >= uint32_t(a.npat)) raise_error(a.err, 1);
+    const uint32_t mask = smask[pat & 31];
+    if (emax < 64 || emax >= 2047) {
+        // zero/denormal-only or non-finite x: the COLUMN order, same result rules as IEEE
+        double acc = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4 * WORDS - 1; ++u)
+            if (u < a.nu && ((mask >> u) & 1u)) {
+                const uint32_t code = byte_of(w, u);
+                const int64_t c = r + a.uoff[u];
+                if (code < uint32_t(a.dict_size) && uint64_t(c) < uint64_t(a.n))
+                    acc = fma(sdict[code & 7], __ldg(x + c), acc);
+            }
+        y[r] = acc;
+        return;
+    }
+    int64_t acc_h = 0, acc_l = 0;
+#pragma unroll
+    for (int u = 0; u < 4 * WORDS - 1; ++u) {
+        if (u < a.nu) {
+            const uint32_t code = byte_of(w, u);
+            // multiplier of the code, sign-extended; absent slots map to 0
+            const int32_t m = int32_t(__byte_perm(a.mult_lo, a.mult_hi, (code & 7u) * 0x1111u + 0x8880u));
+            const int64_t c = r + a.uoff[u];
+            const bool inside = uint64_t(c) < uint64_t(a.n);
+            const double xv = __ldg(x + (inside ? c : r));
+            int32_t xh, xl;
+            to_fixed(xv, emax, xh, xl);
+            const int32_t mm = ((mask >> u) & 1u) ? m : 0;
+            acc_h += int64_t(mm) * xh;
+            acc_l += int64_t(mm) * xl;
+        }
+    }
+    const int64_t acc = acc_h * (int64_t(1) << 26) + acc_l;
+    y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+}
+
+// ------------------------------------------------------------ delta ------
+template <typename T, bool CRAW, bool VRAW>
+__device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, uint32_t w, int64_t r, int l,
+                                       int len, const T* sdict, const T* __restrict__ x) {
+    const uint8_t* cols = base + 32;
+    const uint8_t* vals = base + ((32 + uint64_t(w) * 32 * (CRAW ? 4 : 2) + 15) & ~uint64_t(15));
+    T acc = T(0);
+    for (int t = 0; t < len; ++t) {
+        const int64_t slot = int64_t(t) * 32 + l;
+        int64_t c;
+        if constexpr (CRAW) c = __ldcs(reinterpret_cast<const int32_t*>(cols) + slot);
+        else c = r + __ldcs(reinterpret_cast<const int16_t*>(cols) + slot);
+        T v;
+        if constexpr (VRAW) v = T(__ldcs(reinterpret_cast<const double*>(vals) + slot));
+        else {
+            const uint32_t code = __ldcs(vals + slot);
+            if (code >= uint32_t(a.dict_size)) { raise_error(a.err, 2); continue; }
+            v = sdict[code];
+        }
+        if (uint64_t(c) >= uint64_t(a.n)) { raise_error(a.err, 2); continue; }
+        acc = fma(v, __ldg(x + c), acc);
+    }
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __restrict__ x, T* __restrict__ y) {
+    __shared__ T sdict[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        T v = T(0);
+        if (i < a.dict_size) {
+            if constexpr (sizeof(T) == 8) v = a.dict[i];
+            else v = a.dict32[i];
+        }
+        sdict[i] = v;
+    }
+    __syncthreads();
+    const int64_t s = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+    const int l = threadIdx.x & 31;
+    if (s >= a.nslices) return;
+    const DeltaSlice h = a.hdr[s];
+    const uint8_t* base = a.payload + h.off;
+    const int64_t r = s * 32 + l;
+    int len = r < a.n ? int(base[l]) : 0;
+    if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
+    T acc;
+    const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
+    if (craw) acc = vraw ? delta_row<T, true, true>(a, base, h.w, r, l, len, sdict, x)
+                         : delta_row<T, true, false>(a, base, h.w, r, l, len, sdict, x);
+    else acc = vraw ? delta_row<T, false, true>(a, base, h.w, r, l, len, sdict, x)
+                    : delta_row<T, false, false>(a, base, h.w, r, l, len, sdict, x);
+    if (r < a.n) y[r] = acc;
+}
+
+// ------------------------------------------------------------ SpMM -------
+// Y = A X, X and Y row-major n x k.  One thread per (row, column) pair,
+// column fastest, so X rows are read as contiguous runs.
+template <int WORDS>
+__global__ void __launch_bounds__(kBlock) pattern_spmm_col_kernel(PatternView a, int k, const double* __restrict__ X,
+                                                                  int64_t ldx, double* __restrict__ Y, int64_t ldy) {
+    __shared__ double sdict[256];
+    __shared__ uint32_t smask[32];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sdict[i] = i < a.dict_size ? a.dict[i] : 0.0;
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    __syncthreads();
+    const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t r = idx / k;
+    const int j = int(idx - r * k);
+    if (r >= a.n) return;
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    const uint32_t pat = byte_of(w, a.nu);
+    const uint32_t mask = smask[pat & 31];
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4 * WORDS - 1; ++u)
+        if (u < a.nu && ((mask >> u) & 1u)) {
+            const uint32_t code = byte_of(w, u);
+            const int64_t c = r + a.uoff[u];
+            if (code >= uint32_t(a.dict_size) || uint64_t(c) >= uint64_t(a.n)) { raise_error(a.err, 2); continue; }
+            acc = fma(sdict[code], __ldg(X + c * ldx + j), acc);
+        }
+    Y[r * ldy + j] = acc;
+}
+
+// per-column partial maxima: partial[b * k + j]
+__global__ void __launch_bounds__(256) xmax_cols_kernel(const double* __restrict__ X, int64_t n, int k, int64_t ldx,
+                                                        uint32_t* __restrict__ partial) {
+    // block b handles rows b, b + G, ...; thread t handles column t % k of row group t / k
+    const int j = threadIdx.x % k, sub = threadIdx.x / k, nsub = blockDim.x / k;
+    uint32_t m = 0;
+    if (sub < nsub)
+        for (int64_t r = blockIdx.x * int64_t(nsub) + sub; r < n; r += int64_t(gridDim.x) * nsub)
+            m = max(m, uint32_t(__double2hiint(__ldg(X + r * ldx + j))) & 0x7FFFFFFFu);
+    __shared__ uint32_t sm[256];
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        uint32_t v = 0;
+        for (int s2 = 0; s2 < nsub; ++s2) v = max(v, sm[s2 * k + threadIdx.x]);
+        partial[blockIdx.x * k + threadIdx.x] = v;
+    }
+}
+
+template <int WORDS>
+__global__ void __launch_bounds__(kBlock) pattern_spmm_fast_kernel(PatternView a, int k, const double* __restrict__ X,
+                                                                   int64_t ldx, double* __restrict__ Y, int64_t ldy,
+                                                                   const uint32_t* __restrict__ partial) {
+    __shared__ uint32_t smask[32];
+    __shared__ double sdict[8];
+    __shared__ int s_emax[64];
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    if (threadIdx.x < 8) sdict[threadIdx.x] = threadIdx.x < a.dict_size ? a.dict[threadIdx.x] : 0.0;
+    if (threadIdx.x < k) {
+        uint32_t v = 0;
+        for (int b = 0; b < kXmaxBlocks; ++b) v = max(v, __ldg(partial + b * k + threadIdx.x));
+        s_emax[threadIdx.x] = int(v >> 20);
+    }
+    __syncthreads();
+    const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t r = idx / k;
+    const int j = int(idx - r * k);
+    if (r >= a.n) return;
+    const int emax = s_emax[j];
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    const uint32_t pat = byte_of(w, a.nu);
+    const uint32_t mask = smask[pat & 31];
+    if (emax < 64 || emax >= 2047) {
+        double acc = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4 * WORDS - 1; ++u)
+            if (u < a.nu && ((mask >> u) & 1u)) {
+                const uint32_t code = byte_of(w, u);
+                const int64_t c = r + a.uoff[u];
+                if (code < uint32_t(a.dict_size) && uint64_t(c) < uint64_t(a.n))
+                    acc = fma(sdict[code & 7], __ldg(X + c * ldx + j), acc);
+            }
+        Y[r * ldy + j] = acc;
+        return;
+    }
+    int64_t acc_h = 0, acc_l = 0;
+#pragma unroll
+    for (int u = 0; u < 4 * WORDS - 1; ++u)
+        if (u < a.nu) {
+            const uint32_t code = byte_of(w, u);
+            const int32_t m = int32_t(__byte_perm(a.mult_lo, a.mult_hi, (code & 7u) * 0x1111u + 0x8880u));
+            const int64_t c = r + a.uoff[u];
+            const bool inside = uint64_t(c) < uint64_t(a.n);
+            int32_t xh, xl;
+            to_fixed(__ldg(X + (inside ? c : r) * ldx + j), emax, xh, xl);
+            const int32_t mm = ((mask >> u) & 1u) ? m : 0;
+            acc_h += int64_t(mm) * xh;
+            acc_l += int64_t(mm) * xl;
+        }
+    Y[r * ldy + j] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, emax - 1075 + a.mult_exp);
+}
+
+__global__ void __launch_bounds__(kBlock) ell_spmm_kernel(EllView a, int k, const double* __restrict__ X, int64_t ldx,
+                                                          double* __restrict__ Y, int64_t ldy) {
+    const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t r = idx / k;
+    const int j = int(idx - r * k);
+    if (r >= a.n) return;
+    const int64_t s = r >> 5;
+    const int64_t base = a.slice_off[s] + (r & 31);
+    const int w = a.slice_w[s];
+    double acc = 0.0;
+    for (int t = 0; t < w; ++t) {
+        const int32_t c = __ldg(a.col + base + 32 * t);
+        if (c >= 0) acc = fma(__ldg(a.val + base + 32 * t), __ldg(X + int64_t(c) * ldx + j), acc);
+    }
+    Y[r * ldy + j] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock) delta_spmm_kernel(DeltaView a, int k, const double* __restrict__ X,
+                                                            int64_t ldx, double* __restrict__ Y, int64_t ldy) {
+    const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t r = idx / k;
+    const int j = int(idx - r * k);
+    if (r >= a.n) return;
+    const int64_t s = r >> 5;
+    const int l = int(r & 31);
+    const DeltaSlice h = a.hdr[s];
+    const uint8_t* base = a.payload + h.off;
+    const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
+    const uint8_t* cols = base + 32;
+    const uint8_t* vals = base + ((32 + uint64_t(h.w) * 32 * (craw ? 4 : 2) + 15) & ~uint64_t(15));
+    int len = base[l];
+    if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
+    double acc = 0.0;
+    for (int t = 0; t < len; ++t) {
+        const int64_t slot = int64_t(t) * 32 + l;
+        const int64_t c = craw ? int64_t(reinterpret_cast<const int32_t*>(cols)[slot])
+                               : r + reinterpret_cast<const int16_t*>(cols)[slot];
+        double v;
+        if (vraw) v = reinterpret_cast<const double*>(vals)[slot];
+        else {
+            const uint32_t code = vals[slot];
+            if (code >= uint32_t(a.dict_size)) { raise_error(a.err, 2); continue; }
+            v = a.dict[code];
+        }
+        if (uint64_t(c) >= uint64_t(a.n)) { raise_error(a.err, 2); continue; }
+        acc = fma(v, __ldg(X + c * ldx + j), acc);
+    }
+    Y[r * ldy + j] = acc;
+}
+
+__global__ void fill_u32_kernel(uint32_t* p, uint32_t v, int64_t n) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+unsigned grid_of(int64_t threads) { return unsigned((threads + kBlock - 1) / kBlock); }
+
+
+}  // namespace
+
+// --------------------------------------------------------- launchers -----
+#define SPMVC_DISPATCH_WORDS(WORDS_VAL, CALL)                     \
+    switch (WORDS_VAL) {                                          \
+        case 1: { constexpr int W = 1; CALL; } break;             \
+        case 2: { constexpr int W = 2; CALL; } break;             \
+        case 3: { constexpr int W = 3; CALL; } break;             \
+        case 4: { constexpr int W = 4; CALL; } break;             \
+        case 5: { constexpr int W = 5; CALL; } break;             \
+        case 6: { constexpr int W = 6; CALL; } break;             \
+        case 7: { constexpr int W = 7; CALL; } break;             \
+        case 8: { constexpr int W = 8; CALL; } break;             \
+        default: return cudaErrorInvalidValue;                    \
+    }
+
+cudaError_t launch_ell_f64(const EllView& a, const double* x, double* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    ell_kernel<double><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+cudaError_t launch_ell_f32(const EllView& a, const float* x, float* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    ell_kernel<float><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+cudaError_t launch_pattern_col_f64(const PatternView& a, const double* x, double* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    SPMVC_DISPATCH_WORDS(a.words, (pattern_col_kernel<W, double><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y)));
+    return cudaGetLastError();
+}
+cudaError_t launch_pattern_col_f32(const PatternView& a, const float* x, float* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    SPMVC_DISPATCH_WORDS(a.words, (pattern_col_kernel<W, float><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y)));
+    return cudaGetLastError();
+}
+cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, double* y, uint32_t* partial,
+                                    cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    xmax_kernel<<<kXmaxBlocks, 1024, 0, s>>>(x, a.n, partial);
+    SPMVC_DISPATCH_WORDS(a.words, (pattern_fast_kernel<W><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y, partial)));
+    return cudaGetLastError();
+}
+cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    delta_kernel<double><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    delta_kernel<float><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+cudaError_t launch_pattern_spmm_col(const PatternView& a, int k, const double* X, int64_t ldx, double* Y,
+                                    int64_t ldy, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    SPMVC_DISPATCH_WORDS(a.words,
+                         (pattern_spmm_col_kernel<W><<<grid_of(a.n * k), kBlock, 0, s>>>(a, k, X, ldx, Y, ldy)));
+    return cudaGetLastError();
+}
+cudaError_t launch_pattern_spmm_fast(const PatternView& a, int k, const double* X, int64_t ldx, double* Y,
+                                     int64_t ldy, uint32_t* partial, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (k > 64) return cudaErrorInvalidValue;
+    xmax_cols_kernel<<<kXmaxBlocks, 256, 0, s>>>(X, a.n, k, ldx, partial);
+    SPMVC_DISPATCH_WORDS(a.words, (pattern_spmm_fast_kernel<W><<<grid_of(a.n * k), kBlock, 0, s>>>(
+                                      a, k, X, ldx, Y, ldy, partial)));
+    return cudaGetLastError();
+}
+cudaError_t launch_ell_spmm(const EllView& a, int k, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                            cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    ell_spmm_kernel<<<grid_of(a.n * k), kBlock, 0, s>>>(a, k, X, ldx, Y, ldy);
+    return cudaGetLastError();
+}
+cudaError_t launch_delta_spmm(const DeltaView& a, int k, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                              cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    delta_spmm_kernel<<<grid_of(a.n * k), kBlock, 0, s>>>(a, k, X, ldx, Y, ldy);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    fill_u32_kernel<<<grid_of(n), kBlock, 0, s>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+}  // namespace spmvc

@@ -1,0 +1,187 @@
+// Internal declarations shared by the library's translation units: host-side
+// formats (generation, compression, decompression), device views of each
+// format, and the kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "spmvc.h"
+
+namespace spmvc {
+
+constexpr int kSliceRows = 32;      // rows per slice (one warp)
+constexpr int kMaxUnion = 31;       // union of displacements, pattern format
+constexpr int kMaxPatterns = 32;    // 5-bit pattern numbers
+constexpr int kMaxRecordWords = 8;  // 32-byte row records at most
+constexpr int kMaxFastDict = 7;     // codes 0..6 plus the absent-slot code
+
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+
+// ---------------------------------------------------------------- CSR ----
+struct Csr {
+    int64_t n = 0;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    int64_t nnz() const { return rowptr.empty() ? 0 : rowptr.back(); }
+};
+
+// Generators (Sec. III-A and its irregular variant).
+int generate_hpcg(int nx, int ny, int nz, Csr* out);
+int generate_irregular(const spmv_gen_desc& d, Csr* out);
+// Structural validation of caller CSR.
+int validate_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val);
+
+// ---------------------------------------------------------------- ELL ----
+// Slices of 32 rows, slot-major inside a slice: entry t of row 32s+l is at
+// slice_off[s] + 32*t + l.  Padding slots hold column -1.
+struct EllFormat {
+    int64_t nslices = 0;
+    std::vector<int64_t> slice_off;  // nslices + 1, in entries
+    std::vector<int32_t> slice_w;    // slots per row in the slice
+    std::vector<double> val;
+    std::vector<int32_t> col;
+};
+int pack_ell(const Csr& a, EllFormat* out);
+
+// ------------------------------------------------------------ pattern ----
+// One record of `words` 32-bit words per row: byte u (u < nu) is the value
+// code of union slot u (code = dict index; dict.size() marks an absent
+// slot), byte nu is the row's pattern number, the rest is zero.
+struct PatternFormat {
+    std::vector<double> dict;       // value table, ascending
+    std::vector<int32_t> uoff;      // union displacements, ascending
+    std::vector<uint32_t> pmask;    // per pattern: bit u set if slot u present
+    int words = 0;
+    std::vector<uint32_t> rec;      // n * words
+    // exact fixed-point order: dict[v] = mult[v] * 2^mult_exp
+    bool fast_ok = false;
+    int mult_exp = 0;
+    std::vector<int32_t> mult;
+    int64_t max_row_abs = 0;        // max over rows of sum |mult|
+};
+int compress_pattern(const Csr& a, int max_dict, PatternFormat* out);
+void derive_fast_order(int64_t n, PatternFormat* p);
+
+// -------------------------------------------------------------- delta ----
+enum : uint32_t { kSliceValRaw = 1u, kSliceColRaw = 2u };
+struct DeltaSlice {                 // 16 bytes, one per 32-row slice
+    uint64_t off;                   // byte offset of the slice payload
+    uint32_t w;                     // slots per row
+    uint32_t flags;                 // kSliceValRaw | kSliceColRaw
+};
+// Slice payload (each part 16-byte aligned): row lengths uint8[32]; columns
+// (int16 delta col-row, or int32) [w][32]; values (uint8 code, or double)
+// [w][32].
+struct DeltaFormat {
+    std::vector<double> dict;
+    int64_t nslices = 0;
+    std::vector<DeltaSlice> hdr;
+    std::vector<uint8_t> payload;
+};
+int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out);
+
+// --------------------------------------------------------- device views --
+struct EllView {
+    int64_t n, nslices;
+    const int64_t* slice_off;
+    const int32_t* slice_w;
+    const double* val;
+    const float* val32;
+    const int32_t* col;
+};
+
+struct PatternView {
+    int64_t n;
+    int32_t nu, words, dict_size, npat;
+    int32_t uoff[32];
+    uint32_t pmask[32];
+    const uint4* p16a;              // words 0..3
+    const uint4* p16b;              // words 4..7 (words == 8)
+    const uint2* p8;                // words 4..5 (words 6,7)
+    const uint32_t* p4;             // last odd word
+    const double* dict;             // device copy of the value table
+    const float* dict32;
+    uint32_t mult_lo, mult_hi;      // fast order: int8 multipliers, absent -> 0
+    int32_t mult_exp;
+    int32_t* err;                   // sticky device error word
+};
+
+struct DeltaView {
+    int64_t n, nslices;
+    const DeltaSlice* hdr;
+    const uint8_t* payload;
+    const double* dict;
+    const float* dict32;
+    int32_t dict_size;
+    int32_t* err;
+};
+
+// Kernel launchers (k_spmv.cu).
+cudaError_t launch_ell_f64(const EllView& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_ell_f32(const EllView& a, const float* x, float* y, cudaStream_t s);
+cudaError_t launch_pattern_col_f64(const PatternView& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_pattern_col_f32(const PatternView& a, const float* x, float* y, cudaStream_t s);
+cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, double* y,
+                                    uint32_t* xmax_word, cudaStream_t s);
+cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s);
+// SpMM (k right-hand sides, row-major).
+cudaError_t launch_pattern_spmm_col(const PatternView& a, int k, const double* X, int64_t ldx,
+                                    double* Y, int64_t ldy, cudaStream_t s);
+cudaError_t launch_pattern_spmm_fast(const PatternView& a, int k, const double* X, int64_t ldx,
+                                     double* Y, int64_t ldy, uint32_t* xmax_words, cudaStream_t s);
+cudaError_t launch_ell_spmm(const EllView& a, int k, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, cudaStream_t s);
+cudaError_t launch_delta_spmm(const DeltaView& a, int k, const double* X, int64_t ldx, double* Y,
+                              int64_t ldy, cudaStream_t s);
+
+// Ragged batch (k_batch.cu): one work item = rows [r0, r1) of matrix m.
+struct BatchItem {
+    int32_t m;
+    int32_t pad;
+    int64_t r0, r1;
+};
+cudaError_t launch_pattern_batch(const PatternView* mats_dev, const double* const* xs_dev,
+                                 double* const* ys_dev, const BatchItem* items, int64_t nitems,
+                                 uint32_t* counter, int words, int grid, cudaStream_t s);
+
+// Utility kernels.
+cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, int64_t n, cudaStream_t s);
+
+}  // namespace spmvc
+
+// ------------------------------------------------------------ the handle --
+struct spmv_mat_s {
+    uint32_t magic = 0;
+    int32_t fmt = 0;
+    int32_t order = SPMV_ORDER_COLUMN;
+    int64_t n = 0, nnz = 0;
+    int32_t max_row_nnz = 0;
+    spmvc::Csr csr;                     // plain handles keep the CSR
+    spmvc::EllFormat ell;
+    spmvc::PatternFormat pat;
+    spmvc::DeltaFormat dlt;
+    uint64_t checksum = 0;
+
+    // device side (allocated on first use)
+    int device = -1;
+    std::vector<void*> dev_allocs;
+    spmvc::EllView ell_view{};
+    spmvc::PatternView pat_view{};
+    spmvc::DeltaView dlt_view{};
+    int32_t* d_err = nullptr;
+    uint32_t* d_scratch_words = nullptr; // fast order: per-column max |x| words
+    int64_t scratch_words = 0;
+    // spmv_apply_host staging
+    double* d_hx = nullptr;
+    double* d_hy = nullptr;
+    cudaStream_t own_stream = nullptr;
+    float* d_ell_val32 = nullptr;
+};

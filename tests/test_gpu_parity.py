@@ -1,0 +1,279 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+COLUMN order (ELL, pattern, delta; binary64 and binary32) must match the
+oracle bit for bit.  FAST order must stay within 1e-14 of it, normwise
+(|dy|_inf / |y|_inf) and componentwise (|dy_i| / sum_j |a_ij x_j|), and be
+bit-exact for integer x (every partial sum is then exact).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import spmv_inputs
+
+torch = pytest.importorskip("torch")
+import paper_1612_00530_gb300 as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-14
+GRIDS = [(1, 1, 1), (2, 3, 5), (4, 4, 4), (5, 7, 3), (8, 8, 8), (17, 17, 17), (33, 9, 5), (32, 32, 32)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
+
+
+def run(M, x_np):
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
+    y = torch.full_like(x, float("nan"))
+    P.spmv_apply(M, x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def abs_row_sums(rowptr, col, val, x):
+    return oracle.spmv(rowptr, col, np.abs(val), np.abs(x))
+
+
+def check_fast(y, y_ref, scale):
+    d = np.abs(y - y_ref)
+    assert np.max(d) <= TOL * max(np.max(np.abs(y_ref)), 1e-300)
+    nz = scale > 0
+    assert np.all(d[~nz] == 0)
+    assert np.max(d[nz] / scale[nz], initial=0.0) <= TOL
+
+
+@pytest.mark.parametrize("g", GRIDS)
+def test_hpcg_all_formats(g):
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    A = P.spmv_build("hpcg", *g)
+    Cp = P.spmv_compress(A, format="pattern")
+    Cd = P.spmv_compress(A, format="delta", min_count=1)
+    for seed in (0, 1):
+        x = spmv_inputs.uniform_vector(n, seed=seed)
+        y_ref = oracle.spmv(rowptr, col, val, x)
+        for M in (A, Cp, Cd):
+            assert np.array_equal(run(M, x), y_ref)
+        P.spmv_set_order(Cp, "fast")
+        check_fast(run(Cp, x), y_ref, abs_row_sums(rowptr, col, val, x))
+        xi = spmv_inputs.integer_vector(n, seed=seed)
+        assert np.array_equal(run(Cp, xi), oracle.spmv(rowptr, col, val, xi))
+        P.spmv_set_order(Cp, "column")
+    for M in (A, Cp, Cd):
+        assert P.spmv_device_error(M) == 0
+
+
+def test_config1_32cubed_ell_exact(device):
+    """32^3 HPCG, x ~ U[-1,1) seed 0: plain ELL against the CSR oracle."""
+    rowptr, col, val = oracle.hpcg_csr(32, 32, 32)
+    assert rowptr[-1] == 830584
+    x = spmv_inputs.uniform_vector(32 ** 3, seed=0)
+    A = P.spmv_build("hpcg", 32, 32, 32)
+    assert np.array_equal(run(A, x), oracle.spmv(rowptr, col, val, x))
+
+
+def test_fast_order_edge_vectors():
+    g = (9, 8, 7)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    scale_cases = [1e-300, 1e-200, 1.0, 1e200, 1e300]
+    for s in scale_cases:
+        x = spmv_inputs.uniform_vector(n, seed=3) * s
+        y_ref = oracle.spmv(rowptr, col, val, x)
+        y = run(C, x)
+        if np.all(np.isfinite(y_ref)):
+            check_fast(y, y_ref, abs_row_sums(rowptr, col, val, x))
+    # zeros, denormals and non-finite values take the exact path on the device
+    for x in (np.zeros(n), np.full(n, 5e-324), np.where(np.arange(n) % 7 == 0, np.inf, 1.0),
+              np.where(np.arange(n) == 11, np.nan, -2.0)):
+        y_ref = oracle.spmv(rowptr, col, val, x)
+        y = run(C, x)
+        assert np.array_equal(np.isnan(y), np.isnan(y_ref))
+        ok = ~np.isnan(y_ref)
+        assert np.array_equal(y[ok], y_ref[ok])
+    # one huge entry: normwise bound only
+    x = spmv_inputs.uniform_vector(n, seed=4)
+    x[n // 2] = 1e6
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    y = run(C, x)
+    assert np.max(np.abs(y - y_ref)) <= 52 * 2.0 ** -52 * 1e6
+
+
+@pytest.mark.parametrize("g", [(4, 4, 4), (17, 13, 11), (32, 32, 32)])
+def test_binary32_products(g):
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    x32 = spmv_inputs.uniform_vector(n, seed=2).astype(np.float32)
+    y_ref = oracle.spmv_f32(rowptr, col, val, x32)
+    A = P.spmv_build("hpcg", *g)
+    for M in (A, P.spmv_compress(A, format="pattern"), P.spmv_compress(A, format="delta", min_count=1)):
+        x = torch.from_numpy(x32).cuda()
+        y = torch.empty_like(x)
+        P.spmv_apply_f32(M, x, y)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy(), y_ref)
+
+
+def test_config2_192cubed_sampled():
+    """192^3 HPCG, x ~ U[-1,1) seed 1, in the launch configuration the
+    benchmark times: ELL and pattern (COLUMN) bit-exact and pattern FAST
+    within 1e-14 on sampled rows, plus A*1 = 27 - nnz_i on every row."""
+    nx = ny = nz = 192
+    n = nx * ny * nz
+    x = spmv_inputs.uniform_vector(n, seed=1)
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 20000), np.arange(0, 2 * nx * ny, 997),
+                                     np.arange(n - 2 * nx * ny, n, 991), [0, nx - 1, n - 1]]))
+    y_ref = oracle.hpcg_spmv_rows(nx, ny, nz, rows, x)
+    A = P.spmv_build("hpcg", nx, ny, nz)
+    y = run(A, x)
+    assert np.array_equal(y[rows], y_ref)
+    C = P.spmv_compress(A, format="pattern")
+    assert np.array_equal(run(C, x)[rows], y_ref)
+    P.spmv_set_order(C, "fast")
+    yf = run(C, x)
+    d = np.abs(yf[rows] - y_ref)
+    # sum_j |a_ij x_j| = 26|x_i| + sum_{j!=i} |x_j| = 52|x_i| - (A|x|)_i
+    scale = 52.0 * np.abs(x[rows]) - oracle.hpcg_spmv_rows(nx, ny, nz, rows, np.abs(x))
+    assert np.max(d / scale) <= TOL
+    assert np.max(d) <= TOL * np.max(np.abs(yf))
+    ones = run(C, np.ones(n))
+    lens = np.asarray(P.spmv_decompress(A)[0])
+    assert np.array_equal(ones, 27.0 - np.diff(lens))
+    assert P.spmv_device_error(C) == 0
+
+
+def test_config3_irregular_128_exact():
+    """128^3 irregular variant (seed 2): delta format with per-slice fallback,
+    bit-exact against the oracle on every row."""
+    g = (128, 128, 128)
+    rp, c, v, _ = oracle.irregular_csr(*g, seed=2)
+    n = len(rp) - 1
+    x = spmv_inputs.uniform_vector(n, seed=2)
+    y_ref = oracle.spmv(rp, c, v, x)
+    A = P.spmv_build("irregular", *g, seed=2)
+    C = P.spmv_compress(A)
+    info = P.spmv_info(C)
+    assert info["nnz"] == len(c) and info["format_name"] == "delta"
+    assert np.array_equal(run(C, x), y_ref)
+    assert np.array_equal(run(A, x), y_ref)
+
+
+@pytest.mark.parametrize("k", [1, 4, 8, 16, 32])
+def test_spmm_matches_columns(k):
+    g = (11, 10, 9)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    X_np = spmv_inputs.uniform_matrix(n, k, seed=3)
+    Y_ref = oracle.spmm(rowptr, col, val, X_np)
+    A = P.spmv_build("hpcg", *g)
+    X = torch.from_numpy(X_np).cuda()
+    for M in (A, P.spmv_compress(A, format="pattern"), P.spmv_compress(A, format="delta", min_count=1)):
+        Y = torch.full_like(X, float("nan"))
+        P.spmm_apply(M, X, Y)
+        torch.cuda.synchronize()
+        assert np.array_equal(Y.cpu().numpy(), Y_ref)
+    C = P.spmv_compress(A, format="pattern", order="fast")
+    Y = torch.full_like(X, float("nan"))
+    P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    d = np.abs(Y.cpu().numpy() - Y_ref)
+    scale = oracle.spmm(rowptr, col, np.abs(val), np.abs(X_np))
+    assert np.max(d / scale) <= TOL
+
+
+def test_spmm_160_k32_sampled():
+    nx = 160
+    n = nx ** 3
+    k = 32
+    X_np = spmv_inputs.uniform_matrix(n, k, seed=3)
+    rows = np.random.default_rng(3).integers(0, n, 3000)
+    A = P.spmv_build("hpcg", nx, nx, nx)
+    C = P.spmv_compress(A, format="pattern")
+    X = torch.from_numpy(X_np).cuda()
+    Y = torch.empty_like(X)
+    P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    Yh = Y.cpu().numpy()
+    for j in (0, 7, 31):
+        assert np.array_equal(Yh[rows, j], oracle.hpcg_spmv_rows(nx, nx, nx, rows, np.ascontiguousarray(X_np[:, j])))
+
+
+def test_ragged_batch_exact():
+    edges = spmv_inputs.grid_edges(24, seed=4)
+    mats, xs, ys, refs = [], [], [], []
+    for b, e in enumerate(edges):
+        A = P.spmv_build("hpcg", e, e, e)
+        mats.append(P.spmv_compress(A, format="pattern"))
+        x_np = spmv_inputs.uniform_vector(e ** 3, seed=100 + b)
+        xs.append(torch.from_numpy(x_np).cuda())
+        ys.append(torch.full_like(xs[-1], float("nan")))
+        rows = np.random.default_rng(b).integers(0, e ** 3, 500)
+        refs.append((rows, oracle.hpcg_spmv_rows(e, e, e, rows, x_np)))
+    plan = P.spmv_batch_create(mats, xs, ys)
+    for _ in range(2):
+        P.spmv_batch_launch(plan)
+    torch.cuda.synchronize()
+    for y, (rows, ref) in zip(ys, refs):
+        assert np.array_equal(y.cpu().numpy()[rows], ref)
+    P.spmv_batch_free(plan)
+    # small ones in full, through the one-off call
+    small = [i for i, e in enumerate(edges) if e <= 40]
+    for y in ys:
+        y.fill_(float("nan"))
+    P.spmv_apply_batched([mats[i] for i in small], [xs[i] for i in small], [ys[i] for i in small])
+    for i in small:
+        e = edges[i]
+        rp, c, v = oracle.hpcg_csr(e, e, e)
+        assert np.array_equal(ys[i].cpu().numpy(), oracle.spmv(rp, c, v, xs[i].cpu().numpy()))
+
+
+def test_host_buffers_entry_point():
+    g = (20, 18, 16)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    x = spmv_inputs.uniform_vector(n, seed=5)
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern")
+    y = np.zeros(n)
+    P.spmv_apply_host(C, x, y)
+    assert np.array_equal(y, oracle.spmv(rowptr, col, val, x))
+
+
+def test_graph_capture_of_apply():
+    g = (24, 24, 24)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    x_np = spmv_inputs.uniform_vector(n, seed=6)
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    x = torch.from_numpy(x_np).cuda()
+    y = torch.empty_like(x)
+    P.spmv_apply(C, x, y)  # first call uploads the matrix
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        P.spmv_apply(C, x, y)
+    y.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    y_ref = oracle.spmv(rowptr, col, val, x_np)
+    check_fast(y.cpu().numpy(), y_ref, abs_row_sums(rowptr, col, val, x_np))
+
+
+def test_empty_and_single_row():
+    A = P.spmv_build_csr(np.array([0]), np.array([], np.int32), np.array([]))
+    x = torch.zeros(0, dtype=torch.float64, device="cuda")
+    y = torch.zeros(0, dtype=torch.float64, device="cuda")
+    for M in (A, P.spmv_compress(A, format="delta")):
+        P.spmv_apply(M, x, y)
+    B = P.spmv_build_csr(np.array([0, 1]), np.array([0], np.int32), np.array([-3.5]))
+    assert run(B, np.array([2.0]))[0] == -7.0
+    Bp = P.spmv_compress(B, format="pattern")
+    assert run(Bp, np.array([2.0]))[0] == -7.0

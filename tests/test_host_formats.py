@@ -1,0 +1,172 @@
+"""Host-side logic of the library, checked against the oracle on the CPU:
+generators (bit-exact CSR), compression/decompression round trips, the
+pattern census of Sec. V, byte accounting, export/import and corruption
+detection."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1612_00530_gb300 as P
+import spmv_inputs
+from paper_1612_00530_gb300 import build as lib_build
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    lib_build.build()
+
+
+GRIDS = [(1, 1, 1), (2, 3, 5), (3, 3, 3), (4, 4, 4), (17, 5, 3), (32, 32, 32)]
+
+
+def same_csr(a, b):
+    return all(np.array_equal(u, v) for u, v in zip(a, b))
+
+
+@pytest.mark.parametrize("g", GRIDS)
+def test_hpcg_generator_matches_oracle(g):
+    A = P.spmv_build("hpcg", *g)
+    assert same_csr(P.spmv_decompress(A), oracle.hpcg_csr(*g))
+
+
+@pytest.mark.parametrize("g,seed", [((6, 5, 4), 2), ((12, 12, 12), 2), ((9, 7, 11), 13)])
+def test_irregular_generator_matches_oracle(g, seed):
+    A = P.spmv_build("irregular", *g, seed=seed)
+    rp, c, v, _ = oracle.irregular_csr(*g, seed=seed)
+    got = P.spmv_decompress(A)
+    assert np.array_equal(got[0], rp) and np.array_equal(got[1], c)
+    assert np.array_equal(got[2].view(np.uint64), v.view(np.uint64))
+
+
+def test_irregular_diag_rule_and_no_permutation():
+    g = (7, 6, 5)
+    A = P.spmv_build("irregular", *g, seed=3, diag_rule=1, permute=False)
+    rp, c, v, perm = oracle.irregular_csr(*g, seed=3, diag_rule=1, permute=False)
+    assert np.array_equal(perm, np.arange(len(perm)))
+    assert same_csr(P.spmv_decompress(A), (rp, c, v))
+
+
+@pytest.mark.parametrize("g", GRIDS)
+def test_pattern_round_trip_and_census(g):
+    A = P.spmv_build("hpcg", *g)
+    C = P.spmv_compress(A, format="pattern")
+    info = P.spmv_info(C)
+    assert info["format_name"] == "pattern"
+    ntypes = int(np.prod([min(d, 3) for d in g]))
+    assert info["n_patterns"] == ntypes
+    assert info["dict_size"] == (1 if g == (1, 1, 1) else 2)
+    assert info["fast_eligible"] == 1
+    assert same_csr(P.spmv_decompress(C), oracle.hpcg_csr(*g))
+    if min(g) >= 3:
+        assert info["union_size"] == 27 and info["record_bytes"] == 28
+
+
+def test_pattern_census_matches_oracle_registry():
+    g = (6, 7, 5)
+    rp, c, v = oracle.hpcg_csr(*g)
+    V = oracle.value_table(v)
+    typ, diffs, typelen, ends = oracle.data_index_table(rp, c, v, V)
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern")
+    assert P.spmv_info(C)["n_patterns"] == len(typelen)
+
+
+@pytest.mark.parametrize("g", [(4, 4, 4), (33, 9, 2), (64, 64, 8)])
+def test_delta_round_trip(g):
+    A = P.spmv_build("hpcg", *g)
+    C = P.spmv_compress(A, format="delta", min_count=1)
+    info = P.spmv_info(C)
+    assert info["format_name"] == "delta" and info["slices_value_raw"] == 0
+    assert same_csr(P.spmv_decompress(C), oracle.hpcg_csr(*g))
+
+
+def test_delta_irregular_fallback_fractions():
+    g = (40, 40, 40)
+    A = P.spmv_build("irregular", *g, seed=2)
+    C = P.spmv_compress(A)  # AUTO: too many patterns, goes to delta
+    info = P.spmv_info(C)
+    assert info["format_name"] == "delta"
+    rp, c, v, _ = oracle.irregular_csr(*g, seed=2)
+    got = P.spmv_decompress(C)
+    assert np.array_equal(got[0], rp) and np.array_equal(got[1], c)
+    assert np.array_equal(got[2].view(np.uint64), v.view(np.uint64))
+    # random renumbering spreads columns: almost every slice needs raw columns
+    assert info["slices_col_raw"] >= 0.9 * info["n_slices"]
+    # 16 levels + 26.0 make the table
+    assert info["dict_size"] >= 17
+
+
+def test_round_trip_random_csr_with_signed_zeros():
+    rng = np.random.default_rng(0)
+    n = 300
+    rows = []
+    for i in range(n):
+        cols = np.unique(np.concatenate([[i], rng.integers(0, n, size=rng.integers(0, 12))]))
+        rows.append(cols)
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.choice([-0.0, 0.0, 1.5, -2.25, np.inf, 3.0e-310], size=len(col))
+    A = P.spmv_build_csr(rowptr, col, val)
+    for fmt in ("delta",):
+        C = P.spmv_compress(A, format=fmt, min_count=1)
+        got = P.spmv_decompress(C)
+        assert np.array_equal(got[0], rowptr) and np.array_equal(got[1], col)
+        assert np.array_equal(got[2].view(np.uint64), val.view(np.uint64))
+    with pytest.raises(P.SpmvError) as e:
+        P.spmv_compress(A, format="pattern")
+    assert e.value.status == P.SPMV_EUNSUPPORTED
+
+
+def test_ell_padding_accounting():
+    g = (5, 5, 5)
+    A = P.spmv_build("hpcg", *g)
+    info = P.spmv_info(A)
+    nnz = (3 * 5 - 2) ** 3
+    assert info["nnz"] == nnz
+    slots = (info["format_bytes"] - info["n_slices"] * 12) // 12
+    assert info["padding_bytes"] == (slots - nnz) * 12
+
+
+def test_pattern_bytes_per_row_192():
+    # 27 one-byte codes + the pattern byte: 28 bytes per row, 1.0 per nonzero
+    # plus 1/27 for the pattern, against 12 for ELL (Sec. IV-B, Table II)
+    A = P.spmv_build("hpcg", 20, 20, 20)
+    C = P.spmv_compress(A, format="pattern")
+    info = P.spmv_info(C)
+    assert info["format_bytes"] == 28 * info["n"]
+
+
+@pytest.mark.parametrize("fmt", ["ell", "pattern", "delta"])
+def test_export_import_round_trip(fmt):
+    A = P.spmv_build("hpcg", 7, 6, 5)
+    C = A if fmt == "ell" else P.spmv_compress(A, format=fmt, min_count=1)
+    blob = P.spmv_export(C)
+    D = P.spmv_import(blob)
+    assert P.spmv_info(D)["checksum"] == P.spmv_info(C)["checksum"]
+    assert same_csr(P.spmv_decompress(D), oracle.hpcg_csr(7, 6, 5))
+    if fmt == "pattern":
+        assert P.spmv_info(D)["fast_eligible"] == 1
+
+
+@pytest.mark.parametrize("fmt", ["pattern", "delta"])
+def test_corrupted_stream_rejected(fmt):
+    A = P.spmv_build("hpcg", 7, 6, 5)
+    C = P.spmv_compress(A, format=fmt, min_count=1)
+    blob = bytearray(P.spmv_export(C))
+    rng = np.random.default_rng(1)
+    for pos in list(rng.integers(8, len(blob), size=24)) + [len(blob) - 1, 40]:
+        bad = bytearray(blob)
+        bad[pos] ^= 0x5A
+        with pytest.raises(P.SpmvError) as e:
+            P.spmv_import(bytes(bad))
+        assert e.value.status == P.SPMV_ECORRUPT
+    with pytest.raises(P.SpmvError) as e:
+        P.spmv_import(bytes(blob[:-3]))
+    assert e.value.status == P.SPMV_ECORRUPT
+
+
+def test_empty_matrix():
+    A = P.spmv_build_csr(np.array([0]), np.array([], np.int32), np.array([]))
+    assert P.spmv_info(A)["n"] == 0
+    C = P.spmv_compress(A, format="delta")
+    assert P.spmv_decompress(C)[0].tolist() == [0]
