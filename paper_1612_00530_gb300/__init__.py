@@ -10,7 +10,7 @@ The functions keep the C names: spmv_build, spmv_build_csr, spmv_compress,
 spmv_set_order, spmv_info, spmv_decompress, spmv_export, spmv_import,
 spmv_apply, spmv_apply_host, spmv_apply_f32, spmm_apply, spmv_batch_create,
 spmv_batch_launch, spmv_batch_free, spmv_apply_batched, cg_solve,
-spmv_device_error, spmv_version.
+spmv_device_error, spmv_autotune, spmv_version.
 """
 from __future__ import annotations
 
@@ -45,7 +45,8 @@ class spmv_info_t(ctypes.Structure):
     _fields_ = [("n", _i64), ("nnz", _i64), ("format", _i32), ("order", _i32), ("dict_size", _i32),
                 ("n_patterns", _i32), ("union_size", _i32), ("record_bytes", _i32), ("max_row_nnz", _i32),
                 ("fast_eligible", _i32), ("n_slices", _i64), ("slices_value_raw", _i64), ("slices_col_raw", _i64),
-                ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64)]
+                ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64),
+                ("fast_tile_rows", _i32), ("reserved", _i32)]
 
 
 class spmv_cg_opts(ctypes.Structure):
@@ -95,6 +96,7 @@ def library() -> ctypes.CDLL:
             "spmv_cg_result_free": [ctypes.POINTER(spmv_cg_result)],
             "spmv_free": [_p],
             "spmv_device_error": [_p, ctypes.POINTER(_i32)],
+            "spmv_autotune": [_p, _p, _p, _i32, ctypes.POINTER(_i32)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -296,6 +298,14 @@ def cg_solve(A: SpmvMatrix, b, x, tol: float = 1e-10, max_iter: int = 10000, mod
                rel_residual=r.rel_residual, seconds=r.seconds, history=hist)
     lib.spmv_cg_result_free(ctypes.byref(r))
     return out
+
+
+def spmv_autotune(A: SpmvMatrix, x, y, reps: int = 10) -> int:
+    """Times A's kernel configurations on x, y (CUDA float64); returns the
+    chosen tile rows (0 if nothing to tune)."""
+    c = _i32(0)
+    _check(library().spmv_autotune(A, _dptr(x, "float64"), _dptr(y, "float64"), reps, ctypes.byref(c)))
+    return c.value
 
 
 def spmv_device_error(A: SpmvMatrix) -> int:

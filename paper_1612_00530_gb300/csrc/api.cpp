@@ -4,6 +4,8 @@
 // thread-local message; nothing throws across the boundary.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "spmvc_internal.h"
@@ -71,6 +73,26 @@ void free_device(spmv_mat_s* m) {
     m->device = -1;
     m->d_ell_val32 = nullptr;
     m->d_hx = m->d_hy = nullptr;
+}
+
+// Autotuner cache: (device name, n, nnz, union size) -> rows per thread of
+// the staged FAST kernel.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+std::string tune_key(const spmv_mat_s* m) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    return std::string(prop.name) + "|" + std::to_string(m->n) + "|" + std::to_string(m->nnz) + "|" +
+           std::to_string(m->pat.uoff.size());
+}
+
+int tuned_rows_per_thread(const spmv_mat_s* m, int fallback) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(tune_key(m));
+    return it == g_tune.end() ? fallback : it->second;
 }
 
 // First device use: copy the stored form to the current device.
@@ -147,6 +169,12 @@ int ensure_device(spmv_mat_s* m) {
         std::memcpy(&v.mult_hi, tbl + 4, 4);
         v.mult_exp = p.mult_exp;
         v.err = m->d_err;
+        m->stage_ok = false;
+        if (stage_supported(v.nu)) {
+            const int prefer = tuned_rows_per_thread(m, 4);
+            for (int rpt : {prefer, 4, 2, 1})
+                if (make_stage_plan(p.uoff, rpt, 512, 12288, &m->stage)) { m->stage_ok = true; break; }
+        }
     } else {
         const DeltaFormat& d = m->dlt;
         DeltaView& v = m->dlt_view;
@@ -310,6 +338,7 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->union_size = static_cast<int32_t>(A->pat.uoff.size());
         out->record_bytes = 4 * A->pat.words;
         out->fast_eligible = A->pat.fast_ok ? 1 : 0;
+        out->fast_tile_rows = A->stage_ok ? A->stage.rows : 0;
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
@@ -388,8 +417,9 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
     const cudaStream_t s = as_stream(stream);
     if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
     else if (A->fmt == SPMV_FMT_PATTERN)
-        e = A->order == SPMV_ORDER_FAST ? launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s)
-                                        : launch_pattern_col_f64(A->pat_view, x, y, s);
+        e = A->order != SPMV_ORDER_FAST ? launch_pattern_col_f64(A->pat_view, x, y, s)
+            : A->stage_ok                ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
+                                         : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
     else e = launch_delta_f64(A->dlt_view, x, y, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
     return SPMV_OK;
@@ -453,6 +483,43 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y,
                 : launch_pattern_spmm_col(A->pat_view, k, X, ldx, Y, ldy, s);
     else e = launch_delta_spmm(A->dlt_view, k, X, ldx, Y, ldy, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmm launch");
+    return SPMV_OK;
+}
+
+int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_t* choice) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
+    if (reps <= 0) reps = 10;
+    int st = ensure_device(A);
+    if (st) return st;
+    if (choice) *choice = 0;
+    if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || !A->stage_ok || A->n == 0) return SPMV_OK;
+    cudaEvent_t e0, e1;
+    SPMVC_CUDA(cudaEventCreate(&e0));
+    SPMVC_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    StagePlan best_plan = A->stage;
+    for (int rpt : {1, 2, 4}) {
+        StagePlan plan;
+        if (!make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) continue;
+        cudaError_t e = launch_pattern_fast_staged(A->pat_view, plan, x, y, nullptr);  // warm
+        if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+        SPMVC_CUDA(cudaEventRecord(e0, nullptr));
+        for (int k = 0; k < reps; ++k) launch_pattern_fast_staged(A->pat_view, plan, x, y, nullptr);
+        SPMVC_CUDA(cudaEventRecord(e1, nullptr));
+        SPMVC_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_plan = plan; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A->stage = best_plan;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[tune_key(A)] = best_plan.rows_per_thread;
+    }
+    if (choice) *choice = best_plan.rows;
     return SPMV_OK;
 }
 

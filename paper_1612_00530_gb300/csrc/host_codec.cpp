@@ -92,7 +92,10 @@ int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out) {
         const uint32_t pat = b[nu];
         if (pat >= p.pmask.size()) return corrupt("pattern number out of range");
         for (int u = 0; u < nu; ++u) {
-            if (!((p.pmask[pat] >> u) & 1u)) continue;
+            if (!((p.pmask[pat] >> u) & 1u)) {
+                if (b[u] != ndict) return corrupt("absent slot without the absent code");
+                continue;
+            }
             const int64_t c = r + p.uoff[u];
             if (c < 0 || c >= n) return corrupt("pattern column out of range");
             if (b[u] >= ndict) return corrupt("value code out of range");

@@ -27,6 +27,19 @@ __device__ __forceinline__ void raise_error(int32_t* err, int32_t code) {
     if (err) atomicOr(err, code);
 }
 
+// PTX prmt in its default mode: for each result byte a 4-bit selector picks
+// one of the 8 source bytes; a set selector msb replicates that byte's sign.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Signed multiplier of value code c (< 8) from the packed int8 table.
+__device__ __forceinline__ int32_t mult_of(uint32_t lo, uint32_t hi, uint32_t c) {
+    return int32_t(prmt(lo, hi, (c & 7u) * 0x1111u + 0x8880u));
+}
+
 __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[kMaxRecordWords], int u) {
     return (w[u >> 2] >> (8 * (u & 3))) & 0xFFu;
 }
@@ -212,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_kernel(PatternView a, con
         if (u < a.nu) {
             const uint32_t code = byte_of(w, u);
             // multiplier of the code, sign-extended; absent slots map to 0
-            const int32_t m = int32_t(__byte_perm(a.mult_lo, a.mult_hi, (code & 7u) * 0x1111u + 0x8880u));
+            const int32_t m = mult_of(a.mult_lo, a.mult_hi, code);
             const int64_t c = r + a.uoff[u];
             const bool inside = uint64_t(c) < uint64_t(a.n);
             const double xv = __ldg(x + (inside ? c : r));
@@ -225,6 +238,114 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_kernel(PatternView a, con
     }
     const int64_t acc = acc_h * (int64_t(1) << 26) + acc_l;
     y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+}
+
+
+// ---------------------------------------------- FAST order, staged -------
+// One CTA per tile of sp.rows consecutive rows.  Phase 1 copies the x
+// windows the tile touches (merged segments of the union displacements)
+// into shared memory and takes their largest exponent; phase 2 converts
+// every staged element once to two-limb fixed point in place; phase 3 sums
+// each row slot by slot from shared memory with 32x32->64-bit multiply-adds
+// and rounds once.  Windows outside [0, n) read as zero; they are only ever
+// addressed by absent slots, whose multiplier is 0.  Everything is integer:
+// x is moved as raw 64-bit words and never touches the FP64 pipe.
+constexpr int kStageThreads = 512;
+
+__device__ __forceinline__ void mad_wide(int64_t& acc, int32_t a, int32_t b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+// (lo, hi) words of x -> limbs (xl, xh) of X = sign(x) floor(|x| 2^(1075-E)),
+// X = xh 2^26 + xl with both limbs carrying the sign.
+__device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t emax) {
+    const uint32_t k = emax - ((hi >> 20) & 0x7FFu);
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    uint64_t X;
+    asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"((uint64_t(mh) << 32) | lo), "r"(k));
+    const int32_t s1 = (int32_t(hi) >> 31) | 1;  // +1 or -1
+    return make_int2(int32_t(uint32_t(X) & 0x3FFFFFFu) * s1, int32_t(uint32_t(X >> 26)) * s1);
+}
+
+template <int WORDS, int NU, int RPT>
+__global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
+                                                                            const double* __restrict__ x,
+                                                                            double* __restrict__ y) {
+    extern __shared__ int2 sx[];
+    __shared__ uint32_t s_red[kStageThreads / 32];
+    __shared__ uint32_t smask[32];
+    const int tid = threadIdx.x;
+    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
+    const uint2* __restrict__ xw = reinterpret_cast<const uint2*>(x);
+    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
+    // phase 1: stage raw words of x and find the tile's largest exponent
+    uint32_t mx = 0;
+#pragma unroll
+    for (int sg = 0; sg < kMaxSegments; ++sg) {
+        if (sg >= sp.nseg) break;
+        const int64_t g0 = r0 + sp.seg_min[sg];
+        const int len = sp.rows + sp.seg_span[sg];
+        int2* dst = sx + sp.seg_base[sg];
+        for (int e = tid; e < len; e += kStageThreads) {
+            const int64_t idx = g0 + e;
+            uint2 b = make_uint2(0u, 0u);
+            if (uint64_t(idx) < uint64_t(a.n)) b = __ldg(xw + idx);
+            dst[e] = make_int2(int(b.x), int(b.y));
+            mx = max(mx, b.y & 0x7FFFFFFFu);
+        }
+    }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+#pragma unroll
+    for (int w = 0; w < kStageThreads / 32; ++w) mx = max(mx, s_red[w]);
+    const uint32_t emax = mx >> 20;
+    const bool exact_path = emax < 64u || emax >= 2047u;
+    // phase 2: convert in place
+    if (!exact_path) {
+        for (int e = tid; e < sp.elems; e += kStageThreads) {
+            const int2 b = sx[e];
+            sx[e] = fixed_limbs(uint32_t(b.x), uint32_t(b.y), emax);
+        }
+    }
+    __syncthreads();
+    // phase 3: rows
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int rl = tid + i * kStageThreads;
+        const int64_t r = r0 + rl;
+        if (r >= a.n) break;
+        uint32_t w[kMaxRecordWords];
+        load_record<WORDS>(a, r, w);
+        if (exact_path) {
+            // zeros/denormals only, or non-finite values: the COLUMN order
+            const uint32_t mask = smask[byte_of(w, NU) & 31];
+            double acc = 0.0;
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+                if ((mask >> u) & 1u) {
+                    const int2 b = sx[rl + sp.soff[u]];
+                    acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
+                }
+            y[r] = acc;
+            continue;
+        }
+        // int8 multipliers of four codes at a time: nibble-pack the codes,
+        // then one table permute
+        uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+        for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+        int64_t acc_h = 0, acc_l = 0;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+            const int2 X = sx[rl + sp.soff[u]];
+            mad_wide(acc_h, m, X.y);
+            mad_wide(acc_l, m, X.x);
+        }
+        y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, int(emax) - 1075 + a.mult_exp);
+    }
 }
 
 // ------------------------------------------------------------ delta ------
@@ -373,7 +494,7 @@ __global__ void __launch_bounds__(kBlock) pattern_spmm_fast_kernel(PatternView a
     for (int u = 0; u < 4 * WORDS - 1; ++u)
         if (u < a.nu) {
             const uint32_t code = byte_of(w, u);
-            const int32_t m = int32_t(__byte_perm(a.mult_lo, a.mult_hi, (code & 7u) * 0x1111u + 0x8880u));
+            const int32_t m = mult_of(a.mult_lo, a.mult_hi, code);
             const int64_t c = r + a.uoff[u];
             const bool inside = uint64_t(c) < uint64_t(a.n);
             int32_t xh, xl;
@@ -486,6 +607,70 @@ cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, doubl
     SPMVC_DISPATCH_WORDS(a.words, (pattern_fast_kernel<W><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y, partial)));
     return cudaGetLastError();
 }
+
+cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                       cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
+    const size_t smem = size_t(sp.elems) * sizeof(int2);
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, kStageThreads, smem, s>>>(a, sp, x, y);
+        return cudaGetLastError();
+    };
+    // union sizes of the 3-D 27-, 19- and 7-point stencils and the 2-D 9- and
+    // 5-point ones are compiled with a fixed slot count
+#define SPMVC_NU_CASE(NUV)                                                             \
+    case NUV:                                                                          \
+        if (sp.rows_per_thread == 1) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 1>); \
+        if (sp.rows_per_thread == 2) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 2>); \
+        if (sp.rows_per_thread == 4) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 4>); \
+        return cudaErrorInvalidValue;
+    switch (a.nu) {
+        SPMVC_NU_CASE(27)
+        SPMVC_NU_CASE(19)
+        SPMVC_NU_CASE(9)
+        SPMVC_NU_CASE(7)
+        SPMVC_NU_CASE(5)
+        default: return cudaErrorNotSupported;
+    }
+#undef SPMVC_NU_CASE
+}
+
+bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }
+
+bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
+                     StagePlan* out) {
+    StagePlan p{};
+    p.rows = rows_per_thread * threads;
+    p.rows_per_thread = rows_per_thread;
+    const int nu = int(uoff.size());
+    if (nu == 0 || nu > 31) return false;
+    int seg = -1;
+    for (int u = 0; u < nu; ++u) {
+        if (u == 0 || int64_t(uoff[u]) - uoff[u - 1] > p.rows) {
+            if (++seg >= kMaxSegments) return false;
+            p.seg_min[seg] = uoff[u];
+        }
+        p.seg_span[seg] = uoff[u] - p.seg_min[seg];
+    }
+    p.nseg = seg + 1;
+    int64_t base = 0;
+    for (int sg = 0; sg < p.nseg; ++sg) {
+        p.seg_base[sg] = int32_t(base);
+        base += int64_t(p.rows) + p.seg_span[sg];
+    }
+    if (base > max_elems) return false;
+    p.elems = int32_t(base);
+    for (int u = 0, sg = 0; u < nu; ++u) {
+        while (sg + 1 < p.nseg && uoff[u] >= p.seg_min[sg + 1]) ++sg;
+        p.soff[u] = p.seg_base[sg] + (uoff[u] - p.seg_min[sg]);
+    }
+    *out = p;
+    return true;
+}
+
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     delta_kernel<double><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y);

@@ -123,6 +123,27 @@ struct DeltaView {
     int32_t* err;
 };
 
+// Shared-memory staging plan of the FAST kernel for tiles of `rows` rows:
+// the union displacements are merged into segments whose x windows
+// [r0 + seg_min, r0 + rows - 1 + seg_min + seg_span] overlap; segment s
+// starts at element seg_base[s] of the tile's staged copy, and slot u of
+// row r reads element (r - r0) + soff[u].  Built from the pattern table
+// alone (interval merging), no grid geometry involved.
+constexpr int kMaxSegments = 8;
+struct StagePlan {
+    int32_t rows;                   // tile rows (block threads * rows per thread)
+    int32_t rows_per_thread;
+    int32_t nseg;
+    int32_t elems;                  // staged elements per tile
+    int32_t seg_min[kMaxSegments];
+    int32_t seg_span[kMaxSegments];
+    int32_t seg_base[kMaxSegments];
+    int32_t soff[32];
+};
+bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
+                     StagePlan* out);
+bool stage_supported(int nu);  // union sizes with a compiled staged kernel
+
 // Kernel launchers (k_spmv.cu).
 cudaError_t launch_ell_f64(const EllView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_ell_f32(const EllView& a, const float* x, float* y, cudaStream_t s);
@@ -130,6 +151,8 @@ cudaError_t launch_pattern_col_f64(const PatternView& a, const double* x, double
 cudaError_t launch_pattern_col_f32(const PatternView& a, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, double* y,
                                     uint32_t* xmax_word, cudaStream_t s);
+cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                       cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s);
 // SpMM (k right-hand sides, row-major).
@@ -177,6 +200,8 @@ struct spmv_mat_s {
     spmvc::PatternView pat_view{};
     spmvc::DeltaView dlt_view{};
     int32_t* d_err = nullptr;
+    spmvc::StagePlan stage{};          // FAST order: shared-memory staging plan
+    bool stage_ok = false;
     uint32_t* d_scratch_words = nullptr; // fast order: per-column max |x| words
     int64_t scratch_words = 0;
     // spmv_apply_host staging

@@ -277,3 +277,54 @@ def test_empty_and_single_row():
     assert run(B, np.array([2.0]))[0] == -7.0
     Bp = P.spmv_compress(B, format="pattern")
     assert run(Bp, np.array([2.0]))[0] == -7.0
+
+
+def spread_offsets_csr(n, offsets, vals):
+    """Rows with columns i + d for every d in offsets inside [0, n)."""
+    rowptr = [0]
+    col, val = [], []
+    for i in range(n):
+        for d, v in zip(offsets, vals):
+            if 0 <= i + d < n:
+                col.append(i + d)
+                val.append(v)
+        rowptr.append(len(col))
+    return np.array(rowptr, np.int64), np.array(col, np.int32), np.array(val, np.float64)
+
+
+def test_fast_order_unstaged_kernel():
+    """A union of displacements too spread out for shared-memory tiles (nine
+    segments) takes the direct FAST kernel; same bounds apply."""
+    offs = [-12000, -9000, -6000, -3000, 0, 3000, 6000, 9000, 12000]
+    vals = [-1.0, 0.5, -1.0, 0.25, 6.0, 0.25, -1.0, 0.5, -1.0]
+    rowptr, col, val = spread_offsets_csr(30000, offs, vals)
+    A = P.spmv_build_csr(rowptr, col, val)
+    C = P.spmv_compress(A, format="pattern", order="fast")
+    x = spmv_inputs.uniform_vector(30000, seed=8)
+    y = run(C, x)
+    assert P.spmv_info(C)["fast_tile_rows"] == 0
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    check_fast(y, y_ref, abs_row_sums(rowptr, col, val, x))
+    # the staged kernel for a milder spread
+    rowptr2, col2, val2 = spread_offsets_csr(30000, [-600, -1, 0, 1, 600], [-1.0, -2.0, 8.0, -2.0, -1.0])
+    C2 = P.spmv_compress(P.spmv_build_csr(rowptr2, col2, val2), format="pattern", order="fast")
+    y2 = run(C2, x)
+    assert P.spmv_info(C2)["fast_tile_rows"] > 0
+    check_fast(y2, oracle.spmv(rowptr2, col2, val2, x), abs_row_sums(rowptr2, col2, val2, x))
+
+
+def test_autotune_keeps_results():
+    g = (64, 48, 40)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    x_np = spmv_inputs.uniform_vector(n, seed=9)
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    x = torch.from_numpy(x_np).cuda()
+    y = torch.empty_like(x)
+    rows = P.spmv_autotune(C, x, y, reps=3)
+    assert rows in (512, 1024, 2048)
+    assert P.spmv_info(C)["fast_tile_rows"] == rows
+    y_ref = oracle.spmv(rowptr, col, val, x_np)
+    check_fast(run(C, x_np), y_ref, abs_row_sums(rowptr, col, val, x_np))
+    # ELL and COLUMN order have nothing to tune
+    assert P.spmv_autotune(P.spmv_build("hpcg", *g), x, y) == 0
