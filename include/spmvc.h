@@ -145,9 +145,11 @@ typedef struct {
     int64_t format_bytes;       /* matrix bytes one product reads (incl. padding) */
     int64_t padding_bytes;      /* of format_bytes: padding slots and records */
     uint64_t checksum;          /* FNV-1a of the compressed stream */
-    int32_t fast_tile_rows;     /* FAST order: rows per shared-memory tile
-                                   (0 = unstaged kernel, or not yet on a device) */
-    int32_t reserved;
+    int32_t fast_tile_rows;     /* FAST order: rows per shared-memory tile of the
+                                   staged kernel (0 = no staged kernel for A) */
+    int32_t fast_variant;       /* FAST kernel in use: 0 direct, 1 staged tiles,
+                                   2 pre-converted fixed-point copy of x;
+                                   -1 before A's first device call */
 } spmv_info_t;
 
 /* Fills *out with the sizes and statistics of A (host only). */
@@ -196,15 +198,23 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
                int64_t ldy, spmv_stream_t stream);
 
 /* Autotuner: times the kernel configurations available to A (FAST order:
- * shared-memory tiles of 512, 1024 and 2048 rows) on the caller's device
- * vectors x and y (n doubles each; y is overwritten), keeps the fastest for
- * later calls on A, and remembers it for matrices with the same signature
- * (device name, n, nnz, union size) built later in this process.  reps:
- * timed launches per candidate (default 10 when <= 0).  *choice (may be
- * NULL) receives the chosen tile rows, 0 when A has nothing to tune.
+ * the pre-converted-x kernel, and the shared-memory staged kernel with
+ * tiles of 512, 1024 and 2048 rows) on the caller's device vectors x and y
+ * (n doubles each; y is overwritten), keeps the fastest for later calls on
+ * A, and remembers it for matrices with the same signature (device name, n,
+ * nnz, union size) uploaded later in this process.  reps: timed launches per
+ * candidate (default 10 when <= 0).  *choice (may be NULL) receives the
+ * chosen tile rows for the staged kernel, 1 for the pre-converted kernel,
+ * 0 when A has nothing to tune.
  * Synchronous, uses the legacy default stream: call it outside any stream
  * capture. */
 int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_t *choice);
+
+/* Selects A's FAST kernel by hand (what spmv_autotune chooses): variant 0
+ * direct, 1 staged tiles of tile_rows rows (512, 1024 or 2048), 2
+ * pre-converted copy of x.  SPMV_EUNSUPPORTED when A has no such kernel.
+ * Copies A to the device if it is not there yet. */
+int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 
 /* ---- ragged batches: one persistent launch over many matrices --------- */
 typedef struct spmv_batch_s *spmv_batch_t;

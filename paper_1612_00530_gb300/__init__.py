@@ -10,7 +10,7 @@ The functions keep the C names: spmv_build, spmv_build_csr, spmv_compress,
 spmv_set_order, spmv_info, spmv_decompress, spmv_export, spmv_import,
 spmv_apply, spmv_apply_host, spmv_apply_f32, spmm_apply, spmv_batch_create,
 spmv_batch_launch, spmv_batch_free, spmv_apply_batched, cg_solve,
-spmv_device_error, spmv_autotune, spmv_version.
+spmv_device_error, spmv_autotune, spmv_set_variant, spmv_version.
 """
 from __future__ import annotations
 
@@ -46,7 +46,7 @@ class spmv_info_t(ctypes.Structure):
                 ("n_patterns", _i32), ("union_size", _i32), ("record_bytes", _i32), ("max_row_nnz", _i32),
                 ("fast_eligible", _i32), ("n_slices", _i64), ("slices_value_raw", _i64), ("slices_col_raw", _i64),
                 ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64),
-                ("fast_tile_rows", _i32), ("reserved", _i32)]
+                ("fast_tile_rows", _i32), ("fast_variant", _i32)]
 
 
 class spmv_cg_opts(ctypes.Structure):
@@ -97,6 +97,7 @@ def library() -> ctypes.CDLL:
             "spmv_free": [_p],
             "spmv_device_error": [_p, ctypes.POINTER(_i32)],
             "spmv_autotune": [_p, _p, _p, _i32, ctypes.POINTER(_i32)],
+            "spmv_set_variant": [_p, _i32, _i32],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -302,10 +303,16 @@ def cg_solve(A: SpmvMatrix, b, x, tol: float = 1e-10, max_iter: int = 10000, mod
 
 def spmv_autotune(A: SpmvMatrix, x, y, reps: int = 10) -> int:
     """Times A's kernel configurations on x, y (CUDA float64); returns the
-    chosen tile rows (0 if nothing to tune)."""
+    chosen staged tile rows, 1 for the pre-converted kernel, 0 if nothing
+    to tune."""
     c = _i32(0)
     _check(library().spmv_autotune(A, _dptr(x, "float64"), _dptr(y, "float64"), reps, ctypes.byref(c)))
     return c.value
+
+
+def spmv_set_variant(A: SpmvMatrix, variant: int, tile_rows: int = 0) -> None:
+    """FAST kernel by hand: 0 direct, 1 staged tiles (tile_rows), 2 pre-converted x."""
+    _check(library().spmv_set_variant(A, variant, tile_rows))
 
 
 def spmv_device_error(A: SpmvMatrix) -> int:

@@ -78,7 +78,8 @@ void free_device(spmv_mat_s* m) {
 // Autotuner cache: (device name, n, nnz, union size) -> rows per thread of
 // the staged FAST kernel.
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;
+std::map<std::string, int> g_tune;          // rows per thread of the staged kernel
+std::map<std::string, int> g_tune_variant;  // FAST kernel variant
 
 std::string tune_key(const spmv_mat_s* m) {
     int dev = 0;
@@ -87,6 +88,12 @@ std::string tune_key(const spmv_mat_s* m) {
     cudaGetDeviceProperties(&prop, dev);
     return std::string(prop.name) + "|" + std::to_string(m->n) + "|" + std::to_string(m->nnz) + "|" +
            std::to_string(m->pat.uoff.size());
+}
+
+int tuned_variant(const spmv_mat_s* m, int fallback) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_variant.find(tune_key(m));
+    return it == g_tune_variant.end() ? fallback : it->second;
 }
 
 int tuned_rows_per_thread(const spmv_mat_s* m, int fallback) {
@@ -170,11 +177,26 @@ int ensure_device(spmv_mat_s* m) {
         v.mult_exp = p.mult_exp;
         v.err = m->d_err;
         m->stage_ok = false;
+        m->fast_variant = 0;
+        if (p.fast_ok && stage_supported(v.nu)) {
+            // fixed-point copy of x with zero guard zones as wide as the
+            // largest displacement
+            int64_t guard = 0;
+            for (int32_t d : p.uoff) guard = std::max<int64_t>(guard, d < 0 ? -int64_t(d) : int64_t(d));
+            guard = (guard + 15) / 16 * 16;
+            int2* xf;
+            if ((st = dev_copy<int2>(m, nullptr, static_cast<size_t>(n + 2 * guard), &xf))) return st;
+            m->d_xfixed = xf;
+            m->xfixed_guard = guard;
+            m->fast_variant = tuned_variant(m, 2);
+        }
         if (stage_supported(v.nu)) {
             const int prefer = tuned_rows_per_thread(m, 4);
             for (int rpt : {prefer, 4, 2, 1})
                 if (make_stage_plan(p.uoff, rpt, 512, 12288, &m->stage)) { m->stage_ok = true; break; }
         }
+        if (m->fast_variant == 1 && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
+        if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
     } else {
         const DeltaFormat& d = m->dlt;
         DeltaView& v = m->dlt_view;
@@ -339,6 +361,7 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->record_bytes = 4 * A->pat.words;
         out->fast_eligible = A->pat.fast_ok ? 1 : 0;
         out->fast_tile_rows = A->stage_ok ? A->stage.rows : 0;
+        out->fast_variant = A->device >= 0 ? A->fast_variant : -1;
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
@@ -418,8 +441,10 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
     if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
     else if (A->fmt == SPMV_FMT_PATTERN)
         e = A->order != SPMV_ORDER_FAST ? launch_pattern_col_f64(A->pat_view, x, y, s)
-            : A->stage_ok                ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
-                                         : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
+            : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
+                                                           A->xfixed_guard, s)
+            : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
+                                   : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
     else e = launch_delta_f64(A->dlt_view, x, y, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
     return SPMV_OK;
@@ -493,33 +518,69 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     int st = ensure_device(A);
     if (st) return st;
     if (choice) *choice = 0;
-    if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || !A->stage_ok || A->n == 0) return SPMV_OK;
+    if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || A->n == 0) return SPMV_OK;
+    struct Cand { int variant; StagePlan plan; };
+    std::vector<Cand> cands;
+    if (A->d_xfixed) cands.push_back(Cand{2, A->stage});
+    if (A->stage_ok)
+        for (int rpt : {1, 2, 4}) {
+            StagePlan plan;
+            if (make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) cands.push_back(Cand{1, plan});
+        }
+    if (cands.size() <= 1) return SPMV_OK;
     cudaEvent_t e0, e1;
     SPMVC_CUDA(cudaEventCreate(&e0));
     SPMVC_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    StagePlan best_plan = A->stage;
-    for (int rpt : {1, 2, 4}) {
-        StagePlan plan;
-        if (!make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) continue;
-        cudaError_t e = launch_pattern_fast_staged(A->pat_view, plan, x, y, nullptr);  // warm
+    Cand pick = cands[0];
+    for (const Cand& c : cands) {
+        auto launch = [&]() {
+            return c.variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
+                                                          A->xfixed_guard, nullptr)
+                                  : launch_pattern_fast_staged(A->pat_view, c.plan, x, y, nullptr);
+        };
+        cudaError_t e = launch();
         if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
         SPMVC_CUDA(cudaEventRecord(e0, nullptr));
-        for (int k = 0; k < reps; ++k) launch_pattern_fast_staged(A->pat_view, plan, x, y, nullptr);
+        for (int k = 0; k < reps; ++k) launch();
         SPMVC_CUDA(cudaEventRecord(e1, nullptr));
         SPMVC_CUDA(cudaEventSynchronize(e1));
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; best_plan = plan; }
+        if (ms < best) { best = ms; pick = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    A->stage = best_plan;
+    A->fast_variant = pick.variant;
+    if (pick.variant == 1) A->stage = pick.plan;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
-        g_tune[tune_key(A)] = best_plan.rows_per_thread;
+        g_tune_variant[tune_key(A)] = pick.variant;
+        if (pick.variant == 1) g_tune[tune_key(A)] = pick.plan.rows_per_thread;
     }
-    if (choice) *choice = best_plan.rows;
+    if (choice) *choice = pick.variant == 1 ? pick.plan.rows : 1;
+    return SPMV_OK;
+}
+
+int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->fmt != SPMV_FMT_PATTERN || !A->pat.fast_ok) return fail(SPMV_EUNSUPPORTED, "no FAST kernels for this matrix");
+    int st = ensure_device(A);
+    if (st) return st;
+    if (variant == 0) { A->fast_variant = 0; return SPMV_OK; }
+    if (variant == 2) {
+        if (!A->d_xfixed) return fail(SPMV_EUNSUPPORTED, "no pre-converted kernel for this union size");
+        A->fast_variant = 2;
+        return SPMV_OK;
+    }
+    if (variant != 1) return fail(SPMV_EINVAL, "variant must be 0, 1 or 2");
+    if (!stage_supported(static_cast<int>(A->pat.uoff.size()))) return fail(SPMV_EUNSUPPORTED, "no staged kernel for this union size");
+    StagePlan plan;
+    if (tile_rows % 512 != 0 || !make_stage_plan(A->pat.uoff, tile_rows / 512, 512, 12288, &plan))
+        return fail(SPMV_EUNSUPPORTED, "tile does not fit shared memory (tile_rows 512, 1024 or 2048)");
+    A->stage = plan;
+    A->stage_ok = true;
+    A->fast_variant = 1;
     return SPMV_OK;
 }
 

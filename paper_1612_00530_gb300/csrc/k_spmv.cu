@@ -168,24 +168,33 @@ __device__ __forceinline__ void to_fixed(double xv, int emax, int32_t& xh, int32
     xh = (int32_t(X >> 26) ^ sgn) - sgn;
 }
 
-// acc * 2^S rounded to nearest-even, integer operations only (exponent out
-// of the normal range takes an FP64 detour).
+// acc * 2^S rounded to nearest-even, integer operations only (subnormal
+// results are rounded to their shorter precision, overflow gives +-inf).
 __device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
     if (acc == 0) return 0.0;
     const uint64_t sgn = acc < 0 ? 0x8000000000000000ull : 0ull;
     uint64_t a = acc < 0 ? uint64_t(0) - uint64_t(acc) : uint64_t(acc);
     const int lz = __clzll(a);
-    a <<= lz;
-    uint64_t mant = a >> 11;
-    const uint32_t rest = uint32_t(a) & 0x7FFu;
-    mant += (rest > 0x400u || (rest == 0x400u && (mant & 1u))) ? 1u : 0u;
-    int e = 63 - lz + S + 1023;
-    if (mant >> 53) {
-        mant >>= 1;
-        ++e;
+    a <<= lz;                                   // leading one at bit 63
+    const int e = 63 - lz + S + 1023;           // biased exponent if normal
+    // bits of `a` below the kept mantissa: 11 for a normal result, more for a
+    // subnormal one (the field then holds the value / 2^-1074 directly)
+    const int drop = e >= 1 ? 11 : 12 - e;
+    uint64_t mant, rest;
+    if (drop >= 65) { mant = 0; rest = 0; }             // below half the smallest subnormal
+    else if (drop == 64) { mant = 0; rest = a; }
+    else { mant = a >> drop; rest = a << (64 - drop); }
+    const uint64_t half = 0x8000000000000000ull;
+    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+    uint64_t bits;
+    if (e >= 1) {
+        // mant in [2^52, 2^53]; a carry to 2^53 moves into the exponent field
+        bits = (uint64_t(e - 1) << 52) + mant;
+        if (e - 1 + int(mant >> 52) >= 2047) bits = 0x7FF0000000000000ull;
+    } else {
+        bits = mant;  // subnormal; a carry to 2^52 becomes the smallest normal
     }
-    if (e <= 0 || e >= 2047) return scalbn(__ll2double_rn(acc), S);
-    return __longlong_as_double(int64_t(sgn | (uint64_t(e) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+    return __longlong_as_double(int64_t(sgn | bits));
 }
 
 template <int WORDS>
@@ -240,6 +249,71 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_kernel(PatternView a, con
     y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
 }
 
+
+// ------------------------------------- FAST order, pre-converted x -------
+// x is converted once per product into fixed-point limbs stored in a
+// scratch copy with zero guard zones of `guard` elements on both sides, so
+// that the row kernel reads X[r + d] for every union displacement d without
+// a bounds check (out-of-range slots are absent ones, multiplier 0).
+__global__ void __launch_bounds__(256) convert_x_kernel(const uint2* __restrict__ xw, int64_t n,
+                                                        const uint32_t* __restrict__ partial,
+                                                        int2* __restrict__ X) {
+    __shared__ int s_emax;
+    const uint32_t emax = uint32_t(block_emax(partial, &s_emax));
+    if (emax < 64u || emax >= 2047u) return;   // the row kernel takes the exact path
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const uint2 b = __ldg(xw + i);
+        const uint32_t k = emax - ((b.y >> 20) & 0x7FFu);
+        const uint32_t mh = (b.y & 0xFFFFFu) | 0x100000u;
+        uint64_t v;
+        asm("shr.b64 %0, %1, %2;" : "=l"(v) : "l"((uint64_t(mh) << 32) | b.x), "r"(k));
+        const int32_t s1 = (int32_t(b.y) >> 31) | 1;
+        X[i] = make_int2(int32_t(uint32_t(v) & 0x3FFFFFFu) * s1, int32_t(uint32_t(v >> 26)) * s1);
+    }
+}
+
+__device__ __forceinline__ void mad_wide_x(int64_t& acc, int32_t a, int32_t b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+template <int WORDS, int NU>
+__global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
+                                                                const int2* __restrict__ X,
+                                                                double* __restrict__ y,
+                                                                const uint32_t* __restrict__ partial) {
+    __shared__ uint32_t smask[32];
+    __shared__ int s_emax;
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    const int emax = block_emax(partial, &s_emax);
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    if (emax < 64 || emax >= 2047) {
+        const uint32_t mask = smask[byte_of(w, NU) & 31];
+        double acc = 0.0;
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+            if ((mask >> u) & 1u)
+                acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __ldg(x + r + a.uoff[u]), acc);
+        y[r] = acc;
+        return;
+    }
+    uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+    for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+    const int2* __restrict__ Xr = X + r;
+    int64_t acc_h = 0, acc_l = 0;
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+        const int2 v = __ldg(Xr + a.uoff[u]);
+        mad_wide_x(acc_h, m, v.y);
+        mad_wide_x(acc_l, m, v.x);
+    }
+    y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, emax - 1075 + a.mult_exp);
+}
 
 // ---------------------------------------------- FAST order, staged -------
 // One CTA per tile of sp.rows consecutive rows.  Phase 1 copies the x
@@ -636,6 +710,27 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
         default: return cudaErrorNotSupported;
     }
 #undef SPMVC_NU_CASE
+}
+
+cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
+                                  int2* X_guarded, int64_t guard, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    int2* X = X_guarded + guard;
+    xmax_kernel<<<kXmaxBlocks, 1024, 0, s>>>(x, a.n, partial);
+    convert_x_kernel<<<kXmaxBlocks * 8, 256, 0, s>>>(reinterpret_cast<const uint2*>(x), a.n, partial, X);
+    const unsigned grid = grid_of(a.n);
+#define SPMVC_NU_X(NUV) \
+    case NUV: pattern_fast_x_kernel<(NUV + 4) / 4, NUV><<<grid, kBlock, 0, s>>>(a, x, X, y, partial); break;
+    switch (a.nu) {
+        SPMVC_NU_X(27)
+        SPMVC_NU_X(19)
+        SPMVC_NU_X(9)
+        SPMVC_NU_X(7)
+        SPMVC_NU_X(5)
+        default: return cudaErrorNotSupported;
+    }
+#undef SPMVC_NU_X
+    return cudaGetLastError();
 }
 
 bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }

@@ -153,6 +153,8 @@ cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, doubl
                                     uint32_t* xmax_word, cudaStream_t s);
 cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                        cudaStream_t s);
+cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
+                                  int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s);
 // SpMM (k right-hand sides, row-major).
@@ -202,6 +204,9 @@ struct spmv_mat_s {
     int32_t* d_err = nullptr;
     spmvc::StagePlan stage{};          // FAST order: shared-memory staging plan
     bool stage_ok = false;
+    int32_t fast_variant = 0;          // 0 direct, 1 staged tiles, 2 pre-converted x copy
+    int2* d_xfixed = nullptr;          // FAST order: fixed-point copy of x with guard zones
+    int64_t xfixed_guard = 0;
     uint32_t* d_scratch_words = nullptr; // fast order: per-column max |x| words
     int64_t scratch_words = 0;
     // spmv_apply_host staging

@@ -20,6 +20,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--kind", default="hpcg", choices=("hpcg", "irregular"))
+    ap.add_argument("--variant", type=int, default=-1, help="FAST kernel: 0 direct, 1 staged, 2 pre-converted")
+    ap.add_argument("--tile", type=int, default=2048)
     args = ap.parse_args()
     g = args.grid
     A = P.spmv_build(args.kind, g, g, g, seed=2)
@@ -27,6 +29,8 @@ def main():
     n = P.spmv_info(M)["n"]
     x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=1)).cuda()
     y = torch.empty_like(x)
+    if args.variant >= 0:
+        P.spmv_set_variant(M, args.variant, args.tile)
     for _ in range(args.warmup):
         P.spmv_apply(M, x, y)
     torch.cuda.synchronize()

@@ -292,25 +292,48 @@ def spread_offsets_csr(n, offsets, vals):
     return np.array(rowptr, np.int64), np.array(col, np.int32), np.array(val, np.float64)
 
 
-def test_fast_order_unstaged_kernel():
-    """A union of displacements too spread out for shared-memory tiles (nine
-    segments) takes the direct FAST kernel; same bounds apply."""
-    offs = [-12000, -9000, -6000, -3000, 0, 3000, 6000, 9000, 12000]
-    vals = [-1.0, 0.5, -1.0, 0.25, 6.0, 0.25, -1.0, 0.5, -1.0]
-    rowptr, col, val = spread_offsets_csr(30000, offs, vals)
-    A = P.spmv_build_csr(rowptr, col, val)
-    C = P.spmv_compress(A, format="pattern", order="fast")
+def test_fast_order_every_variant():
+    """Each FAST kernel (direct, staged tiles, pre-converted x) against the
+    oracle, including unions too spread out to stage."""
     x = spmv_inputs.uniform_vector(30000, seed=8)
-    y = run(C, x)
-    assert P.spmv_info(C)["fast_tile_rows"] == 0
-    y_ref = oracle.spmv(rowptr, col, val, x)
-    check_fast(y, y_ref, abs_row_sums(rowptr, col, val, x))
-    # the staged kernel for a milder spread
-    rowptr2, col2, val2 = spread_offsets_csr(30000, [-600, -1, 0, 1, 600], [-1.0, -2.0, 8.0, -2.0, -1.0])
-    C2 = P.spmv_compress(P.spmv_build_csr(rowptr2, col2, val2), format="pattern", order="fast")
-    y2 = run(C2, x)
-    assert P.spmv_info(C2)["fast_tile_rows"] > 0
-    check_fast(y2, oracle.spmv(rowptr2, col2, val2, x), abs_row_sums(rowptr2, col2, val2, x))
+    cases = [
+        # eight displacements: no compiled slot count, direct kernel only
+        ([-12000, -9000, -6000, -3000, 0, 3000, 6000, 9000], [-1.0, 0.5, -1.0, 0.25, 6.0, 0.25, -1.0, 0.5], [0]),
+        # nine spread displacements: nine segments, too many to stage
+        ([-12000, -9000, -6000, -3000, 0, 3000, 6000, 9000, 12000],
+         [-1.0, 0.5, -1.0, 0.25, 6.0, 0.25, -1.0, 0.5, -1.0], [0, 2]),
+        # a compact 5-slot union: every variant and tile
+        ([-600, -1, 0, 1, 600], [-1.0, -2.0, 8.0, -2.0, -1.0], [0, 1, 2]),
+    ]
+    for offs, vals, variants in cases:
+        rowptr, col, val = spread_offsets_csr(30000, offs, vals)
+        C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+        y_ref = oracle.spmv(rowptr, col, val, x)
+        scale = abs_row_sums(rowptr, col, val, x)
+        for v in variants:
+            tiles = [512, 1024, 2048] if v == 1 else [0]
+            for t in tiles:
+                P.spmv_set_variant(C, v, t)
+                assert P.spmv_info(C)["fast_variant"] == v
+                check_fast(run(C, x), y_ref, scale)
+        if 1 not in variants:
+            with pytest.raises(P.SpmvError):
+                P.spmv_set_variant(C, 1, 1024)
+
+
+def test_fast_variants_on_hpcg_grids():
+    for g in [(17, 17, 17), (33, 9, 5), (64, 48, 40)]:
+        rowptr, col, val = oracle.hpcg_csr(*g)
+        n = len(rowptr) - 1
+        x = spmv_inputs.uniform_vector(n, seed=1)
+        y_ref = oracle.spmv(rowptr, col, val, x)
+        scale = abs_row_sums(rowptr, col, val, x)
+        C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+        for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0)]:
+            P.spmv_set_variant(C, v, t)
+            check_fast(run(C, x), y_ref, scale)
+            xi = spmv_inputs.integer_vector(n, seed=2)
+            assert np.array_equal(run(C, xi), oracle.spmv(rowptr, col, val, xi))
 
 
 def test_autotune_keeps_results():
@@ -322,8 +345,11 @@ def test_autotune_keeps_results():
     x = torch.from_numpy(x_np).cuda()
     y = torch.empty_like(x)
     rows = P.spmv_autotune(C, x, y, reps=3)
-    assert rows in (512, 1024, 2048)
-    assert P.spmv_info(C)["fast_tile_rows"] == rows
+    assert rows in (1, 512, 1024, 2048)
+    info = P.spmv_info(C)
+    assert info["fast_variant"] == (2 if rows == 1 else 1)
+    if rows != 1:
+        assert info["fast_tile_rows"] == rows
     y_ref = oracle.spmv(rowptr, col, val, x_np)
     check_fast(run(C, x_np), y_ref, abs_row_sums(rowptr, col, val, x_np))
     # ELL and COLUMN order have nothing to tune
