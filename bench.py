@@ -182,9 +182,13 @@ def main():
     x = torch.from_numpy(x_np).to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    tile_rows = P.spmv_autotune(C, x, y)
+    P.spmv_autotune(C, x, y)
     info_c = P.spmv_info(C)
-    launches_per_step = 1 if info_c["fast_tile_rows"] > 0 else 2
+    variant = info_c["fast_variant"]
+    launches_per_step = {0: 2, 1: 1, 2: 3}[variant]
+    kernel_desc = {0: "xmax pre-pass + pattern_fast_kernel",
+                   1: "pattern_fast_staged_kernel (%d-row shared-memory tiles)" % info_c["fast_tile_rows"],
+                   2: "xmax + convert_x pre-passes + pattern_fast_x_kernel"}[variant]
 
     def timed(M, steps):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -250,8 +254,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": ("pattern_fast_staged_kernel (one launch per step, %d-row tiles)" % info_c["fast_tile_rows"]
-                                if launches_per_step == 1 else "xmax pre-pass + pattern_fast_kernel"),
+                     "kernel": kernel_desc,
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peaks["source"]},
         "ell": {"gflops": world * flops / (ell_ms * 1e-3) / 1e9, "ms_per_step": ell_ms,
                 "achieved_gbs": ell_alg_bytes / (ell_ms * 1e-3) / 1e9,

@@ -176,6 +176,16 @@ int ensure_device(spmv_mat_s* m) {
         std::memcpy(&v.mult_hi, tbl + 4, 4);
         v.mult_exp = p.mult_exp;
         v.err = m->d_err;
+        // runs of consecutive displacements, all of one length
+        v.run_len = 0;
+        for (int len : {3}) {
+            bool ok = v.nu > 0 && v.nu % len == 0;
+            for (int u = 0; ok && u < v.nu; ++u)
+                if (u % len != 0 && p.uoff[u] != p.uoff[u - 1] + 1) ok = false;
+            for (int u = len; ok && u < v.nu; u += len)
+                if (p.uoff[u] == p.uoff[u - 1] + 1) ok = false;  // runs are maximal
+            if (ok) v.run_len = len;
+        }
         m->stage_ok = false;
         m->fast_variant = 0;
         if (p.fast_ok && stage_supported(v.nu)) {

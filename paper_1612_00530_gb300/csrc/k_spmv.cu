@@ -130,9 +130,26 @@ __global__ void __launch_bounds__(kBlock) pattern_col_kernel(PatternView a, cons
 __global__ void __launch_bounds__(1024) xmax_kernel(const double* __restrict__ x, int64_t n,
                                                     uint32_t* __restrict__ partial) {
     uint32_t m = 0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride)
-        m = max(m, uint32_t(__double2hiint(__ldg(x + i))) & 0x7FFFFFFFu);
+    // doubles are 8-byte aligned; peel one element when x is not 16-byte
+    // aligned, then read two doubles per 16-byte load
+    const int64_t head = (n > 0 && (reinterpret_cast<uintptr_t>(x) & 15u)) ? 1 : 0;
+    const uint4* __restrict__ x2 = reinterpret_cast<const uint4*>(x + head);
+    const int64_t na = n - head, n2 = na / 2, stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + 3 * stride < n2; i += 4 * stride) {      // four independent loads in flight
+        const uint4 a = __ldg(x2 + i), b = __ldg(x2 + i + stride);
+        const uint4 c = __ldg(x2 + i + 2 * stride), d = __ldg(x2 + i + 3 * stride);
+        m = max(m, max(max(a.y & 0x7FFFFFFFu, a.w & 0x7FFFFFFFu), max(b.y & 0x7FFFFFFFu, b.w & 0x7FFFFFFFu)));
+        m = max(m, max(max(c.y & 0x7FFFFFFFu, c.w & 0x7FFFFFFFu), max(d.y & 0x7FFFFFFFu, d.w & 0x7FFFFFFFu)));
+    }
+    for (; i < n2; i += stride) {
+        const uint4 a = __ldg(x2 + i);
+        m = max(m, max(a.y & 0x7FFFFFFFu, a.w & 0x7FFFFFFFu));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (head) m = max(m, uint32_t(__double2hiint(__ldg(x))) & 0x7FFFFFFFu);
+        if (na > 0 && (na & 1)) m = max(m, uint32_t(__double2hiint(__ldg(x + n - 1))) & 0x7FFFFFFFu);
+    }
     m = __reduce_max_sync(0xFFFFFFFFu, m);
     __shared__ uint32_t sm[32];
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
@@ -255,21 +272,42 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_kernel(PatternView a, con
 // scratch copy with zero guard zones of `guard` elements on both sides, so
 // that the row kernel reads X[r + d] for every union displacement d without
 // a bounds check (out-of-range slots are absent ones, multiplier 0).
+__device__ __forceinline__ int2 limbs_of(uint32_t lo, uint32_t hi, uint32_t emax) {
+    const uint32_t k = emax - ((hi >> 20) & 0x7FFu);
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    uint64_t v;
+    asm("shr.b64 %0, %1, %2;" : "=l"(v) : "l"((uint64_t(mh) << 32) | lo), "r"(k));
+    const int32_t s1 = (int32_t(hi) >> 31) | 1;
+    return make_int2(int32_t(uint32_t(v) & 0x3FFFFFFu) * s1, int32_t(uint32_t(v >> 26)) * s1);
+}
+
 __global__ void __launch_bounds__(256) convert_x_kernel(const uint2* __restrict__ xw, int64_t n,
                                                         const uint32_t* __restrict__ partial,
                                                         int2* __restrict__ X) {
     __shared__ int s_emax;
     const uint32_t emax = uint32_t(block_emax(partial, &s_emax));
     if (emax < 64u || emax >= 2047u) return;   // the row kernel takes the exact path
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
-        const uint2 b = __ldg(xw + i);
-        const uint32_t k = emax - ((b.y >> 20) & 0x7FFu);
-        const uint32_t mh = (b.y & 0xFFFFFu) | 0x100000u;
-        uint64_t v;
-        asm("shr.b64 %0, %1, %2;" : "=l"(v) : "l"((uint64_t(mh) << 32) | b.x), "r"(k));
-        const int32_t s1 = (int32_t(b.y) >> 31) | 1;
-        X[i] = make_int2(int32_t(uint32_t(v) & 0x3FFFFFFu) * s1, int32_t(uint32_t(v >> 26)) * s1);
+    // peel one element when x is not 16-byte aligned, then two per load
+    const int64_t head = (n > 0 && (reinterpret_cast<uintptr_t>(xw) & 15u)) ? 1 : 0;
+    const uint4* __restrict__ x2 = reinterpret_cast<const uint4*>(xw + head);
+    int2* __restrict__ Xh = X + head;
+    const int64_t na = n - head, n2 = na / 2, stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + stride < n2; i += 2 * stride) {
+        const uint4 a = __ldcs(x2 + i), b = __ldcs(x2 + i + stride);
+        Xh[2 * i] = limbs_of(a.x, a.y, emax);
+        Xh[2 * i + 1] = limbs_of(a.z, a.w, emax);
+        Xh[2 * (i + stride)] = limbs_of(b.x, b.y, emax);
+        Xh[2 * (i + stride) + 1] = limbs_of(b.z, b.w, emax);
+    }
+    for (; i < n2; i += stride) {
+        const uint4 a = __ldcs(x2 + i);
+        Xh[2 * i] = limbs_of(a.x, a.y, emax);
+        Xh[2 * i + 1] = limbs_of(a.z, a.w, emax);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (head) { const uint2 b = __ldg(xw); X[0] = limbs_of(b.x, b.y, emax); }
+        if (na > 0 && (na & 1)) { const uint2 b = __ldg(xw + n - 1); X[n - 1] = limbs_of(b.x, b.y, emax); }
     }
 }
 
@@ -277,7 +315,7 @@ __device__ __forceinline__ void mad_wide_x(int64_t& acc, int32_t a, int32_t b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-template <int WORDS, int NU>
+template <int WORDS, int NU, int RUN>
 __global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
                                                                 const int2* __restrict__ X,
                                                                 double* __restrict__ y,
@@ -306,11 +344,18 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, c
     const int2* __restrict__ Xr = X + r;
     int64_t acc_h = 0, acc_l = 0;
 #pragma unroll
-    for (int u = 0; u < NU; ++u) {
-        const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-        const int2 v = __ldg(Xr + a.uoff[u]);
-        mad_wide_x(acc_h, m, v.y);
-        mad_wide_x(acc_l, m, v.x);
+    for (int k = 0; k < NU / RUN; ++k) {
+        // one pointer per run of RUN consecutive displacements; the run's
+        // slots are then immediate offsets from it
+        const int2* __restrict__ p = Xr + a.uoff[k * RUN];
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) {
+            const int u = k * RUN + j;
+            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+            const int2 v = __ldg(p + j);
+            mad_wide_x(acc_h, m, v.y);
+            mad_wide_x(acc_l, m, v.x);
+        }
     }
     y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, emax - 1075 + a.mult_exp);
 }
@@ -341,7 +386,7 @@ __device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t e
     return make_int2(int32_t(uint32_t(X) & 0x3FFFFFFu) * s1, int32_t(uint32_t(X >> 26)) * s1);
 }
 
-template <int WORDS, int NU, int RPT>
+template <int WORDS, int NU, int RPT, int RUN>
 __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
                                                                             const double* __restrict__ x,
                                                                             double* __restrict__ y) {
@@ -412,11 +457,16 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
         for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
         int64_t acc_h = 0, acc_l = 0;
 #pragma unroll
-        for (int u = 0; u < NU; ++u) {
-            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-            const int2 X = sx[rl + sp.soff[u]];
-            mad_wide(acc_h, m, X.y);
-            mad_wide(acc_l, m, X.x);
+        for (int k = 0; k < NU / RUN; ++k) {
+            const int2* p = sx + rl + sp.soff[k * RUN];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                const int u = k * RUN + j;
+                const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+                const int2 X = p[j];
+                mad_wide(acc_h, m, X.y);
+                mad_wide(acc_l, m, X.x);
+            }
         }
         y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, int(emax) - 1075 + a.mult_exp);
     }
@@ -689,6 +739,9 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
     const size_t smem = size_t(sp.elems) * sizeof(int2);
     auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     int(cudaSharedmemCarveoutMaxShared));
         if (e != cudaSuccess) return e;
         kernel<<<grid, kStageThreads, smem, s>>>(a, sp, x, y);
         return cudaGetLastError();
@@ -697,10 +750,16 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
     // 5-point ones are compiled with a fixed slot count
 #define SPMVC_NU_CASE(NUV)                                                             \
     case NUV:                                                                          \
-        if (sp.rows_per_thread == 1) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 1>); \
-        if (sp.rows_per_thread == 2) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 2>); \
-        if (sp.rows_per_thread == 4) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 4>); \
+        if (sp.rows_per_thread == 1) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 1, 1>); \
+        if (sp.rows_per_thread == 2) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 2, 1>); \
+        if (sp.rows_per_thread == 4) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 4, 1>); \
         return cudaErrorInvalidValue;
+    if (a.run_len == 3 && a.nu == 27) {
+        if (sp.rows_per_thread == 1) return go(pattern_fast_staged_kernel<7, 27, 1, 3>);
+        if (sp.rows_per_thread == 2) return go(pattern_fast_staged_kernel<7, 27, 2, 3>);
+        if (sp.rows_per_thread == 4) return go(pattern_fast_staged_kernel<7, 27, 4, 3>);
+        return cudaErrorInvalidValue;
+    }
     switch (a.nu) {
         SPMVC_NU_CASE(27)
         SPMVC_NU_CASE(19)
@@ -720,8 +779,12 @@ cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double*
     convert_x_kernel<<<kXmaxBlocks * 8, 256, 0, s>>>(reinterpret_cast<const uint2*>(x), a.n, partial, X);
     const unsigned grid = grid_of(a.n);
 #define SPMVC_NU_X(NUV) \
-    case NUV: pattern_fast_x_kernel<(NUV + 4) / 4, NUV><<<grid, kBlock, 0, s>>>(a, x, X, y, partial); break;
-    switch (a.nu) {
+    case NUV: pattern_fast_x_kernel<(NUV + 4) / 4, NUV, 1><<<grid, kBlock, 0, s>>>(a, x, X, y, partial); break;
+    if (a.run_len == 3 && a.nu == 27)
+        pattern_fast_x_kernel<7, 27, 3><<<grid, kBlock, 0, s>>>(a, x, X, y, partial);
+    else if (a.run_len == 3 && a.nu == 9)
+        pattern_fast_x_kernel<3, 9, 3><<<grid, kBlock, 0, s>>>(a, x, X, y, partial);
+    else switch (a.nu) {
         SPMVC_NU_X(27)
         SPMVC_NU_X(19)
         SPMVC_NU_X(9)

@@ -110,6 +110,8 @@ struct PatternView {
     const float* dict32;
     uint32_t mult_lo, mult_hi;      // fast order: int8 multipliers, absent -> 0
     int32_t mult_exp;
+    int32_t run_len;                // the union is nu/run_len runs of run_len consecutive
+                                    // displacements (0 when it is not so split)
     int32_t* err;                   // sticky device error word
 };
 

@@ -329,11 +329,20 @@ def test_fast_variants_on_hpcg_grids():
         y_ref = oracle.spmv(rowptr, col, val, x)
         scale = abs_row_sums(rowptr, col, val, x)
         C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+        xi = spmv_inputs.integer_vector(n, seed=2)
+        yi_ref = oracle.spmv(rowptr, col, val, xi)
+        # x one element into a buffer: 8-byte but not 16-byte aligned
+        xbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+        xbuf[1:] = torch.from_numpy(x).cuda()
+        xoff = xbuf[1:]
         for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0)]:
             P.spmv_set_variant(C, v, t)
             check_fast(run(C, x), y_ref, scale)
-            xi = spmv_inputs.integer_vector(n, seed=2)
-            assert np.array_equal(run(C, xi), oracle.spmv(rowptr, col, val, xi))
+            assert np.array_equal(run(C, xi), yi_ref)
+            y = torch.empty(n, dtype=torch.float64, device="cuda")
+            P.spmv_apply(C, xoff, y)
+            torch.cuda.synchronize()
+            check_fast(y.cpu().numpy(), y_ref, scale)
 
 
 def test_autotune_keeps_results():
