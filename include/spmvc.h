@@ -216,6 +216,25 @@ int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_
  * Copies A to the device if it is not there yet. */
 int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 
+/* Y = A X like spmm_apply, for callers that cannot allocate device memory
+ * (a framework that routes every device allocation through its own pool, a
+ * latency-critical loop that cannot afford the implicit synchronisation of
+ * cudaMalloc/cudaFree).  This call allocates nothing: its only scratch (the
+ * per-column maximum exponents of X, 152 words per column) is a fixed
+ * device array inside the library, present on every GPU that loads it.
+ * The paper has no counterpart; it is an interface convenience.
+ * Limits and rules:
+ *  - pattern-format A in SPMV_ORDER_FAST, already on the current device (an
+ *    earlier ordinary device call on A copies it there; this call never
+ *    does) -- otherwise SPMV_EUNSUPPORTED / SPMV_EINVAL;
+ *  - 1 <= k <= 32 (the scratch's size), ldx >= k, ldy >= k, else SPMV_EINVAL;
+ *  - the first call on each device looks up the scratch's device address
+ *    (no allocation); make that first call before any stream capture;
+ *  - all calls on a device share the one scratch array: calls whose
+ *    kernels can overlap on the GPU race and give wrong results. */
+int spmm_apply_noalloc(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
+                       int64_t ldy, spmv_stream_t stream);
+
 /* ---- ragged batches: one persistent launch over many matrices --------- */
 typedef struct spmv_batch_s *spmv_batch_t;
 

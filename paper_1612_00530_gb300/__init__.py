@@ -98,6 +98,7 @@ def library() -> ctypes.CDLL:
             "spmv_device_error": [_p, ctypes.POINTER(_i32)],
             "spmv_autotune": [_p, _p, _p, _i32, ctypes.POINTER(_i32)],
             "spmv_set_variant": [_p, _i32, _i32],
+            "spmm_apply_noalloc": [_p, _i32, _p, _i64, _p, _i64, _p],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -243,6 +244,14 @@ def spmm_apply(A: SpmvMatrix, X, Y, stream=None) -> None:
     k = X.shape[1]
     _check(library().spmm_apply(A, k, _dptr(X, "float64"), X.stride(0), _dptr(Y, "float64"), Y.stride(0),
                                 _stream(stream)))
+
+
+def spmm_apply_noalloc(A: SpmvMatrix, X, Y, stream=None) -> None:
+    """Y = A X without any device allocation (pattern format, FAST order, A
+    already on the device, at most 32 columns); see include/spmvc.h."""
+    k = X.shape[1]
+    _check(library().spmm_apply_noalloc(A, k, _dptr(X, "float64"), X.stride(0), _dptr(Y, "float64"), Y.stride(0),
+                                        _stream(stream)))
 
 
 class SpmvBatch:
