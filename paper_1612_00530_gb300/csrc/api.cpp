@@ -160,6 +160,13 @@ int ensure_device(spmv_mat_s* m) {
         if (q16 >= 2) { if ((st = upload_plane(4, 4, &ptr))) return st; v.p16b = static_cast<const uint4*>(ptr); }
         if (rem >= 2) { if ((st = upload_plane(4 * q16, 2, &ptr))) return st; v.p8 = static_cast<const uint2*>(ptr); }
         if (rem & 1) { if ((st = upload_plane(p.words - 1, 1, &ptr))) return st; v.p4 = static_cast<const uint32_t*>(ptr); }
+        {
+            std::vector<uint32_t> pm(32, 0u);
+            for (int q = 0; q < v.npat; ++q) pm[q] = p.pmask[q];
+            uint32_t* d;
+            if ((st = dev_copy(m, pm.data(), pm.size(), &d))) return st;
+            v.pmask_dev = d;
+        }
         std::vector<double> dict(p.dict);
         std::vector<float> dict32;
         for (double d : dict) dict32.push_back(static_cast<float>(d));

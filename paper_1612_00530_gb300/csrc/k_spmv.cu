@@ -187,7 +187,7 @@ __device__ __forceinline__ void to_fixed(double xv, int emax, int32_t& xh, int32
 
 // acc * 2^S rounded to nearest-even, integer operations only (subnormal
 // results are rounded to their shorter precision, overflow gives +-inf).
-__device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
+__device__ __noinline__ double fixed_to_double_int(int64_t acc, int S) {
     if (acc == 0) return 0.0;
     const uint64_t sgn = acc < 0 ? 0x8000000000000000ull : 0ull;
     uint64_t a = acc < 0 ? uint64_t(0) - uint64_t(acc) : uint64_t(acc);
@@ -212,6 +212,18 @@ __device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
         bits = mant;  // subnormal; a carry to 2^52 becomes the smallest normal
     }
     return __longlong_as_double(int64_t(sgn | bits));
+}
+
+// acc * 2^S rounded to nearest-even.  The int64 -> binary64 conversion
+// rounds once (RN); scaling by 2^S is then an exact add to the exponent
+// field unless the result leaves the normal range, which the integer
+// routine above handles.
+__device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
+    const double d = __ll2double_rn(acc);
+    const int32_t hi = __double2hiint(d);
+    const int e = ((hi >> 20) & 0x7FF) + S;
+    if (acc != 0 && (e < 1 || e > 2046)) return fixed_to_double_int(acc, S);
+    return acc == 0 ? 0.0 : __hiloint2double(hi + (S << 20), __double2loint(d));
 }
 
 template <int WORDS>
@@ -282,10 +294,11 @@ __device__ __forceinline__ int2 limbs_of(uint32_t lo, uint32_t hi, uint32_t emax
 }
 
 __global__ void __launch_bounds__(256) convert_x_kernel(const uint2* __restrict__ xw, int64_t n,
-                                                        const uint32_t* __restrict__ partial,
+                                                        uint32_t* __restrict__ partial,
                                                         int2* __restrict__ X) {
     __shared__ int s_emax;
     const uint32_t emax = uint32_t(block_emax(partial, &s_emax));
+    if (blockIdx.x == 0 && threadIdx.x == 0) partial[kXmaxBlocks] = emax;
     if (emax < 64u || emax >= 2047u) return;   // the row kernel takes the exact path
     // peel one element when x is not 16-byte aligned, then two per load
     const int64_t head = (n > 0 && (reinterpret_cast<uintptr_t>(xw) & 15u)) ? 1 : 0;
@@ -311,25 +324,19 @@ __global__ void __launch_bounds__(256) convert_x_kernel(const uint2* __restrict_
     }
 }
 
-__device__ __forceinline__ void mad_wide_x(int64_t& acc, int32_t a, int32_t b) {
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
-}
-
 template <int WORDS, int NU, int RUN>
 __global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
                                                                 const int2* __restrict__ X,
                                                                 double* __restrict__ y,
                                                                 const uint32_t* __restrict__ partial) {
-    __shared__ uint32_t smask[32];
-    __shared__ int s_emax;
-    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
-    const int emax = block_emax(partial, &s_emax);
+    // the largest exponent of x, left by the conversion pass
+    const int emax = int(__ldg(partial + kXmaxBlocks));
     const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (r >= a.n) return;
     uint32_t w[kMaxRecordWords];
     load_record<WORDS>(a, r, w);
     if (emax < 64 || emax >= 2047) {
-        const uint32_t mask = smask[byte_of(w, NU) & 31];
+        const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
         double acc = 0.0;
 #pragma unroll
         for (int u = 0; u < NU; ++u)
@@ -353,8 +360,8 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, c
             const int u = k * RUN + j;
             const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
             const int2 v = __ldg(p + j);
-            mad_wide_x(acc_h, m, v.y);
-            mad_wide_x(acc_l, m, v.x);
+            acc_h += int64_t(m) * v.y;
+            acc_l += int64_t(m) * v.x;
         }
     }
     y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, emax - 1075 + a.mult_exp);
@@ -370,10 +377,6 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, c
 // addressed by absent slots, whose multiplier is 0.  Everything is integer:
 // x is moved as raw 64-bit words and never touches the FP64 pipe.
 constexpr int kStageThreads = 512;
-
-__device__ __forceinline__ void mad_wide(int64_t& acc, int32_t a, int32_t b) {
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
-}
 
 // (lo, hi) words of x -> limbs (xl, xh) of X = sign(x) floor(|x| 2^(1075-E)),
 // X = xh 2^26 + xl with both limbs carrying the sign.
@@ -464,8 +467,8 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
                 const int u = k * RUN + j;
                 const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
                 const int2 X = p[j];
-                mad_wide(acc_h, m, X.y);
-                mad_wide(acc_l, m, X.x);
+                acc_h += int64_t(m) * X.y;
+                acc_l += int64_t(m) * X.x;
             }
         }
         y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, int(emax) - 1075 + a.mult_exp);

@@ -106,6 +106,7 @@ struct PatternView {
     const uint4* p16b;              // words 4..7 (words == 8)
     const uint2* p8;                // words 4..5 (words 6,7)
     const uint32_t* p4;             // last odd word
+    const uint32_t* pmask_dev;      // device copy of pmask
     const double* dict;             // device copy of the value table
     const float* dict32;
     uint32_t mult_lo, mult_hi;      // fast order: int8 multipliers, absent -> 0

@@ -363,3 +363,46 @@ def test_autotune_keeps_results():
     check_fast(run(C, x_np), y_ref, abs_row_sums(rowptr, col, val, x_np))
     # ELL and COLUMN order have nothing to tune
     assert P.spmv_autotune(P.spmv_build("hpcg", *g), x, y) == 0
+
+
+def fast_order_exact_model(rowptr, col, mult, mult_exp, x):
+    """What FAST order computes, in exact integer arithmetic: every x_j
+    truncated to fixed point with 2^(1075-E) scaling (E = largest biased
+    exponent of x), each row summed exactly, then one rounding to nearest."""
+    from fractions import Fraction
+    bits = x.view(np.uint64)
+    E = int(((bits >> np.uint64(52)) & np.uint64(0x7FF)).max())
+    X = []
+    for b in bits.tolist():
+        e = (b >> 52) & 0x7FF
+        mant = (b & ((1 << 52) - 1)) | (1 << 52)
+        k = E - e
+        v = mant >> k if k < 64 else 0
+        X.append(-v if b >> 63 else v)
+    out = np.empty(len(rowptr) - 1)
+    for i in range(len(rowptr) - 1):
+        s = sum(mult[k] * X[col[k]] for k in range(rowptr[i], rowptr[i + 1]))
+        out[i] = float(Fraction(s) * Fraction(2) ** (E - 1075 + mult_exp))
+    return out
+
+
+@pytest.mark.parametrize("vscale,xscale", [(1.0, 1.0), (2.0 ** -100, 2.0 ** -950), (2.0 ** -60, 2.0 ** -958),
+                                           (1.0, 3.0e5)])
+def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale):
+    """Bit-exact model check of every FAST kernel, including results in the
+    subnormal range (rounded by the integer routine)."""
+    g = (9, 7, 6)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    val = val * vscale
+    mult = np.where(val > 0, 26, -1).astype(np.int64)
+    mult_exp = int(np.round(np.log2(vscale)))
+    x = spmv_inputs.uniform_vector(n, seed=12) * xscale
+    want = fast_order_exact_model(rowptr, col, mult, mult_exp, x)
+    C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+    for v, t in [(0, 0), (1, 512), (1, 2048), (2, 0)]:
+        P.spmv_set_variant(C, v, t)
+        got = run(C, x)
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (v, t)
+    if vscale < 1e-20:
+        assert np.any((want != 0) & (np.abs(want) < 2.2250738585072014e-308))  # subnormal results occur
