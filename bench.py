@@ -147,6 +147,114 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_suite(args):
+    """One JSON line per further workload (irregular 128^3, CG vs IR-CG on
+    192^3, SpMM k = 1..32 on 160^3, the ragged batch).  Not the headline."""
+    import torch
+
+    import oracle
+    import paper_1612_00530_gb300 as P
+    import spmv_inputs
+    from paper_1612_00530_gb300 import build as lib_build
+
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = measured_peaks()
+
+    def time_ms(fn, steps, warm=3):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    # --- irregular 128^3: delta format (bit-exact) vs ELL
+    A = P.spmv_build("irregular", 128, 128, 128, seed=2)
+    C = P.spmv_compress(A)
+    ia, ic = P.spmv_info(A), P.spmv_info(C)
+    n, nnz = ic["n"], ic["nnz"]
+    x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=2)).to(dev)
+    y = torch.empty_like(x)
+    t_ell = time_ms(lambda: P.spmv_apply(A, x, y), 200)
+    t_d = time_ms(lambda: P.spmv_apply(C, x, y), 200)
+    emit({"workload": "irregular_128^3_seed2", "rows": n, "nnz": nnz,
+          "ell": {"gflops": 2 * nnz / t_ell / 1e6, "ms": t_ell, "gbs": (ia["format_bytes"] + 16 * n) / t_ell / 1e6},
+          "delta": {"gflops": 2 * nnz / t_d / 1e6, "ms": t_d, "gbs": (ic["format_bytes"] + 16 * n) / t_d / 1e6,
+                    "format_bytes_per_nnz": ic["format_bytes"] / nnz, "dict_size": ic["dict_size"],
+                    "slices_value_raw_frac": ic["slices_value_raw"] / ic["n_slices"],
+                    "slices_col_raw_frac": ic["slices_col_raw"] / ic["n_slices"]},
+          "peak_gbs": peaks["hbm_gbs"], "order": "column (bit-exact)"})
+    del A, C, x, y
+
+    # --- CG vs IR-CG on 192^3, b = A 1, x0 = 0, tol 1e-10
+    A = P.spmv_build("hpcg", 192, 192, 192)
+    C = P.spmv_compress(A, format="pattern", order="fast")
+    n = P.spmv_info(C)["n"]
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    b = torch.empty_like(ones)
+    Ccol = P.spmv_compress(A, format="pattern", order="column")
+    P.spmv_apply(Ccol, ones, b)            # b = A 1 exactly (integer sums)
+    del Ccol
+    xx = torch.zeros_like(b)
+    P.spmv_autotune(C, ones, xx)
+    res = {}
+    for mode in ("fp64", "ir_fp32"):
+        xx.zero_()
+        r = P.cg_solve(C, b, xx, tol=1e-10, mode=mode, max_iter=5000)
+        err = float((xx - 1.0).abs().max())
+        res[mode] = {"seconds": r["seconds"], "iterations": r["iterations"], "outer": r["outer_iterations"],
+                     "rel_residual": r["rel_residual"], "max_abs_err_x_minus_1": err,
+                     "status": r["status"], "history_head": r["history"][:4], "history_tail": r["history"][-3:]}
+    emit({"workload": "cg_192^3_b_eq_A1_tol1e-10", "rows": n, "spmv_order": "fast", **res,
+          "ir_speedup": res["fp64"]["seconds"] / res["ir_fp32"]["seconds"]})
+    del A, C, b, xx, ones
+
+    # --- SpMM on 160^3, k = 1, 4, 8, 16, 32 (X seed 3)
+    A = P.spmv_build("hpcg", 160, 160, 160)
+    Cf = P.spmv_compress(A, format="pattern", order="fast")
+    Cc = P.spmv_compress(A, format="pattern", order="column")
+    n, nnz = P.spmv_info(Cf)["n"], P.spmv_info(Cf)["nnz"]
+    out = {}
+    for k in (1, 4, 8, 16, 32):
+        X = torch.from_numpy(spmv_inputs.uniform_matrix(n, k, seed=3)).to(dev)
+        Y = torch.empty_like(X)
+        tf = time_ms(lambda: P.spmm_apply(Cf, X, Y), 20)
+        tc = time_ms(lambda: P.spmm_apply(Cc, X, Y), 5, warm=1)
+        out[f"k{k}"] = {"fast_gflops": 2 * nnz * k / tf / 1e6, "fast_ms": tf,
+                        "column_gflops": 2 * nnz * k / tc / 1e6, "column_ms": tc,
+                        "fast_gbs_alg": (nnz + n * 5 / 8 + 16 * n * k) / tf / 1e6}
+        del X, Y
+    emit({"workload": "spmm_160^3_X_seed3", "rows": n, "nnz": nnz, **out})
+    del A, Cf, Cc
+
+    # --- ragged batch: 24 cubes, edges U{16..96} (seed 4), one graph launch
+    edges = spmv_inputs.grid_edges(24, seed=4)
+    mats, xs, ys = [], [], []
+    tot_nnz = 0
+    for bidx, e in enumerate(edges):
+        M = P.spmv_compress(P.spmv_build("hpcg", e, e, e), format="pattern")
+        mats.append(M)
+        tot_nnz += P.spmv_info(M)["nnz"]
+        xs.append(torch.from_numpy(spmv_inputs.uniform_vector(e ** 3, seed=100 + bidx)).to(dev))
+        ys.append(torch.empty_like(xs[-1]))
+    plan = P.spmv_batch_create(mats, xs, ys)
+    tb = time_ms(lambda: P.spmv_batch_launch(plan), 50)
+    ts = time_ms(lambda: [P.spmv_apply(M, xv, yv) for M, xv, yv in zip(mats, xs, ys)], 20)
+    emit({"workload": "ragged_24_cubes_seed4", "edges": edges, "nnz": tot_nnz,
+          "batched_graph": {"ms": tb, "gflops": 2 * tot_nnz / tb / 1e6},
+          "one_launch_per_matrix": {"ms": ts, "gflops": 2 * tot_nnz / ts / 1e6},
+          "order": "column (bit-exact)"})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +262,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", action="store_true", help="measure the further workloads instead of the headline")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
@@ -164,6 +273,11 @@ def main():
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     if args.impl == "reference":
         run_reference(args, world, rank)
+        barrier(world)
+        return
+    if args.suite:
+        if rank == 0:
+            run_suite(args)
         barrier(world)
         return
 

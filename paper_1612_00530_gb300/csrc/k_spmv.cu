@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) convert_x_kernel(const uint2* __restrict_
 }
 
 template <int WORDS, int NU, int RUN>
-__global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, 3) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
                                                                 const int2* __restrict__ X,
                                                                 double* __restrict__ y,
                                                                 const uint32_t* __restrict__ partial) {
@@ -345,26 +345,30 @@ __global__ void __launch_bounds__(kBlock) pattern_fast_x_kernel(PatternView a, c
         y[r] = acc;
         return;
     }
+    // every load first (one pointer per run of RUN consecutive
+    // displacements, the run's other slots at immediate offsets), so that
+    // all of a row's memory requests are in flight together
+    const int2* __restrict__ Xr = X + r;
+    int2 v[NU];
+#pragma unroll
+    for (int k = 0; k < NU / RUN; ++k) {
+        const int2* __restrict__ p = Xr + a.uoff[k * RUN];
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) v[k * RUN + j] = __ldg(p + j);
+    }
     uint32_t mw[(NU + 3) / 4];
 #pragma unroll
     for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
-    const int2* __restrict__ Xr = X + r;
-    int64_t acc_h = 0, acc_l = 0;
+    // three independent accumulator pairs shorten the dependency chains
+    int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < NU / RUN; ++k) {
-        // one pointer per run of RUN consecutive displacements; the run's
-        // slots are then immediate offsets from it
-        const int2* __restrict__ p = Xr + a.uoff[k * RUN];
-#pragma unroll
-        for (int j = 0; j < RUN; ++j) {
-            const int u = k * RUN + j;
-            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-            const int2 v = __ldg(p + j);
-            acc_h += int64_t(m) * v.y;
-            acc_l += int64_t(m) * v.x;
-        }
+    for (int u = 0; u < NU; ++u) {
+        const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+        ah[u % 3] += int64_t(m) * v[u].y;
+        al[u % 3] += int64_t(m) * v[u].x;
     }
-    y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, emax - 1075 + a.mult_exp);
+    const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
+    y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
 }
 
 // ---------------------------------------------- FAST order, staged -------
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
         uint32_t mw[(NU + 3) / 4];
 #pragma unroll
         for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
-        int64_t acc_h = 0, acc_l = 0;
+        int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
 #pragma unroll
         for (int k = 0; k < NU / RUN; ++k) {
             const int2* p = sx + rl + sp.soff[k * RUN];
@@ -467,11 +471,12 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
                 const int u = k * RUN + j;
                 const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
                 const int2 X = p[j];
-                acc_h += int64_t(m) * X.y;
-                acc_l += int64_t(m) * X.x;
+                ah[u % 3] += int64_t(m) * X.y;
+                al[u % 3] += int64_t(m) * X.x;
             }
         }
-        y[r] = fixed_to_double(acc_h * (int64_t(1) << 26) + acc_l, int(emax) - 1075 + a.mult_exp);
+        const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
+        y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
     }
 }
 
