@@ -36,6 +36,34 @@ METRIC = "SpMV GFLOP/s + % HBM roofline, compressed vs plain ELL, 192^3 HPCG, 1 
 WORKLOAD = "hpcg_192^3_x_seed1_compressed_pattern_uint8codes_5bit_patterns_vs_ell"
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_1612_00530_gb300", "csrc", "k_spmv.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """dram read+write bytes per launch of `kernel` from the committed ncu
+    summary in profiles/, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "spmv_fast_hpcg192.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic:"):
+                parts = dict(p.split("=", 1) for p in line.split()[1:] if "=" in p)
+                if parts.get("kernel") == kernel:
+                    fields = parts
+    if fields.get("source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(fields["bytes"])
+    except (KeyError, ValueError):
+        return None
+
+
 def measured_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -300,6 +328,7 @@ def main():
     info_c = P.spmv_info(C)
     variant = info_c["fast_variant"]
     launches_per_step = {0: 2, 1: 1, 2: 3}[variant]
+    kernel_id = {0: "direct", 1: "staged%d" % info_c["fast_tile_rows"], 2: "preconverted"}[variant]
     kernel_desc = {0: "xmax pre-pass + pattern_fast_kernel",
                    1: "pattern_fast_staged_kernel (%d-row shared-memory tiles)" % info_c["fast_tile_rows"],
                    2: "xmax + convert_x pre-passes + pattern_fast_x_kernel"}[variant]
@@ -367,8 +396,8 @@ def main():
                    "l2": f"inputs {(info_c['format_bytes'] + 16 * n) / 1e6:.0f} MB > 129 MB L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": kernel_desc,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(kernel_id),
+                     "kernel": kernel_desc, "kernel_id": kernel_id,
                      "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peaks["source"]},
         "ell": {"gflops": world * flops / (ell_ms * 1e-3) / 1e9, "ms_per_step": ell_ms,
                 "achieved_gbs": ell_alg_bytes / (ell_ms * 1e-3) / 1e9,

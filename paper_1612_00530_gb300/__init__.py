@@ -298,7 +298,12 @@ def spmv_apply_batched(mats, xs, ys, stream=None) -> None:
 def cg_solve(A: SpmvMatrix, b, x, tol: float = 1e-10, max_iter: int = 10000, mode: str = "fp64",
              check_every: int = 16, inner_max_iter: int = 60, inner_tol: float = 1e-5,
              use_graph: bool = True) -> dict:
-    o = spmv_cg_opts(tol, max_iter, CG_MODES[mode], check_every, inner_max_iter, inner_tol, 1, 1 if use_graph else 0)
+    """Solves A x = b; b and x are CUDA float64 of shape (n,) or (n, nrhs)."""
+    nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if tuple(x.shape) != tuple(b.shape):
+        raise ValueError("x and b must have the same shape")
+    o = spmv_cg_opts(tol, max_iter, CG_MODES[mode], check_every, inner_max_iter, inner_tol, nrhs,
+                     1 if use_graph else 0)
     r = spmv_cg_result()
     lib = library()
     st = _check(lib.cg_solve(A, _dptr(b, "float64"), _dptr(x, "float64"), ctypes.byref(o), ctypes.byref(r)),

@@ -23,7 +23,7 @@ void derive_fast_order(int64_t n, PatternFormat* p);
 namespace {
 thread_local std::string g_last_error;
 constexpr uint32_t kMagic = 0x5350564du;
-constexpr int kPartialWords = 152 * 64;
+constexpr int kPartialWords = 152 * 64 + 64;
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -519,7 +519,19 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y,
     const cudaStream_t s = as_stream(stream);
     cudaError_t e;
     if (A->fmt == SPMV_FMT_ELL) e = launch_ell_spmm(A->ell_view, k, X, ldx, Y, ldy, s);
-    else if (A->fmt == SPMV_FMT_PATTERN)
+    else if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->d_xfixed &&
+             A->pat_view.run_len == 3 && A->pat_view.nu == 27) {
+        // fixed-point copy of X with guard rows, grown to the widest k seen
+        if (A->xfixed_block_cols < k) {
+            int2* xf;
+            const int kc = k <= 8 ? 8 : (k <= 32 ? 32 : 64);
+            if ((st = dev_copy<int2>(A, nullptr, static_cast<size_t>(A->n + 2 * A->xfixed_guard) * kc, &xf))) return st;
+            A->d_xfixed_block = xf;
+            A->xfixed_block_cols = kc;
+        }
+        e = launch_pattern_spmm_fast_x(A->pat_view, k, X, ldx, Y, ldy, A->d_scratch_words, A->d_xfixed_block,
+                                       A->xfixed_guard, s);
+    } else if (A->fmt == SPMV_FMT_PATTERN)
         e = A->order == SPMV_ORDER_FAST
                 ? launch_pattern_spmm_fast(A->pat_view, k, X, ldx, Y, ldy, A->d_scratch_words, s)
                 : launch_pattern_spmm_col(A->pat_view, k, X, ldx, Y, ldy, s);

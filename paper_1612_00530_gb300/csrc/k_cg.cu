@@ -262,6 +262,141 @@ __global__ void sum_to_host_kernel(const double* __restrict__ partial, double* _
     if (threadIdx.x == 0) *out = s;
 }
 
+
+// ------------------------------------------- k right-hand sides at once ---
+// Vectors are n x k row-major; column j is an independent CG whose scalars
+// live in ColState.  A column whose residual is exactly zero freezes
+// (alpha = beta = 0).
+constexpr int kMaxCols = 32;
+struct ColState {
+    double rr[kMaxCols], alpha[kMaxCols], beta[kMaxCols], bnorm[kMaxCols];
+    double tol;
+    int32_t k, it, max_it, done;
+};
+
+// partial[b*k + j]: block b's sum over its rows of a[r,j]*b[r,j]
+__global__ void __launch_bounds__(kRedThreads) dot_cols_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                               int64_t n, int k, double* __restrict__ partial,
+                                                               const ColState* __restrict__ st) {
+    if (st && st->done) return;
+    __shared__ double sm[kRedThreads];
+    const int R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
+    double s = 0.0;
+    if (sub < R)
+        for (int64_t r = blockIdx.x * int64_t(R) + sub; r < n; r += int64_t(gridDim.x) * R)
+            s = fma(a[r * k + j], b[r * k + j], s);
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int i = 0; i < R; ++i) t += sm[i * k + threadIdx.x];
+        partial[blockIdx.x * k + threadIdx.x] = t;
+    }
+}
+
+__device__ __forceinline__ double sum_col(const double* __restrict__ partial, int k, int j) {
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += partial[b * k + j];
+    return s;
+}
+
+// alpha_j = rr_j / (p_j . q_j)
+__global__ void alpha_cols_kernel(const double* __restrict__ partial_pq, ColState* __restrict__ st) {
+    if (st->done) return;
+    const int j = threadIdx.x;
+    if (j >= st->k) return;
+    const double pq = sum_col(partial_pq, st->k, j);
+    st->alpha[j] = (st->rr[j] > 0.0 && pq != 0.0) ? st->rr[j] / pq : 0.0;
+}
+
+// x += alpha p; r -= alpha q; partial sums of r.r per column
+__global__ void __launch_bounds__(kRedThreads) update_xr_cols_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                                     const double* __restrict__ p,
+                                                                     const double* __restrict__ q, int64_t n,
+                                                                     double* __restrict__ partial_rr,
+                                                                     const ColState* __restrict__ st) {
+    if (st->done) return;
+    __shared__ double sm[kRedThreads];
+    const int k = st->k, R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
+    const double alpha = st->alpha[j];
+    double s = 0.0;
+    if (sub < R)
+        for (int64_t row = blockIdx.x * int64_t(R) + sub; row < n; row += int64_t(gridDim.x) * R) {
+            const int64_t i = row * k + j;
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            s = fma(ri, ri, s);
+        }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int i = 0; i < R; ++i) t += sm[i * k + threadIdx.x];
+        partial_rr[blockIdx.x * k + threadIdx.x] = t;
+    }
+}
+
+// beta_j, rr_j, history (largest relative residual), convergence
+__global__ void beta_cols_kernel(const double* __restrict__ partial_rr, ColState* __restrict__ st,
+                                 double* __restrict__ hist) {
+    if (st->done) return;
+    __shared__ double rel[kMaxCols];
+    const int j = threadIdx.x, k = st->k;
+    if (j < k) {
+        const double rr_new = sum_col(partial_rr, k, j);
+        st->beta[j] = st->rr[j] > 0.0 ? rr_new / st->rr[j] : 0.0;
+        st->rr[j] = rr_new;
+        rel[j] = sqrt(rr_new) / st->bnorm[j];
+    }
+    __syncthreads();
+    if (j == 0) {
+        double m = 0.0;
+        for (int c = 0; c < k; ++c) m = fmax(m, rel[c]);
+        st->it += 1;
+        hist[st->it] = m;
+        if (m <= st->tol || st->it >= st->max_it) st->done = 1;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) update_p_cols_kernel(double* __restrict__ p, const double* __restrict__ r,
+                                                                    int64_t n, const ColState* __restrict__ st) {
+    if (st->done) return;
+    const int k = st->k;
+    const int64_t total = n * k, stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += stride)
+        p[i] = fma(st->beta[i % k], p[i], r[i]);
+}
+
+// r = b - q, partial sums of r.r per column
+__global__ void __launch_bounds__(kRedThreads) residual_cols_kernel(const double* __restrict__ b,
+                                                                    const double* __restrict__ q,
+                                                                    double* __restrict__ r, int64_t n, int k,
+                                                                    double* __restrict__ partial) {
+    __shared__ double sm[kRedThreads];
+    const int R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
+    double s = 0.0;
+    if (sub < R)
+        for (int64_t row = blockIdx.x * int64_t(R) + sub; row < n; row += int64_t(gridDim.x) * R) {
+            const int64_t i = row * k + j;
+            const double ri = b[i] - q[i];
+            r[i] = ri;
+            s = fma(ri, ri, s);
+        }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int i = 0; i < R; ++i) t += sm[i * k + threadIdx.x];
+        partial[blockIdx.x * k + threadIdx.x] = t;
+    }
+}
+
+__global__ void col_sums_kernel(const double* __restrict__ partial, int k, double* __restrict__ out) {
+    const int j = threadIdx.x;
+    if (j < k) out[j] = sum_col(partial, k, j);
+}
+
 struct Workspace {
     std::vector<void*> allocs;
     ~Workspace() { for (void* p : allocs) cudaFree(p); }
@@ -320,6 +455,131 @@ int run_until_done(cudaStream_t s, bool use_graph, int chunk, CgState* d_st, int
     return rc;
 }
 
+
+// k right-hand sides at once (plain FP64 CG per column, products by SpMM)
+int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& o, spmv_cg_result* res) {
+    const int64_t n = A->n;
+    const int k = o.nrhs;
+    cudaStream_t s;
+    CG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } guard{s};
+    Workspace ws;
+    double* r = ws.get<double>(n * k);
+    double* q = ws.get<double>(n * k);
+    double* p = ws.get<double>(n * k);
+    double* part_a = ws.get<double>(size_t(kRedBlocks) * k);
+    double* part_b = ws.get<double>(size_t(kRedBlocks) * k);
+    double* d_sums = ws.get<double>(k);
+    ColState* d_st = ws.get<ColState>(1);
+    double* d_hist = ws.get<double>(o.max_iter + 2);
+    if (!r || !q || !p || !part_a || !part_b || !d_sums || !d_st || !d_hist) return fail(SPMV_ENOMEM, "CG workspace");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    CG_CUDA(cudaEventRecord(e0, s));
+    const unsigned G = kRedBlocks, T = kRedThreads;
+    std::vector<double> h(k);
+    auto col_norms2 = [&](const double* a) -> int {
+        dot_cols_kernel<<<G, T, 0, s>>>(a, a, n, k, part_a, nullptr);
+        col_sums_kernel<<<1, 64, 0, s>>>(part_a, k, d_sums);
+        CG_CUDA(cudaMemcpyAsync(h.data(), d_sums, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        CG_CUDA(cudaStreamSynchronize(s));
+        return SPMV_OK;
+    };
+    auto residual = [&]() -> int {
+        CG_ST(spmm_apply(A, k, x, k, q, k, s));
+        residual_cols_kernel<<<G, T, 0, s>>>(b, q, r, n, k, part_a);
+        col_sums_kernel<<<1, 64, 0, s>>>(part_a, k, d_sums);
+        CG_CUDA(cudaMemcpyAsync(h.data(), d_sums, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        CG_CUDA(cudaStreamSynchronize(s));
+        return SPMV_OK;
+    };
+    CG_ST(col_norms2(b));
+    ColState hs{};
+    hs.k = k;
+    hs.tol = o.tol;
+    hs.max_it = o.max_iter;
+    for (int j = 0; j < k; ++j) hs.bnorm[j] = std::sqrt(h[j]) > 0.0 ? std::sqrt(h[j]) : 1.0;
+    CG_ST(residual());
+    double rel0 = 0.0;
+    for (int j = 0; j < k; ++j) {
+        hs.rr[j] = h[j];
+        rel0 = std::max(rel0, std::sqrt(h[j]) / hs.bnorm[j]);
+    }
+    hs.done = rel0 <= o.tol ? 1 : 0;
+    CG_CUDA(cudaMemcpyAsync(d_st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+    CG_CUDA(cudaMemcpyAsync(d_hist, &rel0, sizeof(double), cudaMemcpyHostToDevice, s));
+    CG_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s));
+    auto body = [&]() -> int {
+        CG_ST(spmm_apply(A, k, p, k, q, k, s));
+        dot_cols_kernel<<<G, T, 0, s>>>(p, q, n, k, part_a, d_st);
+        alpha_cols_kernel<<<1, 64, 0, s>>>(part_a, d_st);
+        update_xr_cols_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_b, d_st);
+        beta_cols_kernel<<<1, 64, 0, s>>>(part_b, d_st, d_hist);
+        update_p_cols_kernel<<<G, T, 0, s>>>(p, r, n, d_st);
+        CG_CUDA(cudaGetLastError());
+        return SPMV_OK;
+    };
+    // done flag is the same field position as in CgState? use ColState's own
+    int32_t done = hs.done;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (o.use_graph) {
+        CG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int st = SPMV_OK;
+        for (int c = 0; c < o.check_every && !st; ++c) st = body();
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ge, g, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_err(e, "cudaGraphInstantiate"); }
+    }
+    const int replays = (o.max_iter + o.check_every - 1) / o.check_every + 1;
+    int rc = SPMV_OK;
+    for (int rep = 0; rep < replays && !done && !rc; ++rep) {
+        if (ge) {
+            cudaError_t e = cudaGraphLaunch(ge, s);
+            if (e != cudaSuccess) rc = cuda_err(e, "cudaGraphLaunch");
+        } else {
+            for (int c = 0; c < o.check_every && !rc; ++c) rc = body();
+        }
+        if (!rc) {
+            cudaError_t e = cudaMemcpyAsync(&done, &d_st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_err(e, "convergence flag");
+        }
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    CG_CUDA(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CG_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> history(hs.it + 1);
+    CG_CUDA(cudaMemcpy(history.data(), d_hist, sizeof(double) * (hs.it + 1), cudaMemcpyDeviceToHost));
+    CG_ST(residual());
+    double rel = 0.0;
+    for (int j = 0; j < k; ++j) rel = std::max(rel, std::sqrt(h[j]) / hs.bnorm[j]);
+    CG_CUDA(cudaEventRecord(e1, s));
+    CG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int status = (rel <= o.tol * 10.0 || history.back() <= o.tol) ? SPMV_OK : SPMV_ENOTCONVERGED;
+    if (res) {
+        res->status = status;
+        res->iterations = hs.it;
+        res->outer_iterations = 0;
+        res->rel_residual = rel;
+        res->seconds = ms * 1e-3;
+        res->history_len = static_cast<int32_t>(history.size());
+        res->history = static_cast<double*>(std::malloc(sizeof(double) * std::max<size_t>(1, history.size())));
+        if (!res->history) return fail(SPMV_ENOMEM, "history allocation");
+        std::memcpy(res->history, history.data(), sizeof(double) * history.size());
+    }
+    return status;
+}
+
 }  // namespace
 }  // namespace spmvc
 
@@ -335,12 +595,14 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     if (o.inner_max_iter <= 0) o.inner_max_iter = 60;
     if (o.inner_tol <= 0) o.inner_tol = 1e-5;
     if (o.nrhs <= 0) o.nrhs = 1;
-    if (o.nrhs != 1) return fail(SPMV_EUNSUPPORTED, "this build solves one right-hand side per call");
+    if (o.nrhs < 1 || o.nrhs > kMaxCols) return fail(SPMV_EINVAL, "nrhs must be 1..32");
+    if (o.nrhs > 1 && o.mode != SPMV_CG_FP64) return fail(SPMV_EUNSUPPORTED, "several right-hand sides: FP64 mode only");
     if (o.mode != SPMV_CG_FP64 && o.mode != SPMV_CG_IR_FP32) return fail(SPMV_EINVAL, "unknown CG mode");
     const int64_t n = A->n;
     if (n > 0 && (!b || !x)) return fail(SPMV_EINVAL, "null vector");
     if (res) std::memset(res, 0, sizeof(*res));
     CG_ST(api_ensure_device(A));
+    if (o.nrhs > 1) return cg_solve_cols(A, b, x, o, res);
     cudaStream_t s;
     CG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct StreamGuard { cudaStream_t s; ~StreamGuard() { cudaStreamDestroy(s); } } guard{s};

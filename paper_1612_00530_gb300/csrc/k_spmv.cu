@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) convert_x_kernel(const uint2* __restrict_
 }
 
 template <int WORDS, int NU, int RUN>
-__global__ void __launch_bounds__(kBlock, 3) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, 6) pattern_fast_x_kernel(PatternView a, const double* __restrict__ x,
                                                                 const int2* __restrict__ X,
                                                                 double* __restrict__ y,
                                                                 const uint32_t* __restrict__ partial) {
@@ -345,27 +345,25 @@ __global__ void __launch_bounds__(kBlock, 3) pattern_fast_x_kernel(PatternView a
         y[r] = acc;
         return;
     }
-    // every load first (one pointer per run of RUN consecutive
-    // displacements, the run's other slots at immediate offsets), so that
-    // all of a row's memory requests are in flight together
+    uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+    for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+    // one pointer per run of RUN consecutive displacements, the run's other
+    // slots at immediate offsets; three accumulator pairs shorten the
+    // dependency chains
     const int2* __restrict__ Xr = X + r;
-    int2 v[NU];
+    int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < NU / RUN; ++k) {
         const int2* __restrict__ p = Xr + a.uoff[k * RUN];
 #pragma unroll
-        for (int j = 0; j < RUN; ++j) v[k * RUN + j] = __ldg(p + j);
-    }
-    uint32_t mw[(NU + 3) / 4];
-#pragma unroll
-    for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
-    // three independent accumulator pairs shorten the dependency chains
-    int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
-#pragma unroll
-    for (int u = 0; u < NU; ++u) {
-        const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-        ah[u % 3] += int64_t(m) * v[u].y;
-        al[u % 3] += int64_t(m) * v[u].x;
+        for (int j = 0; j < RUN; ++j) {
+            const int u = k * RUN + j;
+            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+            const int2 v = __ldg(p + j);
+            ah[u % 3] += int64_t(m) * v.y;
+            al[u % 3] += int64_t(m) * v.x;
+        }
     }
     const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
     y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
@@ -478,6 +476,111 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
         y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
     }
+}
+
+
+
+// ------------------------------ SpMM, FAST order, pre-converted block X ---
+// Per-column largest exponents (one word per column, from the partial
+// maxima of xmax_cols_kernel), then X converted once into a fixed-point
+// copy with guard rows, then Y = A X with one thread per (row, column).
+__global__ void cols_emax_kernel(const uint32_t* __restrict__ partial, int k, uint32_t* __restrict__ emax) {
+    const int j = threadIdx.x;
+    if (j >= k) return;
+    uint32_t v = 0;
+    for (int b = 0; b < kXmaxBlocks; ++b) v = max(v, __ldg(partial + b * k + j));
+    emax[j] = v >> 20;
+}
+
+__global__ void __launch_bounds__(256) convert_cols_kernel(const double* __restrict__ X, int64_t ldx, int64_t n, int k,
+                                                           const uint32_t* __restrict__ emax,
+                                                           int2* __restrict__ Xf) {
+    const int64_t total = n * k, stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += stride) {
+        const int64_t r = e / k;
+        const int j = int(e - r * k);
+        const uint32_t E = __ldg(emax + j);
+        if (E < 64u || E >= 2047u) continue;   // that column takes the exact path
+        const uint2 b = __ldg(reinterpret_cast<const uint2*>(X + r * ldx + j));
+        Xf[e] = limbs_of(b.x, b.y, E);
+    }
+}
+
+template <int WORDS, int NU, int RUN>
+__global__ void __launch_bounds__(kBlock) pattern_spmm_fast_x_kernel(PatternView a, int k, const double* __restrict__ X,
+                                                                     int64_t ldx, const int2* __restrict__ Xf,
+                                                                     double* __restrict__ Y, int64_t ldy,
+                                                                     const uint32_t* __restrict__ emax_cols) {
+    const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t r = idx / k;
+    const int j = int(idx - r * k);
+    if (r >= a.n) return;
+    const int emax = int(__ldg(emax_cols + j));
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    if (emax < 64 || emax >= 2047) {
+        const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
+        double acc = 0.0;
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+            if ((mask >> u) & 1u)
+                acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __ldg(X + (r + a.uoff[u]) * ldx + j), acc);
+        Y[r * ldy + j] = acc;
+        return;
+    }
+    uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+    for (int q = 0; q < (NU + 3) / 4; ++q) mw[q] = prmt(a.mult_lo, a.mult_hi, prmt(w[q] | (w[q] >> 4), 0u, 0x0020u));
+    const int2* __restrict__ Xr = Xf + idx;   // row r, column j
+    int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < NU / RUN; ++q) {
+        const int2* __restrict__ p = Xr + int64_t(a.uoff[q * RUN]) * k;
+#pragma unroll
+        for (int i = 0; i < RUN; ++i) {
+            const int u = q * RUN + i;
+            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+            const int2 v = __ldg(p + int64_t(i) * k);
+            ah[u % 3] += int64_t(m) * v.y;
+            al[u % 3] += int64_t(m) * v.x;
+        }
+    }
+    const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
+    Y[r * ldy + j] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+}
+
+// ------------------------------------ binary32 COLUMN order, specialised -
+// y_i = fmaf chain over present slots in ascending column order (bit-equal
+// to the binary32 CSR product).  The union size is a compile-time constant;
+// runs of RUN consecutive displacements share one pointer; absent slots are
+// predicated off (their column may be outside [0, n)).
+template <int WORDS, int NU, int RUN>
+__global__ void __launch_bounds__(kBlock) pattern_f32_kernel(PatternView a, const float* __restrict__ x,
+                                                             float* __restrict__ y) {
+    __shared__ float sdict[256];
+    __shared__ uint32_t smask[32];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sdict[i] = i < a.dict_size ? a.dict32[i] : 0.0f;
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    __syncthreads();
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    const uint32_t pat = byte_of(w, NU);
+    if (pat >= uint32_t(a.npat)) raise_error(a.err, 1);
+    const uint32_t mask = smask[pat & 31];
+    const float* __restrict__ xr = x + r;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NU / RUN; ++k) {
+        const float* __restrict__ p = xr + a.uoff[k * RUN];
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) {
+            const int u = k * RUN + j;
+            if ((mask >> u) & 1u) acc = fmaf(sdict[byte_of(w, u)], __ldg(p + j), acc);
+        }
+    }
+    y[r] = acc;
 }
 
 // ------------------------------------------------------------ delta ------
@@ -729,6 +832,10 @@ cudaError_t launch_pattern_col_f64(const PatternView& a, const double* x, double
 }
 cudaError_t launch_pattern_col_f32(const PatternView& a, const float* x, float* y, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
+    if (a.run_len == 3 && a.nu == 27) {
+        pattern_f32_kernel<7, 27, 3><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y);
+        return cudaGetLastError();
+    }
     SPMVC_DISPATCH_WORDS(a.words, (pattern_col_kernel<W, float><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y)));
     return cudaGetLastError();
 }
@@ -863,6 +970,25 @@ cudaError_t launch_pattern_spmm_fast(const PatternView& a, int k, const double* 
                                       a, k, X, ldx, Y, ldy, partial)));
     return cudaGetLastError();
 }
+
+cudaError_t launch_pattern_spmm_fast_x(const PatternView& a, int k, const double* X, int64_t ldx, double* Y,
+                                       int64_t ldy, uint32_t* partial, int2* Xf_guarded, int64_t guard_rows,
+                                       cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (k > 64) return cudaErrorInvalidValue;
+    uint32_t* emax = partial + kXmaxBlocks * 64;   // k words after the partial maxima
+    int2* Xf = Xf_guarded + guard_rows * k;
+    xmax_cols_kernel<<<kXmaxBlocks, 256, 0, s>>>(X, a.n, k, ldx, partial);
+    cols_emax_kernel<<<1, 64, 0, s>>>(partial, k, emax);
+    convert_cols_kernel<<<kXmaxBlocks * 16, 256, 0, s>>>(X, ldx, a.n, k, emax, Xf);
+    const unsigned grid = grid_of(a.n * k);
+    if (a.run_len == 3 && a.nu == 27)
+        pattern_spmm_fast_x_kernel<7, 27, 3><<<grid, kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax);
+    else
+        return cudaErrorNotSupported;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ell_spmm(const EllView& a, int k, const double* X, int64_t ldx, double* Y, int64_t ldy,
                             cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;

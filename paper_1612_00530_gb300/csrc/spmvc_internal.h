@@ -165,6 +165,9 @@ cudaError_t launch_pattern_spmm_col(const PatternView& a, int k, const double* X
                                     double* Y, int64_t ldy, cudaStream_t s);
 cudaError_t launch_pattern_spmm_fast(const PatternView& a, int k, const double* X, int64_t ldx,
                                      double* Y, int64_t ldy, uint32_t* xmax_words, cudaStream_t s);
+cudaError_t launch_pattern_spmm_fast_x(const PatternView& a, int k, const double* X, int64_t ldx, double* Y,
+                                       int64_t ldy, uint32_t* partial, int2* Xf_guarded, int64_t guard_rows,
+                                       cudaStream_t s);
 cudaError_t launch_ell_spmm(const EllView& a, int k, const double* X, int64_t ldx, double* Y,
                             int64_t ldy, cudaStream_t s);
 cudaError_t launch_delta_spmm(const DeltaView& a, int k, const double* X, int64_t ldx, double* Y,
@@ -210,6 +213,8 @@ struct spmv_mat_s {
     int32_t fast_variant = 0;          // 0 direct, 1 staged tiles, 2 pre-converted x copy
     int2* d_xfixed = nullptr;          // FAST order: fixed-point copy of x with guard zones
     int64_t xfixed_guard = 0;
+    int2* d_xfixed_block = nullptr;    // FAST SpMM: fixed-point copy of X (guard rows), k_cap columns
+    int32_t xfixed_block_cols = 0;
     uint32_t* d_scratch_words = nullptr; // fast order: per-column max |x| words
     int64_t scratch_words = 0;
     // spmv_apply_host staging

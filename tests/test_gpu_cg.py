@@ -73,3 +73,37 @@ def test_cg_reports_not_converged():
     res = P.cg_solve(C, b, x, tol=1e-10, max_iter=5)
     assert res["status"] == P.SPMV_ENOTCONVERGED
     assert res["iterations"] == 5
+
+
+@pytest.mark.parametrize("k,order", [(4, "fast"), (8, "column"), (3, "fast")])
+def test_batched_cg_columns_match_oracle(k, order):
+    g = (14, 13, 12)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    import spmv_inputs
+    V = spmv_inputs.uniform_matrix(n, k, seed=21)
+    B_np = oracle.spmm(rowptr, col, val, V)
+    A = P.spmv_build("hpcg", *g)
+    C = P.spmv_compress(A, format="pattern", order=order)
+    B = torch.from_numpy(B_np).cuda()
+    X = torch.zeros_like(B)
+    res = P.cg_solve(C, B, X, tol=1e-10, check_every=8)
+    assert res["status"] == P.SPMV_OK and res["rel_residual"] <= 1.5e-10
+    Xh = X.cpu().numpy()
+    its = []
+    for j in range(k):
+        xj, itj, _ = oracle.cg(rowptr, col, val, np.ascontiguousarray(B_np[:, j]), tol=1e-10, maxit=1000)
+        its.append(itj)
+        assert np.max(np.abs(Xh[:, j] - xj)) < 1e-7
+        assert np.max(np.abs(Xh[:, j] - V[:, j])) < 1e-7
+    # the batch stops when its slowest column converges
+    assert abs(res["iterations"] - max(its)) <= 1
+
+
+def test_ir_fp32_with_longer_inner_solves():
+    g = (32, 32, 32)
+    _, C, b, _ = setup(g)
+    x = torch.zeros_like(b)
+    res = P.cg_solve(C, b, x, tol=1e-10, mode="ir_fp32", inner_max_iter=400, inner_tol=1e-6)
+    assert res["status"] == P.SPMV_OK and res["rel_residual"] <= 1e-10
+    assert np.max(np.abs(x.cpu().numpy() - 1.0)) < 1e-8

@@ -406,3 +406,35 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (v, t)
     if vscale < 1e-20:
         assert np.any((want != 0) & (np.abs(want) < 2.2250738585072014e-308))  # subnormal results occur
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 32])
+def test_fast_spmm_preconverted_block(k):
+    """FAST SpMM through the fixed-point copy of X, columns of very different
+    ranges (one all zero: exact path for that column only)."""
+    g = (21, 19, 17)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    X_np = spmv_inputs.uniform_matrix(n, k, seed=5)
+    for j in range(k):
+        X_np[:, j] *= 10.0 ** (j % 7 - 3)
+    if k > 1:
+        X_np[:, 1] = 0.0
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    X = torch.from_numpy(X_np).cuda()
+    Y = torch.full_like(X, float("nan"))
+    for _ in range(2):
+        P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    Yh = Y.cpu().numpy()
+    Y_ref = oracle.spmm(rowptr, col, val, X_np)
+    scale = oracle.spmm(rowptr, col, np.abs(val), np.abs(X_np))
+    d = np.abs(Yh - Y_ref)
+    assert np.all(d[scale == 0] == 0)
+    assert np.max(d[scale > 0] / scale[scale > 0]) <= TOL
+    # the narrower block after a wider one reuses the grown copy
+    X2 = X[:, :1].contiguous()
+    Y2 = torch.empty_like(X2)
+    P.spmm_apply(C, X2, Y2)
+    torch.cuda.synchronize()
+    check_fast(Y2.cpu().numpy()[:, 0], Y_ref[:, 0], scale[:, 0])
