@@ -235,16 +235,30 @@ def run_suite(args):
     xx = torch.zeros_like(b)
     P.spmv_autotune(C, ones, xx)
     res = {}
-    for mode in ("fp64", "ir_fp32"):
+    for mode, extra in (("fp64", {}), ("ir_fp32", {"inner_max_iter": 400, "inner_tol": 1e-6})):
         xx.zero_()
-        r = P.cg_solve(C, b, xx, tol=1e-10, mode=mode, max_iter=5000)
+        r = P.cg_solve(C, b, xx, tol=1e-10, mode=mode, max_iter=5000, **extra)
         err = float((xx - 1.0).abs().max())
         res[mode] = {"seconds": r["seconds"], "iterations": r["iterations"], "outer": r["outer_iterations"],
                      "rel_residual": r["rel_residual"], "max_abs_err_x_minus_1": err,
-                     "status": r["status"], "history_head": r["history"][:4], "history_tail": r["history"][-3:]}
+                     "status": r["status"], "history_head": r["history"][:4], "history_tail": r["history"][-3:],
+                     **extra}
+    # eight right-hand sides in one batched solve (b_j = A v_j, v_j ~ U[-1,1) seed 22)
+    kb = 8
+    V = torch.from_numpy(spmv_inputs.uniform_matrix(n, kb, seed=22)).to(dev)
+    Bm = torch.empty_like(V)
+    Ccol2 = P.spmv_compress(A, format="pattern", order="column")
+    P.spmm_apply(Ccol2, V, Bm)
+    del Ccol2
+    Xm = torch.zeros_like(Bm)
+    r = P.cg_solve(C, Bm, Xm, tol=1e-10, max_iter=5000)
+    res["fp64_batched_8rhs"] = {"seconds": r["seconds"], "seconds_per_rhs": r["seconds"] / kb,
+                                "iterations": r["iterations"], "rel_residual": r["rel_residual"],
+                                "max_abs_err_x_minus_v": float((Xm - V).abs().max()), "status": r["status"]}
     emit({"workload": "cg_192^3_b_eq_A1_tol1e-10", "rows": n, "spmv_order": "fast", **res,
-          "ir_speedup": res["fp64"]["seconds"] / res["ir_fp32"]["seconds"]})
-    del A, C, b, xx, ones
+          "ir_speedup": res["fp64"]["seconds"] / res["ir_fp32"]["seconds"],
+          "batched_speedup_per_rhs": res["fp64"]["seconds"] / res["fp64_batched_8rhs"]["seconds_per_rhs"]})
+    del A, C, b, xx, ones, V, Bm, Xm
 
     # --- SpMM on 160^3, k = 1, 4, 8, 16, 32 (X seed 3)
     A = P.spmv_build("hpcg", 160, 160, 160)
