@@ -24,6 +24,7 @@ namespace {
 thread_local std::string g_last_error;
 constexpr uint32_t kMagic = 0x5350564du;
 constexpr int kPartialWords = 152 * 64 + 64;
+constexpr int64_t kTileOverhang = 4096;  // rows a staged tile may reach past n
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -198,11 +199,14 @@ int ensure_device(spmv_mat_s* m) {
         if (p.fast_ok && stage_supported(v.nu)) {
             // fixed-point copy of x with zero guard zones as wide as the
             // largest displacement
+            // leading guard: the largest displacement plus the element of
+            // padding an odd window start adds; trailing guard: the same plus
+            // the overhang of the last shared-memory tile (at most 2048 rows)
             int64_t guard = 0;
             for (int32_t d : p.uoff) guard = std::max<int64_t>(guard, d < 0 ? -int64_t(d) : int64_t(d));
-            guard = (guard + 15) / 16 * 16;
+            guard = (guard + 2 + 15) / 16 * 16;
             int2* xf;
-            if ((st = dev_copy<int2>(m, nullptr, static_cast<size_t>(n + 2 * guard), &xf))) return st;
+            if ((st = dev_copy<int2>(m, nullptr, static_cast<size_t>(n + 2 * guard + kTileOverhang), &xf))) return st;
             m->d_xfixed = xf;
             m->xfixed_guard = guard;
             m->fast_variant = tuned_variant(m, 2);
@@ -212,7 +216,7 @@ int ensure_device(spmv_mat_s* m) {
             for (int rpt : {prefer, 4, 2, 1})
                 if (make_stage_plan(p.uoff, rpt, 512, 12288, &m->stage)) { m->stage_ok = true; break; }
         }
-        if (m->fast_variant == 1 && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
+        if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
         if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
     } else {
         const DeltaFormat& d = m->dlt;
@@ -458,6 +462,8 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
     if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
     else if (A->fmt == SPMV_FMT_PATTERN)
         e = A->order != SPMV_ORDER_FAST ? launch_pattern_col_f64(A->pat_view, x, y, s)
+            : A->fast_variant == 3 ? launch_pattern_fast_xstaged(A->pat_view, A->stage, x, y, A->d_scratch_words,
+                                                                 A->d_xfixed, A->xfixed_guard, s)
             : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                            A->xfixed_guard, s)
             : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
@@ -554,7 +560,10 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     if (A->stage_ok)
         for (int rpt : {1, 2, 4}) {
             StagePlan plan;
-            if (make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) cands.push_back(Cand{1, plan});
+            if (make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) {
+                cands.push_back(Cand{1, plan});
+                if (A->d_xfixed && A->pat_view.run_len == 3 && A->pat_view.nu == 27) cands.push_back(Cand{3, plan});
+            }
         }
     if (cands.size() <= 1) return SPMV_OK;
     cudaEvent_t e0, e1;
@@ -566,6 +575,8 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         auto launch = [&]() {
             return c.variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                           A->xfixed_guard, nullptr)
+                 : c.variant == 3 ? launch_pattern_fast_xstaged(A->pat_view, c.plan, x, y, A->d_scratch_words,
+                                                                A->d_xfixed, A->xfixed_guard, nullptr)
                                   : launch_pattern_fast_staged(A->pat_view, c.plan, x, y, nullptr);
         };
         cudaError_t e = launch();
@@ -581,13 +592,13 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     A->fast_variant = pick.variant;
-    if (pick.variant == 1) A->stage = pick.plan;
+    if (pick.variant == 1 || pick.variant == 3) A->stage = pick.plan;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_variant[tune_key(A)] = pick.variant;
-        if (pick.variant == 1) g_tune[tune_key(A)] = pick.plan.rows_per_thread;
+        if (pick.variant == 1 || pick.variant == 3) g_tune[tune_key(A)] = pick.plan.rows_per_thread;
     }
-    if (choice) *choice = pick.variant == 1 ? pick.plan.rows : 1;
+    if (choice) *choice = (pick.variant == 1 || pick.variant == 3) ? pick.plan.rows : 1;
     return SPMV_OK;
 }
 
@@ -602,14 +613,16 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows) {
         A->fast_variant = 2;
         return SPMV_OK;
     }
-    if (variant != 1) return fail(SPMV_EINVAL, "variant must be 0, 1 or 2");
+    if (variant != 1 && variant != 3) return fail(SPMV_EINVAL, "variant must be 0, 1, 2 or 3");
+    if (variant == 3 && !(A->d_xfixed && A->pat_view.run_len == 3 && A->pat_view.nu == 27))
+        return fail(SPMV_EUNSUPPORTED, "no staged pre-converted kernel for this union");
     if (!stage_supported(static_cast<int>(A->pat.uoff.size()))) return fail(SPMV_EUNSUPPORTED, "no staged kernel for this union size");
     StagePlan plan;
     if (tile_rows % 512 != 0 || !make_stage_plan(A->pat.uoff, tile_rows / 512, 512, 12288, &plan))
         return fail(SPMV_EUNSUPPORTED, "tile does not fit shared memory (tile_rows 512, 1024 or 2048)");
     A->stage = plan;
     A->stage_ok = true;
-    A->fast_variant = 1;
+    A->fast_variant = variant;
     return SPMV_OK;
 }
 

@@ -480,6 +480,76 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
 
 
 
+
+// ------------------- FAST order, staged tiles of the pre-converted copy ---
+// As the staged kernel, but the tile's windows are copied from the
+// fixed-point copy X (guard zones make every window index valid), so the
+// CTA neither reduces an exponent nor converts: phase 1 is a plain 16-byte
+// copy into shared memory, phase 2 the rows.
+template <int WORDS, int NU, int RPT, int RUN>
+__global__ void __launch_bounds__(kStageThreads) pattern_fast_xstaged_kernel(PatternView a, StagePlan sp,
+                                                                             const double* __restrict__ x,
+                                                                             const int2* __restrict__ X,
+                                                                             double* __restrict__ y,
+                                                                             const uint32_t* __restrict__ partial) {
+    extern __shared__ int4 sx4[];
+    const int2* sx = reinterpret_cast<const int2*>(sx4);
+    const int tid = threadIdx.x;
+    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
+    const int emax = int(__ldg(partial + kXmaxBlocks));
+    const bool exact_path = emax < 64 || emax >= 2047;
+    if (!exact_path) {
+#pragma unroll
+        for (int sg = 0; sg < kMaxSegments; ++sg) {
+            if (sg >= sp.nseg) break;
+            // segment windows start at an even element (the plan keeps seg_base even
+            // and rounds the global start down), so both sides are 16-byte aligned
+            const int64_t g0 = r0 + sp.seg_min[sg] - sp.seg_pad[sg];
+            const int len2 = (sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2;
+            const int4* src = reinterpret_cast<const int4*>(X + g0);
+            int4* dst = sx4 + sp.seg_pbase[sg] / 2;
+            for (int e = tid; e < len2; e += kStageThreads) dst[e] = __ldg(src + e);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int rl = tid + i * kStageThreads;
+        const int64_t r = r0 + rl;
+        if (r >= a.n) break;
+        uint32_t w[kMaxRecordWords];
+        load_record<WORDS>(a, r, w);
+        if (exact_path) {
+            const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
+            double acc = 0.0;
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+                if ((mask >> u) & 1u)
+                    acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __ldg(x + r + a.uoff[u]), acc);
+            y[r] = acc;
+            continue;
+        }
+        uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+        for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+        int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < NU / RUN; ++k) {
+            const int2* p = sx + rl + sp.soff_padded[k * RUN];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                const int u = k * RUN + j;
+                const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+                const int2 v = p[j];
+                ah[u % 3] += int64_t(m) * v.y;
+                al[u % 3] += int64_t(m) * v.x;
+            }
+        }
+        const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
+        y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+    }
+}
+
 // ------------------------------ SpMM, FAST order, pre-converted block X ---
 // Per-column largest exponents (one word per column, from the partial
 // maxima of xmax_cols_kernel), then X converted once into a fixed-point
@@ -911,6 +981,31 @@ cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double*
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                        uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (!(a.run_len == 3 && a.nu == 27)) return cudaErrorNotSupported;
+    int2* X = X_guarded + guard;
+    xmax_kernel<<<kXmaxBlocks, 1024, 0, s>>>(x, a.n, partial);
+    convert_x_kernel<<<kXmaxBlocks * 8, 256, 0, s>>>(reinterpret_cast<const uint2*>(x), a.n, partial, X);
+    const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
+    const size_t smem = size_t(sp.elems_padded) * sizeof(int2);
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     int(cudaSharedmemCarveoutMaxShared));
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, kStageThreads, smem, s>>>(a, sp, x, X, y, partial);
+        return cudaGetLastError();
+    };
+    if (sp.rows_per_thread == 1) return go(pattern_fast_xstaged_kernel<7, 27, 1, 3>);
+    if (sp.rows_per_thread == 2) return go(pattern_fast_xstaged_kernel<7, 27, 2, 3>);
+    if (sp.rows_per_thread == 4) return go(pattern_fast_xstaged_kernel<7, 27, 4, 3>);
+    return cudaErrorInvalidValue;
+}
+
 bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }
 
 bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
@@ -939,6 +1034,21 @@ bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int 
     for (int u = 0, sg = 0; u < nu; ++u) {
         while (sg + 1 < p.nseg && uoff[u] >= p.seg_min[sg + 1]) ++sg;
         p.soff[u] = p.seg_base[sg] + (uoff[u] - p.seg_min[sg]);
+    }
+    // 16-byte staging of an int2 copy: each segment window starts at an even
+    // global element (one element of padding in front when seg_min is odd;
+    // tile starts are multiples of 512 and so even) and at an even position
+    // in shared memory
+    int64_t pbase = 0;
+    for (int sg = 0; sg < p.nseg; ++sg) {
+        p.seg_pad[sg] = (p.seg_min[sg] % 2 != 0) ? 1 : 0;
+        p.seg_pbase[sg] = int32_t(pbase);
+        pbase += (int64_t(p.rows) + p.seg_span[sg] + p.seg_pad[sg] + 1) / 2 * 2;
+    }
+    p.elems_padded = int32_t(pbase);
+    for (int u = 0, sg = 0; u < nu; ++u) {
+        while (sg + 1 < p.nseg && uoff[u] >= p.seg_min[sg + 1]) ++sg;
+        p.soff_padded[u] = p.seg_pbase[sg] + p.seg_pad[sg] + (uoff[u] - p.seg_min[sg]);
     }
     *out = p;
     return true;

@@ -142,6 +142,11 @@ struct StagePlan {
     int32_t seg_span[kMaxSegments];
     int32_t seg_base[kMaxSegments];
     int32_t soff[32];
+    // layout for 16-byte copies of an int2 array (seg_min - seg_pad even)
+    int32_t seg_pad[kMaxSegments];
+    int32_t seg_pbase[kMaxSegments];
+    int32_t soff_padded[32];
+    int32_t elems_padded;
 };
 bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
                      StagePlan* out);
@@ -156,6 +161,8 @@ cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, doubl
                                     uint32_t* xmax_word, cudaStream_t s);
 cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                        cudaStream_t s);
+cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                        uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
