@@ -22,6 +22,9 @@ def main():
     ap.add_argument("--kind", default="hpcg", choices=("hpcg", "irregular"))
     ap.add_argument("--variant", type=int, default=-1, help="FAST kernel: 0 direct, 1 staged, 2 pre-converted")
     ap.add_argument("--tile", type=int, default=2048)
+    ap.add_argument("--cg", choices=("fp64", "ir_fp32"), default=None,
+                    help="run one CG solve (b = A 1) instead of SpMV steps")
+    ap.add_argument("--cg-iters", type=int, default=40)
     args = ap.parse_args()
     g = args.grid
     A = P.spmv_build(args.kind, g, g, g, seed=2)
@@ -31,6 +34,15 @@ def main():
     y = torch.empty_like(x)
     if args.variant >= 0:
         P.spmv_set_variant(M, args.variant, args.tile)
+    if args.cg:
+        ones = torch.ones_like(x)
+        P.spmv_apply(M, ones, y)
+        xs = torch.zeros_like(x)
+        r = P.cg_solve(M, y.clone(), xs, tol=1e-30, max_iter=args.cg_iters, mode=args.cg,
+                       inner_max_iter=args.cg_iters, inner_tol=1e-30)
+        print(f"cg {args.cg}: {r['iterations']} steps in {r['seconds'] * 1e3:.2f} ms "
+              f"({r['seconds'] / max(1, r['iterations']) * 1e6:.1f} us/step)")
+        return
     for _ in range(args.warmup):
         P.spmv_apply(M, x, y)
     torch.cuda.synchronize()
