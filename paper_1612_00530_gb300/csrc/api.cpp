@@ -2,6 +2,7 @@
 // Handles own host copies of their stored form and, after the first device
 // call, device copies.  All errors come back as status codes with a
 // thread-local message; nothing throws across the boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -184,6 +185,30 @@ int ensure_device(spmv_mat_s* m) {
         std::memcpy(&v.mult_hi, tbl + 4, 4);
         v.mult_exp = p.mult_exp;
         v.err = m->d_err;
+        // the dominant record (most frequent; its slots must all be present)
+        v.dom_ok = 0;
+        if (n > 0) {
+            std::map<std::vector<uint32_t>, int64_t> freq;
+            std::vector<uint32_t> key(p.words);
+            const int64_t step = std::max<int64_t>(1, n / 65536);   // a sample is enough to find it
+            for (int64_t r = 0; r < n; r += step) {
+                std::copy(&p.rec[r * p.words], &p.rec[r * p.words] + p.words, key.begin());
+                freq[key]++;
+            }
+            const auto best = std::max_element(freq.begin(), freq.end(),
+                                               [](const auto& a2, const auto& b2) { return a2.second < b2.second; });
+            const uint8_t* bytes = reinterpret_cast<const uint8_t*>(best->first.data());
+            bool all_present = true;
+            for (int u = 0; u < v.nu; ++u) all_present = all_present && bytes[u] < p.dict.size();
+            if (all_present) {
+                v.dom_ok = 1;
+                for (int k2 = 0; k2 < p.words; ++k2) v.dom_w[k2] = best->first[k2];
+                for (int u = 0; u < v.nu; ++u) {
+                    v.dom_m[u] = p.fast_ok ? p.mult[bytes[u]] : 0;
+                    v.dom_v32[u] = static_cast<float>(p.dict[bytes[u]]);
+                }
+            }
+        }
         // runs of consecutive displacements, all of one length
         v.run_len = 0;
         for (int len : {3}) {

@@ -22,7 +22,7 @@ bool api_valid(spmv_mat_t m);
 
 namespace {
 
-constexpr int kRedBlocks = 304;
+constexpr int kRedBlocks = 1216;   // 8 blocks per SM; partial sums reduced by one warp
 constexpr int kRedThreads = 256;
 
 struct CgState {
@@ -61,10 +61,23 @@ __global__ void __launch_bounds__(kRedThreads) dot_kernel(const double* __restri
                                                           const CgState* __restrict__ st) {
     if (st && st->done) return;
     __shared__ double sm[32];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        s = fma(a[i], b[i], s);
-    s = block_sum(s, sm);
+    double s = 0.0, s2 = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t n2 = n / 2;
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const double2* b2 = reinterpret_cast<const double2*>(b);
+    const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
+    if (vec) {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2; i += stride) {
+            const double2 u = a2[i], v = b2[i];
+            s = fma(u.x, v.x, s);
+            s2 = fma(u.y, v.y, s2);
+        }
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s = fma(a[n - 1], b[n - 1], s);
+    } else {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) s = fma(a[i], b[i], s);
+    }
+    s = block_sum(s + s2, sm);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -84,14 +97,44 @@ __global__ void __launch_bounds__(kRedThreads) update_xr_kernel(double* __restri
     }
     __syncthreads();
     const double alpha = s_alpha;
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        s = fma(ri, ri, s);
+    double s = 0.0, s2 = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
+                       reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15u) == 0;
+    if (vec) {
+        const int64_t n2 = n / 2;
+        double2* x2 = reinterpret_cast<double2*>(x);
+        double2* r2 = reinterpret_cast<double2*>(r);
+        const double2* p2 = reinterpret_cast<const double2*>(p);
+        const double2* q2 = reinterpret_cast<const double2*>(q);
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2; i += stride) {
+            double2 xv = x2[i], rv = r2[i];
+            const double2 pv = p2[i], qv = q2[i];
+            xv.x = fma(alpha, pv.x, xv.x);
+            xv.y = fma(alpha, pv.y, xv.y);
+            rv.x = fma(-alpha, qv.x, rv.x);
+            rv.y = fma(-alpha, qv.y, rv.y);
+            x2[i] = xv;
+            r2[i] = rv;
+            s = fma(rv.x, rv.x, s);
+            s2 = fma(rv.y, rv.y, s2);
+        }
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            const int64_t i = n - 1;
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            s = fma(ri, ri, s);
+        }
+    } else {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            s = fma(ri, ri, s);
+        }
     }
-    s = block_sum(s, sm);
+    s = block_sum(s + s2, sm);
     if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
 }
 
@@ -107,8 +150,23 @@ __global__ void __launch_bounds__(kRedThreads) update_p_kernel(double* __restric
     }
     __syncthreads();
     const double beta = s_beta;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        p[i] = fma(beta, p[i], r[i]);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(r)) & 15u) == 0) {
+        const int64_t n2 = n / 2;
+        double2* p2 = reinterpret_cast<double2*>(p);
+        const double2* r2 = reinterpret_cast<const double2*>(r);
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2; i += stride) {
+            double2 pv = p2[i];
+            const double2 rv = r2[i];
+            pv.x = fma(beta, pv.x, rv.x);
+            pv.y = fma(beta, pv.y, rv.y);
+            p2[i] = pv;
+        }
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = fma(beta, p[n - 1], r[n - 1]);
+    } else {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride)
+            p[i] = fma(beta, p[i], r[i]);
+    }
 }
 
 // rr = rr_new, history, convergence flag (one warp)
@@ -153,10 +211,20 @@ __global__ void __launch_bounds__(kRedThreads) dot32_kernel(const float* __restr
     if (st->done) return;
     __shared__ double sm[32];
     double s = 0.0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
-    for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; i0 < n; i0 += stride) {
+    // chunks of 8 products (two 16-byte loads per operand) summed in binary32
+    const int64_t n8 = n / 8, stride = int64_t(gridDim.x) * blockDim.x;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    for (int64_t c8 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c8 < n8; c8 += stride) {
+        const float4 u0 = a4[2 * c8], u1 = a4[2 * c8 + 1], v0 = b4[2 * c8], v1 = b4[2 * c8 + 1];
+        float c = u0.x * v0.x;
+        c = fmaf(u0.y, v0.y, c); c = fmaf(u0.z, v0.z, c); c = fmaf(u0.w, v0.w, c);
+        c = fmaf(u1.x, v1.x, c); c = fmaf(u1.y, v1.y, c); c = fmaf(u1.z, v1.z, c); c = fmaf(u1.w, v1.w, c);
+        s += double(c);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         float c = 0.0f;
-        for (int k = 0; k < 8 && i0 + k < n; ++k) c = fmaf(a[i0 + k], b[i0 + k], c);
+        for (int64_t i = n8 * 8; i < n; ++i) c = fmaf(a[i], b[i], c);
         s += double(c);
     }
     s = block_sum(s, sm);
@@ -178,11 +246,28 @@ __global__ void __launch_bounds__(kRedThreads) update_dr32_kernel(float* __restr
     __syncthreads();
     const float alpha = s_alpha;
     double s = 0.0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
-    for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; i0 < n; i0 += stride) {
+    // four elements per 16-byte access; chunk sums of r.r in binary32
+    const int64_t n4 = n / 4, stride = int64_t(gridDim.x) * blockDim.x;
+    float4* d4 = reinterpret_cast<float4*>(d);
+    float4* r4 = reinterpret_cast<float4*>(r);
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const float4* q4 = reinterpret_cast<const float4*>(q);
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += stride) {
+        float4 dv = d4[i], rv = r4[i];
+        const float4 pv = p4[i], qv = q4[i];
+        dv.x = fmaf(alpha, pv.x, dv.x); dv.y = fmaf(alpha, pv.y, dv.y);
+        dv.z = fmaf(alpha, pv.z, dv.z); dv.w = fmaf(alpha, pv.w, dv.w);
+        rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
+        rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
+        d4[i] = dv;
+        r4[i] = rv;
+        float c = rv.x * rv.x;
+        c = fmaf(rv.y, rv.y, c); c = fmaf(rv.z, rv.z, c); c = fmaf(rv.w, rv.w, c);
+        s += double(c);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         float c = 0.0f;
-        for (int k = 0; k < 8 && i0 + k < n; ++k) {
-            const int64_t i = i0 + k;
+        for (int64_t i = n4 * 4; i < n; ++i) {
             d[i] = fmaf(alpha, p[i], d[i]);
             const float ri = fmaf(-alpha, q[i], r[i]);
             r[i] = ri;
@@ -205,8 +290,20 @@ __global__ void __launch_bounds__(kRedThreads) update_p32_kernel(float* __restri
     }
     __syncthreads();
     const float beta = s_beta;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    const int64_t n4 = n / 4, stride = int64_t(gridDim.x) * blockDim.x;
+    float4* p4 = reinterpret_cast<float4*>(p);
+    const float4* r4 = reinterpret_cast<const float4*>(r);
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += stride) {
+        float4 pv = p4[i];
+        const float4 rv = r4[i];
+        pv.x = fmaf(beta, pv.x, rv.x); pv.y = fmaf(beta, pv.y, rv.y);
+        pv.z = fmaf(beta, pv.z, rv.z); pv.w = fmaf(beta, pv.w, rv.w);
+        p4[i] = pv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 4 && n4 * 4 + threadIdx.x < n) {
+        const int64_t i = n4 * 4 + threadIdx.x;
         p[i] = fmaf(beta, p[i], r[i]);
+    }
 }
 
 __global__ void finalize32_kernel(const double* __restrict__ partial_rr, CgState* __restrict__ st) {
@@ -294,19 +391,22 @@ __global__ void __launch_bounds__(kRedThreads) dot_cols_kernel(const double* __r
     }
 }
 
-__device__ __forceinline__ double sum_col(const double* __restrict__ partial, int k, int j) {
+// column j's partials summed by one warp in a fixed order (valid in every lane)
+__device__ __forceinline__ double sum_col_warp(const double* __restrict__ partial, int k, int j) {
     double s = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) s += partial[b * k + j];
+    for (int b = threadIdx.x & 31; b < kRedBlocks; b += 32) s += partial[b * k + j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     return s;
 }
 
 // alpha_j = rr_j / (p_j . q_j)
+// one warp per column
 __global__ void alpha_cols_kernel(const double* __restrict__ partial_pq, ColState* __restrict__ st) {
     if (st->done) return;
-    const int j = threadIdx.x;
+    const int j = threadIdx.x >> 5;
     if (j >= st->k) return;
-    const double pq = sum_col(partial_pq, st->k, j);
-    st->alpha[j] = (st->rr[j] > 0.0 && pq != 0.0) ? st->rr[j] / pq : 0.0;
+    const double pq = sum_col_warp(partial_pq, st->k, j);
+    if ((threadIdx.x & 31) == 0) st->alpha[j] = (st->rr[j] > 0.0 && pq != 0.0) ? st->rr[j] / pq : 0.0;
 }
 
 // x += alpha p; r -= alpha q; partial sums of r.r per column
@@ -342,15 +442,17 @@ __global__ void beta_cols_kernel(const double* __restrict__ partial_rr, ColState
                                  double* __restrict__ hist) {
     if (st->done) return;
     __shared__ double rel[kMaxCols];
-    const int j = threadIdx.x, k = st->k;
+    const int j = threadIdx.x >> 5, k = st->k;
     if (j < k) {
-        const double rr_new = sum_col(partial_rr, k, j);
-        st->beta[j] = st->rr[j] > 0.0 ? rr_new / st->rr[j] : 0.0;
-        st->rr[j] = rr_new;
-        rel[j] = sqrt(rr_new) / st->bnorm[j];
+        const double rr_new = sum_col_warp(partial_rr, k, j);
+        if ((threadIdx.x & 31) == 0) {
+            st->beta[j] = st->rr[j] > 0.0 ? rr_new / st->rr[j] : 0.0;
+            st->rr[j] = rr_new;
+            rel[j] = sqrt(rr_new) / st->bnorm[j];
+        }
     }
     __syncthreads();
-    if (j == 0) {
+    if (threadIdx.x == 0) {
         double m = 0.0;
         for (int c = 0; c < k; ++c) m = fmax(m, rel[c]);
         st->it += 1;
@@ -393,8 +495,10 @@ __global__ void __launch_bounds__(kRedThreads) residual_cols_kernel(const double
 }
 
 __global__ void col_sums_kernel(const double* __restrict__ partial, int k, double* __restrict__ out) {
-    const int j = threadIdx.x;
-    if (j < k) out[j] = sum_col(partial, k, j);
+    const int j = threadIdx.x >> 5;
+    if (j >= k) return;
+    const double s = sum_col_warp(partial, k, j);
+    if ((threadIdx.x & 31) == 0) out[j] = s;
 }
 
 struct Workspace {
@@ -481,7 +585,7 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
     std::vector<double> h(k);
     auto col_norms2 = [&](const double* a) -> int {
         dot_cols_kernel<<<G, T, 0, s>>>(a, a, n, k, part_a, nullptr);
-        col_sums_kernel<<<1, 64, 0, s>>>(part_a, k, d_sums);
+        col_sums_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, k, d_sums);
         CG_CUDA(cudaMemcpyAsync(h.data(), d_sums, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
         CG_CUDA(cudaStreamSynchronize(s));
         return SPMV_OK;
@@ -489,7 +593,7 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
     auto residual = [&]() -> int {
         CG_ST(spmm_apply(A, k, x, k, q, k, s));
         residual_cols_kernel<<<G, T, 0, s>>>(b, q, r, n, k, part_a);
-        col_sums_kernel<<<1, 64, 0, s>>>(part_a, k, d_sums);
+        col_sums_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, k, d_sums);
         CG_CUDA(cudaMemcpyAsync(h.data(), d_sums, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
         CG_CUDA(cudaStreamSynchronize(s));
         return SPMV_OK;
@@ -513,9 +617,9 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
     auto body = [&]() -> int {
         CG_ST(spmm_apply(A, k, p, k, q, k, s));
         dot_cols_kernel<<<G, T, 0, s>>>(p, q, n, k, part_a, d_st);
-        alpha_cols_kernel<<<1, 64, 0, s>>>(part_a, d_st);
+        alpha_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, d_st);
         update_xr_cols_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_b, d_st);
-        beta_cols_kernel<<<1, 64, 0, s>>>(part_b, d_st, d_hist);
+        beta_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_b, d_st, d_hist);
         update_p_cols_kernel<<<G, T, 0, s>>>(p, r, n, d_st);
         CG_CUDA(cudaGetLastError());
         return SPMV_OK;

@@ -64,6 +64,16 @@ __device__ __forceinline__ void load_record(const PatternView& a, int64_t r, uin
     if (rem & 1) w[WORDS - 1] = __ldcs(a.p4 + r);
 }
 
+
+// true when the row's record equals the matrix's dominant record
+template <int WORDS>
+__device__ __forceinline__ bool is_dominant(const PatternView& a, const uint32_t (&w)[kMaxRecordWords]) {
+    bool eq = a.dom_ok != 0;
+#pragma unroll
+    for (int k = 0; k < WORDS; ++k) eq = eq && (w[k] == a.dom_w[k]);
+    return eq;
+}
+
 // ------------------------------------------------------------- ELL -------
 template <typename T>
 __global__ void __launch_bounds__(kBlock) ell_kernel(EllView a, const T* __restrict__ x, T* __restrict__ y) {
@@ -345,24 +355,40 @@ __global__ void __launch_bounds__(kBlock, 6) pattern_fast_x_kernel(PatternView a
         y[r] = acc;
         return;
     }
-    uint32_t mw[(NU + 3) / 4];
-#pragma unroll
-    for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
     // one pointer per run of RUN consecutive displacements, the run's other
     // slots at immediate offsets; three accumulator pairs shorten the
     // dependency chains
     const int2* __restrict__ Xr = X + r;
     int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+    if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+        // the warp's rows all carry the dominant record: multipliers are
+        // kernel parameters
 #pragma unroll
-    for (int k = 0; k < NU / RUN; ++k) {
-        const int2* __restrict__ p = Xr + a.uoff[k * RUN];
+        for (int k = 0; k < NU / RUN; ++k) {
+            const int2* __restrict__ p = Xr + a.uoff[k * RUN];
 #pragma unroll
-        for (int j = 0; j < RUN; ++j) {
-            const int u = k * RUN + j;
-            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-            const int2 v = __ldg(p + j);
-            ah[u % 3] += int64_t(m) * v.y;
-            al[u % 3] += int64_t(m) * v.x;
+            for (int j = 0; j < RUN; ++j) {
+                const int u = k * RUN + j;
+                const int2 v = __ldg(p + j);
+                ah[u % 3] += int64_t(a.dom_m[u]) * v.y;
+                al[u % 3] += int64_t(a.dom_m[u]) * v.x;
+            }
+        }
+    } else {
+        uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+        for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+#pragma unroll
+        for (int k = 0; k < NU / RUN; ++k) {
+            const int2* __restrict__ p = Xr + a.uoff[k * RUN];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) {
+                const int u = k * RUN + j;
+                const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+                const int2 v = __ldg(p + j);
+                ah[u % 3] += int64_t(m) * v.y;
+                al[u % 3] += int64_t(m) * v.x;
+            }
         }
     }
     const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
@@ -392,7 +418,7 @@ __device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t e
 }
 
 template <int WORDS, int NU, int RPT, int RUN>
-__global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
+__global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
                                                                             const double* __restrict__ x,
                                                                             double* __restrict__ y) {
     extern __shared__ int2 sx[];
@@ -457,20 +483,34 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
         }
         // int8 multipliers of four codes at a time: nibble-pack the codes,
         // then one table permute
-        uint32_t mw[(NU + 3) / 4];
-#pragma unroll
-        for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+        if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
 #pragma unroll
-        for (int k = 0; k < NU / RUN; ++k) {
-            const int2* p = sx + rl + sp.soff[k * RUN];
+            for (int k = 0; k < NU / RUN; ++k) {
+                const int2* p = sx + rl + sp.soff[k * RUN];
 #pragma unroll
-            for (int j = 0; j < RUN; ++j) {
-                const int u = k * RUN + j;
-                const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-                const int2 X = p[j];
-                ah[u % 3] += int64_t(m) * X.y;
-                al[u % 3] += int64_t(m) * X.x;
+                for (int j = 0; j < RUN; ++j) {
+                    const int u = k * RUN + j;
+                    const int2 v = p[j];
+                    ah[u % 3] += int64_t(a.dom_m[u]) * v.y;
+                    al[u % 3] += int64_t(a.dom_m[u]) * v.x;
+                }
+            }
+        } else {
+            uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+            for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+#pragma unroll
+            for (int k = 0; k < NU / RUN; ++k) {
+                const int2* p = sx + rl + sp.soff[k * RUN];
+#pragma unroll
+                for (int j = 0; j < RUN; ++j) {
+                    const int u = k * RUN + j;
+                    const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+                    const int2 v = p[j];
+                    ah[u % 3] += int64_t(m) * v.y;
+                    al[u % 3] += int64_t(m) * v.x;
+                }
             }
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
@@ -487,7 +527,7 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_staged_kernel(Patt
 // CTA neither reduces an exponent nor converts: phase 1 is a plain 16-byte
 // copy into shared memory, phase 2 the rows.
 template <int WORDS, int NU, int RPT, int RUN>
-__global__ void __launch_bounds__(kStageThreads) pattern_fast_xstaged_kernel(PatternView a, StagePlan sp,
+__global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_xstaged_kernel(PatternView a, StagePlan sp,
                                                                              const double* __restrict__ x,
                                                                              const int2* __restrict__ X,
                                                                              double* __restrict__ y,
@@ -529,20 +569,34 @@ __global__ void __launch_bounds__(kStageThreads) pattern_fast_xstaged_kernel(Pat
             y[r] = acc;
             continue;
         }
-        uint32_t mw[(NU + 3) / 4];
-#pragma unroll
-        for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+        if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
 #pragma unroll
-        for (int k = 0; k < NU / RUN; ++k) {
-            const int2* p = sx + rl + sp.soff_padded[k * RUN];
+            for (int k = 0; k < NU / RUN; ++k) {
+                const int2* p = sx + rl + sp.soff_padded[k * RUN];
 #pragma unroll
-            for (int j = 0; j < RUN; ++j) {
-                const int u = k * RUN + j;
-                const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
-                const int2 v = p[j];
-                ah[u % 3] += int64_t(m) * v.y;
-                al[u % 3] += int64_t(m) * v.x;
+                for (int j = 0; j < RUN; ++j) {
+                    const int u = k * RUN + j;
+                    const int2 v = p[j];
+                    ah[u % 3] += int64_t(a.dom_m[u]) * v.y;
+                    al[u % 3] += int64_t(a.dom_m[u]) * v.x;
+                }
+            }
+        } else {
+            uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+            for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+#pragma unroll
+            for (int k = 0; k < NU / RUN; ++k) {
+                const int2* p = sx + rl + sp.soff_padded[k * RUN];
+#pragma unroll
+                for (int j = 0; j < RUN; ++j) {
+                    const int u = k * RUN + j;
+                    const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+                    const int2 v = p[j];
+                    ah[u % 3] += int64_t(m) * v.y;
+                    al[u % 3] += int64_t(m) * v.x;
+                }
             }
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
@@ -636,11 +690,23 @@ __global__ void __launch_bounds__(kBlock) pattern_f32_kernel(PatternView a, cons
     if (r >= a.n) return;
     uint32_t w[kMaxRecordWords];
     load_record<WORDS>(a, r, w);
+    const float* __restrict__ xr = x + r;
+    float acc = 0.0f;
+    if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+        // every row of the warp carries the dominant record: all slots
+        // present, values are kernel parameters
+#pragma unroll
+        for (int k = 0; k < NU / RUN; ++k) {
+            const float* __restrict__ p = xr + a.uoff[k * RUN];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) acc = fmaf(a.dom_v32[k * RUN + j], __ldg(p + j), acc);
+        }
+        y[r] = acc;
+        return;
+    }
     const uint32_t pat = byte_of(w, NU);
     if (pat >= uint32_t(a.npat)) raise_error(a.err, 1);
     const uint32_t mask = smask[pat & 31];
-    const float* __restrict__ xr = x + r;
-    float acc = 0.0f;
 #pragma unroll
     for (int k = 0; k < NU / RUN; ++k) {
         const float* __restrict__ p = xr + a.uoff[k * RUN];

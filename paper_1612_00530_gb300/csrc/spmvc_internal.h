@@ -113,6 +113,12 @@ struct PatternView {
     int32_t mult_exp;
     int32_t run_len;                // the union is nu/run_len runs of run_len consecutive
                                     // displacements (0 when it is not so split)
+    // the most frequent row record, when it has no absent slot: a warp whose
+    // rows all carry it takes multipliers / values from these parameters
+    int32_t dom_ok;
+    uint32_t dom_w[kMaxRecordWords];
+    int32_t dom_m[32];              // FAST order: int8 multipliers of its slots
+    float dom_v32[32];              // binary32: its slot values
     int32_t* err;                   // sticky device error word
 };
 
