@@ -12,6 +12,7 @@
 //    53-bit fixed point by integer bit manipulation, every row is summed
 //    exactly with 32x32->64-bit integer multiply-adds, and one rounding to
 //    nearest makes the double result -- no FP64 instruction per nonzero.
+#include <algorithm>
 #include <cstdint>
 
 #include "spmvc_internal.h"
@@ -604,6 +605,179 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_xstaged_kernel(
     }
 }
 
+
+// ------------------------------- FAST order, persistent, double-buffered --
+// One CTA of 1024 threads per SM walks tiles of 1024 rows.  While it
+// converts and sums tile t from shared memory, the cp.async copies of tile
+// t+1 -- the x windows of its merged segments (8-byte copies, zero-filled
+// outside [0, n)) and its row records (16/8/4-byte planes, zero-filled past
+// n) -- are already in flight into the other buffer.  cp.async groups and
+// block barriers order everything; the kernel has no spin-wait of its own.
+constexpr int kAsyncThreads = 1024;
+constexpr int kAsyncRows = 1024;
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool valid) {
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool valid) {
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+struct AsyncBuf {
+    int2* xw;        // staged x windows, elems entries
+    uint4* r16;      // record words 0..3
+    uint2* r8;       // words 4..5
+    uint32_t* r4;    // word 6
+};
+
+// Issues the copies of tile `tile` into `b` (WORDS == 7 record layout).
+__device__ __forceinline__ void async_issue(const PatternView& a, const StagePlan& sp, const double* __restrict__ x,
+                                            int64_t tile, const AsyncBuf& b) {
+    const int tid = threadIdx.x;
+    const int64_t r0 = tile * kAsyncRows;
+#pragma unroll
+    for (int sg = 0; sg < kMaxSegments; ++sg) {
+        if (sg >= sp.nseg) break;
+        const int64_t g0 = r0 + sp.seg_min[sg];
+        const int len = kAsyncRows + sp.seg_span[sg];
+        int2* dst = b.xw + sp.seg_base[sg];
+        for (int e = tid; e < len; e += kAsyncThreads) {
+            const int64_t idx = g0 + e;
+            const bool ok = uint64_t(idx) < uint64_t(a.n);
+            cp_async8(dst + e, x + (ok ? idx : 0), ok);
+        }
+    }
+    const int64_t r = r0 + tid;
+    const bool ok = r < a.n;
+    const int64_t rs = ok ? r : 0;
+    cp_async16(b.r16 + tid, a.p16a + rs, ok);
+    cp_async8(b.r8 + tid, a.p8 + rs, ok);
+    cp_async4(b.r4 + tid, a.p4 + rs, ok);
+    cp_async_commit();
+}
+
+template <int NU, int RUN>
+__global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(PatternView a, StagePlan sp,
+                                                                              const double* __restrict__ x,
+                                                                              double* __restrict__ y,
+                                                                              int64_t ntiles) {
+    constexpr int WORDS = 7;
+    extern __shared__ int4 smem4[];
+    __shared__ uint32_t s_red[kAsyncThreads / 32];
+    __shared__ double sdict[8];
+    __shared__ uint32_t smask[32];
+    const int tid = threadIdx.x;
+    if (tid < 8) sdict[tid] = tid < a.dict_size ? a.dict[tid] : 0.0;
+    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
+    // two buffers: [x windows | r16 | r8 | r4]
+    const size_t xbytes = (size_t(sp.elems) * 8 + 15) / 16 * 16;
+    const size_t bbytes = xbytes + size_t(kAsyncRows) * 28;
+    AsyncBuf buf[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        char* base = reinterpret_cast<char*>(smem4) + q * bbytes;
+        buf[q].xw = reinterpret_cast<int2*>(base);
+        buf[q].r16 = reinterpret_cast<uint4*>(base + xbytes);
+        buf[q].r8 = reinterpret_cast<uint2*>(base + xbytes + kAsyncRows * 16);
+        buf[q].r4 = reinterpret_cast<uint32_t*>(base + xbytes + kAsyncRows * 24);
+    }
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) async_issue(a, sp, x, tile, buf[0]);
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const AsyncBuf& cur = buf[it & 1];
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) {
+            async_issue(a, sp, x, next, buf[(it + 1) & 1]);
+            cp_async_wait<1>();          // this thread's copies of `tile` have landed
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();                 // ... and everybody else's
+        // largest exponent of the staged windows
+        uint32_t mx = 0;
+        for (int e = tid; e < sp.elems; e += kAsyncThreads) mx = max(mx, uint32_t(cur.xw[e].y) & 0x7FFFFFFFu);
+        mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+        if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+        __syncthreads();
+        mx = 0;
+#pragma unroll
+        for (int w = 0; w < kAsyncThreads / 32; ++w) mx = max(mx, s_red[w]);
+        const uint32_t emax = mx >> 20;
+        const bool exact_path = emax < 64u || emax >= 2047u;
+        if (!exact_path)
+            for (int e = tid; e < sp.elems; e += kAsyncThreads) {
+                const int2 b = cur.xw[e];
+                cur.xw[e] = limbs_of(uint32_t(b.x), uint32_t(b.y), emax);
+            }
+        __syncthreads();
+        const int64_t r = tile * kAsyncRows + tid;
+        if (r < a.n) {
+            uint32_t w[kMaxRecordWords];
+            {
+                const uint4 v16 = cur.r16[tid];
+                const uint2 v8 = cur.r8[tid];
+                w[0] = v16.x; w[1] = v16.y; w[2] = v16.z; w[3] = v16.w;
+                w[4] = v8.x; w[5] = v8.y; w[6] = cur.r4[tid];
+            }
+            if (exact_path) {
+                const uint32_t mask = smask[byte_of(w, NU) & 31];
+                double acc = 0.0;
+#pragma unroll
+                for (int u = 0; u < NU; ++u)
+                    if ((mask >> u) & 1u) {
+                        const int2 b = cur.xw[tid + sp.soff[u]];
+                        acc = fma(sdict[byte_of(w, u) & 7], __hiloint2double(b.y, b.x), acc);
+                    }
+                y[r] = acc;
+            } else {
+                int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
+                if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+#pragma unroll
+                    for (int k = 0; k < NU / RUN; ++k) {
+                        const int2* p = cur.xw + tid + sp.soff[k * RUN];
+#pragma unroll
+                        for (int j = 0; j < RUN; ++j) {
+                            const int u = k * RUN + j;
+                            const int2 v = p[j];
+                            ah[u % 3] += int64_t(a.dom_m[u]) * v.y;
+                            al[u % 3] += int64_t(a.dom_m[u]) * v.x;
+                        }
+                    }
+                } else {
+                    uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+                    for (int k = 0; k < (NU + 3) / 4; ++k)
+                        mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
+#pragma unroll
+                    for (int k = 0; k < NU / RUN; ++k) {
+                        const int2* p = cur.xw + tid + sp.soff[k * RUN];
+#pragma unroll
+                        for (int j = 0; j < RUN; ++j) {
+                            const int u = k * RUN + j;
+                            const int32_t m = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+                            const int2 v = p[j];
+                            ah[u % 3] += int64_t(m) * v.y;
+                            al[u % 3] += int64_t(m) * v.x;
+                        }
+                    }
+                }
+                const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
+                y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
+            }
+        }
+        __syncthreads();                 // done with `cur` before it is refilled
+    }
+}
+
 // ------------------------------ SpMM, FAST order, pre-converted block X ---
 // Per-column largest exponents (one word per column, from the partial
 // maxima of xmax_cols_kernel), then X converted once into a fixed-point
@@ -1070,6 +1244,25 @@ cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& s
     if (sp.rows_per_thread == 2) return go(pattern_fast_xstaged_kernel<7, 27, 2, 3>);
     if (sp.rows_per_thread == 4) return go(pattern_fast_xstaged_kernel<7, 27, 4, 3>);
     return cudaErrorInvalidValue;
+}
+
+
+cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                      int num_sms, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (!(a.run_len == 3 && a.nu == 27 && a.words == 7) || sp.rows != kAsyncRows) return cudaErrorNotSupported;
+    const int64_t ntiles = (a.n + kAsyncRows - 1) / kAsyncRows;
+    const size_t xbytes = (size_t(sp.elems) * 8 + 15) / 16 * 16;
+    const size_t smem = 2 * (xbytes + size_t(kAsyncRows) * 28);
+    auto kernel = pattern_fast_async_kernel<27, 3>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    const unsigned grid = unsigned(std::min<int64_t>(ntiles, num_sms));
+    kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, y, ntiles);
+    return cudaGetLastError();
 }
 
 bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }

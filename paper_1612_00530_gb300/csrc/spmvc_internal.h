@@ -169,6 +169,8 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
                                        cudaStream_t s);
 cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                         uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s);
+cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                      int num_sms, cudaStream_t s);
 cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
@@ -223,6 +225,9 @@ struct spmv_mat_s {
     int32_t* d_err = nullptr;
     spmvc::StagePlan stage{};          // FAST order: shared-memory staging plan
     bool stage_ok = false;
+    spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
+    bool async_ok = false;
+    int32_t num_sms = 0;
     int32_t fast_variant = 0;          // 0 direct, 1 staged tiles, 2 pre-converted x copy
     int2* d_xfixed = nullptr;          // FAST order: fixed-point copy of x with guard zones
     int64_t xfixed_guard = 0;

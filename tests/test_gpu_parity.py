@@ -335,7 +335,7 @@ def test_fast_variants_on_hpcg_grids():
         xbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
         xbuf[1:] = torch.from_numpy(x).cuda()
         xoff = xbuf[1:]
-        for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0), (3, 512), (3, 1024), (3, 2048)]:
+        for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0), (3, 512), (3, 1024), (3, 2048), (4, 0)]:
             P.spmv_set_variant(C, v, t)
             check_fast(run(C, x), y_ref, scale)
             assert np.array_equal(run(C, xi), yi_ref)
@@ -400,7 +400,7 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
     x = spmv_inputs.uniform_vector(n, seed=12) * xscale
     want = fast_order_exact_model(rowptr, col, mult, mult_exp, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
-    for v, t in [(0, 0), (1, 512), (1, 2048), (2, 0), (3, 1024), (3, 2048)]:
+    for v, t in [(0, 0), (1, 512), (1, 2048), (2, 0), (3, 1024), (3, 2048), (4, 0)]:
         P.spmv_set_variant(C, v, t)
         got = run(C, x)
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (v, t)
@@ -438,3 +438,32 @@ def test_fast_spmm_preconverted_block(k):
     P.spmm_apply(C, X2, Y2)
     torch.cuda.synchronize()
     check_fast(Y2.cpu().numpy()[:, 0], Y_ref[:, 0], scale[:, 0])
+
+
+def test_fast_variant_persistent_many_tiles():
+    """The persistent double-buffered kernel walking several tiles per CTA
+    (96^3 rows = 864 tiles), on sampled rows and on A*1, plus the exact
+    fallback for non-finite x."""
+    g = (96, 96, 96)
+    n = 96 ** 3
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    P.spmv_set_variant(C, 4, 0)
+    x = spmv_inputs.uniform_vector(n, seed=13)
+    rows = np.unique(np.concatenate([np.random.default_rng(13).integers(0, n, 20000), np.arange(0, 3000),
+                                     np.arange(n - 3000, n)]))
+    y = run(C, x)
+    y_ref = oracle.hpcg_spmv_rows(*g, rows, x)
+    scale = 52.0 * np.abs(x[rows]) - oracle.hpcg_spmv_rows(*g, rows, np.abs(x))
+    assert np.max(np.abs(y[rows] - y_ref) / scale) <= TOL
+    rp, _, _ = oracle.hpcg_csr(*g)
+    assert np.array_equal(run(C, np.ones(n)), 27.0 - np.diff(rp))
+    xi = spmv_inputs.integer_vector(n, seed=14)
+    assert np.array_equal(run(C, xi)[rows], oracle.hpcg_spmv_rows(*g, rows, xi))
+    xb = x.copy()
+    xb[n // 3] = np.inf
+    yb = run(C, xb)
+    yb_ref = oracle.hpcg_spmv_rows(*g, rows, xb)
+    ok = ~np.isnan(yb_ref)
+    assert np.array_equal(np.isnan(yb[rows]), ~ok)
+    assert np.array_equal(yb[rows][ok], yb_ref[ok])
+    assert P.spmv_info(C)["fast_variant"] == 4
