@@ -678,30 +678,28 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
     const int tid = threadIdx.x;
     if (tid < 8) sdict[tid] = tid < a.dict_size ? a.dict[tid] : 0.0;
     if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
-    // two buffers: [x windows | r16 | r8 | r4]
-    const size_t xbytes = (size_t(sp.elems) * 8 + 15) / 16 * 16;
-    const size_t bbytes = xbytes + size_t(kAsyncRows) * 28;
-    AsyncBuf buf[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        char* base = reinterpret_cast<char*>(smem4) + q * bbytes;
-        buf[q].xw = reinterpret_cast<int2*>(base);
-        buf[q].r16 = reinterpret_cast<uint4*>(base + xbytes);
-        buf[q].r8 = reinterpret_cast<uint2*>(base + xbytes + kAsyncRows * 16);
-        buf[q].r4 = reinterpret_cast<uint32_t*>(base + xbytes + kAsyncRows * 24);
-    }
+    // two buffers, each [x windows | r16 | r8 | r4]; pointers computed from
+    // the buffer index (no runtime-indexed local arrays)
+    const uint32_t xbytes = (uint32_t(sp.elems) * 8u + 15u) / 16u * 16u;
+    const uint32_t bbytes = xbytes + uint32_t(kAsyncRows) * 28u;
+    char* const smem = reinterpret_cast<char*>(smem4);
+    auto buffer = [&](int q) {
+        AsyncBuf bb;
+        char* base = smem + q * bbytes;
+        bb.xw = reinterpret_cast<int2*>(base);
+        bb.r16 = reinterpret_cast<uint4*>(base + xbytes);
+        bb.r8 = reinterpret_cast<uint2*>(base + xbytes + kAsyncRows * 16);
+        bb.r4 = reinterpret_cast<uint32_t*>(base + xbytes + kAsyncRows * 24);
+        return bb;
+    };
     int64_t tile = blockIdx.x;
-    if (tile < ntiles) async_issue(a, sp, x, tile, buf[0]);
+    if (tile < ntiles) async_issue(a, sp, x, tile, buffer(0));
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-        const AsyncBuf& cur = buf[it & 1];
+        const AsyncBuf cur = buffer(it & 1);
+        cp_async_wait<0>();              // this thread's copies of `tile` have landed
+        __syncthreads();                 // everybody's have, and the other buffer is free
         const int64_t next = tile + gridDim.x;
-        if (next < ntiles) {
-            async_issue(a, sp, x, next, buf[(it + 1) & 1]);
-            cp_async_wait<1>();          // this thread's copies of `tile` have landed
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();                 // ... and everybody else's
+        if (next < ntiles) async_issue(a, sp, x, next, buffer((it + 1) & 1));
         // largest exponent of the staged windows
         uint32_t mx = 0;
         for (int e = tid; e < sp.elems; e += kAsyncThreads) mx = max(mx, uint32_t(cur.xw[e].y) & 0x7FFFFFFFu);
@@ -774,7 +772,8 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
                 y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
             }
         }
-        __syncthreads();                 // done with `cur` before it is refilled
+        // the barrier at the top of the next iteration keeps `cur` from being
+        // refilled while any thread still reads it
     }
 }
 
