@@ -148,8 +148,10 @@ typedef struct {
     int32_t fast_tile_rows;     /* FAST order: rows per shared-memory tile of the
                                    staged kernel (0 = no staged kernel for A) */
     int32_t fast_variant;       /* FAST kernel in use: 0 direct, 1 staged tiles,
-                                   2 pre-converted fixed-point copy of x;
-                                   -1 before A's first device call */
+                                   2 pre-converted fixed-point copy of x, 3 staged
+                                   tiles of that copy, 4 persistent double-buffered
+                                   tiles, 5 the same from the copy; -1 before A's
+                                   first device call */
 } spmv_info_t;
 
 /* Fills *out with the sizes and statistics of A (host only). */
@@ -204,15 +206,17 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
  * A, and remembers it for matrices with the same signature (device name, n,
  * nnz, union size) uploaded later in this process.  reps: timed launches per
  * candidate (default 10 when <= 0).  *choice (may be NULL) receives the
- * chosen tile rows for the staged kernel, 1 for the pre-converted kernel,
- * 0 when A has nothing to tune.
+ * chosen tile rows for a staged kernel, 1 for the pre-converted kernel, 4 or
+ * 5 for the persistent kernels, 0 when A has nothing to tune.
  * Synchronous, uses the legacy default stream: call it outside any stream
  * capture. */
 int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_t *choice);
 
 /* Selects A's FAST kernel by hand (what spmv_autotune chooses): variant 0
  * direct, 1 staged tiles of tile_rows rows (512, 1024 or 2048), 2
- * pre-converted copy of x.  SPMV_EUNSUPPORTED when A has no such kernel.
+ * pre-converted copy of x, 3 staged tiles of that copy, 4 persistent
+ * double-buffered tiles, 5 the same fed from the copy (tile_rows ignored for
+ * 0, 2, 4, 5).  SPMV_EUNSUPPORTED when A has no such kernel.
  * Copies A to the device if it is not there yet. */
 int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 

@@ -246,7 +246,8 @@ int ensure_device(spmv_mat_s* m) {
         if (p.fast_ok && v.run_len == 3 && v.nu == 27 && v.words == 7 &&
             make_stage_plan(p.uoff, 1, 1024, 12288, &m->async_plan)) {
             const size_t xbytes = (size_t(m->async_plan.elems) * 8 + 15) / 16 * 16;
-            m->async_ok = 2 * (xbytes + 1024 * 28) <= 220 * 1024;
+            const size_t xpbytes = (size_t(std::max(m->async_plan.elems, m->async_plan.elems_padded)) * 8 + 15) / 16 * 16;
+            m->async_ok = 2 * (std::max(xbytes, xpbytes) + 1024 * 28) <= 220 * 1024;
         }
         {
             int d = 0, sms = 0;
@@ -254,7 +255,7 @@ int ensure_device(spmv_mat_s* m) {
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
             m->num_sms = sms > 0 ? sms : 152;
         }
-        if (m->fast_variant == 4 && !m->async_ok) m->fast_variant = 2;
+        if ((m->fast_variant == 4 || m->fast_variant == 5) && !m->async_ok) m->fast_variant = 2;
         if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
         if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
     } else {
@@ -501,6 +502,8 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
     if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
     else if (A->fmt == SPMV_FMT_PATTERN)
         e = A->order != SPMV_ORDER_FAST ? launch_pattern_col_f64(A->pat_view, x, y, s)
+            : A->fast_variant == 5 ? launch_pattern_fast_async_x(A->pat_view, A->async_plan, x, y, A->d_scratch_words,
+                                                                 A->d_xfixed, A->xfixed_guard, A->num_sms, s)
             : A->fast_variant == 4 ? launch_pattern_fast_async(A->pat_view, A->async_plan, x, y, A->num_sms, s)
             : A->fast_variant == 3 ? launch_pattern_fast_xstaged(A->pat_view, A->stage, x, y, A->d_scratch_words,
                                                                  A->d_xfixed, A->xfixed_guard, s)
@@ -598,6 +601,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     std::vector<Cand> cands;
     if (A->d_xfixed) cands.push_back(Cand{2, A->stage});
     if (A->async_ok) cands.push_back(Cand{4, A->async_plan});
+    if (A->async_ok && A->d_xfixed) cands.push_back(Cand{5, A->async_plan});
     if (A->stage_ok)
         for (int rpt : {1, 2, 4}) {
             StagePlan plan;
@@ -615,6 +619,9 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     for (const Cand& c : cands) {
         auto launch = [&]() {
             if (c.variant == 4) return launch_pattern_fast_async(A->pat_view, c.plan, x, y, A->num_sms, nullptr);
+            if (c.variant == 5)
+                return launch_pattern_fast_async_x(A->pat_view, c.plan, x, y, A->d_scratch_words, A->d_xfixed,
+                                                   A->xfixed_guard, A->num_sms, nullptr);
             return c.variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                           A->xfixed_guard, nullptr)
                  : c.variant == 3 ? launch_pattern_fast_xstaged(A->pat_view, c.plan, x, y, A->d_scratch_words,
@@ -635,13 +642,13 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     cudaEventDestroy(e1);
     A->fast_variant = pick.variant;
     if (pick.variant == 1 || pick.variant == 3) A->stage = pick.plan;
-    if (pick.variant == 4) A->async_plan = pick.plan;
+    if (pick.variant == 4 || pick.variant == 5) A->async_plan = pick.plan;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_variant[tune_key(A)] = pick.variant;
         if (pick.variant == 1 || pick.variant == 3) g_tune[tune_key(A)] = pick.plan.rows_per_thread;
     }
-    if (choice) *choice = (pick.variant == 1 || pick.variant == 3) ? pick.plan.rows : (pick.variant == 4 ? 4 : 1);
+    if (choice) *choice = (pick.variant == 1 || pick.variant == 3) ? pick.plan.rows : (pick.variant >= 4 ? pick.variant : 1);
     return SPMV_OK;
 }
 
@@ -656,9 +663,10 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows) {
         A->fast_variant = 2;
         return SPMV_OK;
     }
-    if (variant == 4) {
-        if (!A->async_ok) return fail(SPMV_EUNSUPPORTED, "no persistent double-buffered kernel for this union");
-        A->fast_variant = 4;
+    if (variant == 4 || variant == 5) {
+        if (!A->async_ok || (variant == 5 && !A->d_xfixed))
+            return fail(SPMV_EUNSUPPORTED, "no persistent double-buffered kernel for this union");
+        A->fast_variant = variant;
         return SPMV_OK;
     }
     if (variant != 1 && variant != 3) return fail(SPMV_EINVAL, "variant must be 0..4");

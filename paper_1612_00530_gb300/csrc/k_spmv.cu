@@ -665,11 +665,36 @@ __device__ __forceinline__ void async_issue(const PatternView& a, const StagePla
     cp_async_commit();
 }
 
-template <int NU, int RUN>
+// Issues the copies of tile `tile` of the pre-converted copy X (guard zones
+// make every window index valid; 16-byte copies on the padded layout).
+__device__ __forceinline__ void async_issue_x(const PatternView& a, const StagePlan& sp, const int2* __restrict__ X,
+                                              int64_t tile, const AsyncBuf& b) {
+    const int tid = threadIdx.x;
+    const int64_t r0 = tile * kAsyncRows;
+#pragma unroll
+    for (int sg = 0; sg < kMaxSegments; ++sg) {
+        if (sg >= sp.nseg) break;
+        const int4* src = reinterpret_cast<const int4*>(X + (r0 + sp.seg_min[sg] - sp.seg_pad[sg]));
+        int4* dst = reinterpret_cast<int4*>(b.xw + sp.seg_pbase[sg]);
+        const int len2 = (kAsyncRows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2;
+        for (int e = tid; e < len2; e += kAsyncThreads) cp_async16(dst + e, src + e, true);
+    }
+    const int64_t r = r0 + tid;
+    const bool ok = r < a.n;
+    const int64_t rs = ok ? r : 0;
+    cp_async16(b.r16 + tid, a.p16a + rs, ok);
+    cp_async8(b.r8 + tid, a.p8 + rs, ok);
+    cp_async4(b.r4 + tid, a.p4 + rs, ok);
+    cp_async_commit();
+}
+
+template <int NU, int RUN, bool PRECONVERTED>
 __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(PatternView a, StagePlan sp,
                                                                               const double* __restrict__ x,
+                                                                              const int2* __restrict__ X,
                                                                               double* __restrict__ y,
-                                                                              int64_t ntiles) {
+                                                                              int64_t ntiles,
+                                                                              const uint32_t* __restrict__ partial) {
     constexpr int WORDS = 7;
     extern __shared__ int4 smem4[];
     __shared__ uint32_t s_red[kAsyncThreads / 32];
@@ -680,9 +705,12 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
     if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
     // two buffers, each [x windows | r16 | r8 | r4]; pointers computed from
     // the buffer index (no runtime-indexed local arrays)
-    const uint32_t xbytes = (uint32_t(sp.elems) * 8u + 15u) / 16u * 16u;
+    const uint32_t xbytes = (uint32_t(PRECONVERTED ? sp.elems_padded : sp.elems) * 8u + 15u) / 16u * 16u;
     const uint32_t bbytes = xbytes + uint32_t(kAsyncRows) * 28u;
     char* const smem = reinterpret_cast<char*>(smem4);
+    // FAST order scale: the largest exponent of x (left by the conversion
+    // pass) for the pre-converted copy; per tile otherwise
+    const uint32_t emax_x = PRECONVERTED ? __ldg(partial + kXmaxBlocks) : 0u;
     auto buffer = [&](int q) {
         AsyncBuf bb;
         char* base = smem + q * bbytes;
@@ -692,31 +720,46 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
         bb.r4 = reinterpret_cast<uint32_t*>(base + xbytes + kAsyncRows * 24);
         return bb;
     };
+    const bool x_exact = PRECONVERTED && (emax_x < 64u || emax_x >= 2047u);
+    auto issue = [&](int64_t t, const AsyncBuf& bb) {
+        if (PRECONVERTED && !x_exact) async_issue_x(a, sp, X, t, bb);
+        else async_issue(a, sp, x, t, bb);
+    };
     int64_t tile = blockIdx.x;
-    if (tile < ntiles) async_issue(a, sp, x, tile, buffer(0));
+    if (tile < ntiles) issue(tile, buffer(0));
     for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
         const AsyncBuf cur = buffer(it & 1);
         cp_async_wait<0>();              // this thread's copies of `tile` have landed
         __syncthreads();                 // everybody's have, and the other buffer is free
         const int64_t next = tile + gridDim.x;
-        if (next < ntiles) async_issue(a, sp, x, next, buffer((it + 1) & 1));
-        // largest exponent of the staged windows
-        uint32_t mx = 0;
-        for (int e = tid; e < sp.elems; e += kAsyncThreads) mx = max(mx, uint32_t(cur.xw[e].y) & 0x7FFFFFFFu);
-        mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-        if ((tid & 31) == 0) s_red[tid >> 5] = mx;
-        __syncthreads();
-        mx = 0;
+        if (next < ntiles) issue(next, buffer((it + 1) & 1));
+        uint32_t emax;
+        bool exact_path;
+        int soff_shift;     // pre-converted copy: padded layout
+        if constexpr (PRECONVERTED) {
+            emax = emax_x;
+            exact_path = x_exact;
+            soff_shift = 1;
+        } else {
+            soff_shift = 0;
+            // largest exponent of the staged windows
+            uint32_t mx = 0;
+            for (int e = tid; e < sp.elems; e += kAsyncThreads) mx = max(mx, uint32_t(cur.xw[e].y) & 0x7FFFFFFFu);
+            mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+            if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+            __syncthreads();
+            mx = 0;
 #pragma unroll
-        for (int w = 0; w < kAsyncThreads / 32; ++w) mx = max(mx, s_red[w]);
-        const uint32_t emax = mx >> 20;
-        const bool exact_path = emax < 64u || emax >= 2047u;
-        if (!exact_path)
-            for (int e = tid; e < sp.elems; e += kAsyncThreads) {
-                const int2 b = cur.xw[e];
-                cur.xw[e] = limbs_of(uint32_t(b.x), uint32_t(b.y), emax);
-            }
-        __syncthreads();
+            for (int w = 0; w < kAsyncThreads / 32; ++w) mx = max(mx, s_red[w]);
+            emax = mx >> 20;
+            exact_path = emax < 64u || emax >= 2047u;
+            if (!exact_path)
+                for (int e = tid; e < sp.elems; e += kAsyncThreads) {
+                    const int2 b = cur.xw[e];
+                    cur.xw[e] = limbs_of(uint32_t(b.x), uint32_t(b.y), emax);
+                }
+            __syncthreads();
+        }
         const int64_t r = tile * kAsyncRows + tid;
         if (r < a.n) {
             uint32_t w[kMaxRecordWords];
@@ -732,7 +775,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
 #pragma unroll
                 for (int u = 0; u < NU; ++u)
                     if ((mask >> u) & 1u) {
-                        const int2 b = cur.xw[tid + sp.soff[u]];
+                        const int2 b = cur.xw[tid + sp.soff[u]];   // raw copies (unpadded layout)
                         acc = fma(sdict[byte_of(w, u) & 7], __hiloint2double(b.y, b.x), acc);
                     }
                 y[r] = acc;
@@ -741,7 +784,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
                 if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
 #pragma unroll
                     for (int k = 0; k < NU / RUN; ++k) {
-                        const int2* p = cur.xw + tid + sp.soff[k * RUN];
+                        const int2* p = cur.xw + tid + (soff_shift ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
 #pragma unroll
                         for (int j = 0; j < RUN; ++j) {
                             const int u = k * RUN + j;
@@ -757,7 +800,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
                         mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
 #pragma unroll
                     for (int k = 0; k < NU / RUN; ++k) {
-                        const int2* p = cur.xw + tid + sp.soff[k * RUN];
+                        const int2* p = cur.xw + tid + (soff_shift ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
 #pragma unroll
                         for (int j = 0; j < RUN; ++j) {
                             const int u = k * RUN + j;
@@ -844,6 +887,95 @@ __global__ void __launch_bounds__(kBlock) pattern_spmm_fast_x_kernel(PatternView
     }
     const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
     Y[r * ldy + j] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+}
+
+
+// SpMM, FAST order, one thread per (row, group of KC columns): the record,
+// the dominant-record vote and the multipliers are decoded once per KC
+// columns, and X is read as 16-byte pairs of columns.
+template <int KC, int NU, int RUN>
+__global__ void __launch_bounds__(kBlock, 2) pattern_spmm_rows_kernel(PatternView a, int k, const double* __restrict__ X,
+                                                                   int64_t ldx, const int2* __restrict__ Xf,
+                                                                   double* __restrict__ Y, int64_t ldy,
+                                                                   const uint32_t* __restrict__ emax_cols) {
+    constexpr int WORDS = (NU + 4) / 4;
+    const int ng = k / KC;
+    const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t r = idx / ng;
+    const int g = int(idx - r * ng);
+    if (r >= a.n) return;
+    const int c0 = g * KC;
+    int em[KC];
+    bool exact = false;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+        em[c] = int(__ldg(emax_cols + c0 + c));
+        exact = exact || em[c] < 64 || em[c] >= 2047;
+    }
+    uint32_t w[kMaxRecordWords];
+    load_record<WORDS>(a, r, w);
+    if (exact) {
+        const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
+#pragma unroll 1
+        for (int c = 0; c < KC; ++c) {
+            double acc = 0.0;
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+                if ((mask >> u) & 1u)
+                    acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __ldg(X + (r + a.uoff[u]) * ldx + c0 + c), acc);
+            Y[r * ldy + c0 + c] = acc;
+        }
+        return;
+    }
+    // the row's multipliers, once (kernel parameters when the whole warp
+    // carries the dominant record)
+    int32_t mult[NU];
+    if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) mult[u] = a.dom_m[u];
+    } else {
+        uint32_t mw[(NU + 3) / 4];
+#pragma unroll
+        for (int q = 0; q < (NU + 3) / 4; ++q) mw[q] = prmt(a.mult_lo, a.mult_hi, prmt(w[q] | (w[q] >> 4), 0u, 0x0020u));
+#pragma unroll
+        for (int u = 0; u < NU; ++u) mult[u] = int32_t(prmt(mw[u >> 2], 0u, uint32_t(u & 3) * 0x1111u + 0x8880u));
+    }
+    const int2* __restrict__ Xr = Xf + r * k + c0;
+    if constexpr (KC >= 2) {
+        // a pair of columns per pass over the slots
+#pragma unroll 1
+        for (int c = 0; c < KC; c += 2) {
+            int64_t ah0 = 0, al0 = 0, ah1 = 0, al1 = 0;
+#pragma unroll
+            for (int q = 0; q < NU / RUN; ++q) {
+                const int2* __restrict__ p = Xr + int64_t(a.uoff[q * RUN]) * k + c;
+#pragma unroll
+                for (int i = 0; i < RUN; ++i) {
+                    const int32_t m = mult[q * RUN + i];
+                    const int4 v = __ldg(reinterpret_cast<const int4*>(p + int64_t(i) * k));
+                    ah0 += int64_t(m) * v.y;
+                    al0 += int64_t(m) * v.x;
+                    ah1 += int64_t(m) * v.w;
+                    al1 += int64_t(m) * v.z;
+                }
+            }
+            Y[r * ldy + c0 + c] = fixed_to_double(ah0 * (int64_t(1) << 26) + al0, em[c] - 1075 + a.mult_exp);
+            Y[r * ldy + c0 + c + 1] = fixed_to_double(ah1 * (int64_t(1) << 26) + al1, em[c + 1] - 1075 + a.mult_exp);
+        }
+    } else {
+        int64_t ah = 0, al = 0;
+#pragma unroll
+        for (int q = 0; q < NU / RUN; ++q) {
+            const int2* __restrict__ p = Xr + int64_t(a.uoff[q * RUN]) * k;
+#pragma unroll
+            for (int i = 0; i < RUN; ++i) {
+                const int2 v = __ldg(p + int64_t(i) * k);
+                ah += int64_t(mult[q * RUN + i]) * v.y;
+                al += int64_t(mult[q * RUN + i]) * v.x;
+            }
+        }
+        Y[r * ldy + c0] = fixed_to_double(ah * (int64_t(1) << 26) + al, em[0] - 1075 + a.mult_exp);
+    }
 }
 
 // ------------------------------------ binary32 COLUMN order, specialised -
@@ -1253,14 +1385,37 @@ cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp,
     const int64_t ntiles = (a.n + kAsyncRows - 1) / kAsyncRows;
     const size_t xbytes = (size_t(sp.elems) * 8 + 15) / 16 * 16;
     const size_t smem = 2 * (xbytes + size_t(kAsyncRows) * 28);
-    auto kernel = pattern_fast_async_kernel<27, 3>;
+    auto kernel = pattern_fast_async_kernel<27, 3, false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  int(cudaSharedmemCarveoutMaxShared));
     if (e != cudaSuccess) return e;
     const unsigned grid = unsigned(std::min<int64_t>(ntiles, num_sms));
-    kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, y, ntiles);
+    kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, nullptr, y, ntiles, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_fast_async_x(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                        uint32_t* partial, int2* X_guarded, int64_t guard, int num_sms,
+                                        cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (!(a.run_len == 3 && a.nu == 27 && a.words == 7) || sp.rows != kAsyncRows) return cudaErrorNotSupported;
+    int2* X = X_guarded + guard;
+    xmax_kernel<<<kXmaxBlocks, 1024, 0, s>>>(x, a.n, partial);
+    convert_x_kernel<<<kXmaxBlocks * 8, 256, 0, s>>>(reinterpret_cast<const uint2*>(x), a.n, partial, X);
+    const int64_t ntiles = (a.n + kAsyncRows - 1) / kAsyncRows;
+    // both layouts must fit: raw windows for the exact fallback, padded ones otherwise
+    const size_t xbytes = (size_t(std::max(sp.elems, sp.elems_padded)) * 8 + 15) / 16 * 16;
+    const size_t smem = 2 * (xbytes + size_t(kAsyncRows) * 28);
+    auto kernel = pattern_fast_async_kernel<27, 3, true>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared));
+    if (e != cudaSuccess) return e;
+    const unsigned grid = unsigned(std::min<int64_t>(ntiles, num_sms));
+    kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, X, y, ntiles, partial);
     return cudaGetLastError();
 }
 
@@ -1349,11 +1504,16 @@ cudaError_t launch_pattern_spmm_fast_x(const PatternView& a, int k, const double
     xmax_cols_kernel<<<kXmaxBlocks, 256, 0, s>>>(X, a.n, k, ldx, partial);
     cols_emax_kernel<<<1, 64, 0, s>>>(partial, k, emax);
     convert_cols_kernel<<<kXmaxBlocks * 16, 256, 0, s>>>(X, ldx, a.n, k, emax, Xf);
-    const unsigned grid = grid_of(a.n * k);
-    if (a.run_len == 3 && a.nu == 27)
-        pattern_spmm_fast_x_kernel<7, 27, 3><<<grid, kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax);
-    else
-        return cudaErrorNotSupported;
+    if (!(a.run_len == 3 && a.nu == 27)) return cudaErrorNotSupported;
+    // columns per thread: the widest of 8, 4, 2, 1 that divides k
+    const int kc = (k % 8 == 0) ? 8 : (k % 4 == 0) ? 4 : (k % 2 == 0) ? 2 : 1;
+    const unsigned grid = grid_of(a.n * (k / kc));
+    switch (kc) {
+        case 8: pattern_spmm_rows_kernel<8, 27, 3><<<grid, kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax); break;
+        case 4: pattern_spmm_rows_kernel<4, 27, 3><<<grid, kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax); break;
+        case 2: pattern_spmm_rows_kernel<2, 27, 3><<<grid, kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax); break;
+        default: pattern_spmm_fast_x_kernel<7, 27, 3><<<grid_of(a.n * k), kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax);
+    }
     return cudaGetLastError();
 }
 

@@ -171,6 +171,9 @@ cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& s
                                         uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                       int num_sms, cudaStream_t s);
+cudaError_t launch_pattern_fast_async_x(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                        uint32_t* partial, int2* X_guarded, int64_t guard, int num_sms,
+                                        cudaStream_t s);
 cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
@@ -228,7 +231,8 @@ struct spmv_mat_s {
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;
-    int32_t fast_variant = 0;          // 0 direct, 1 staged tiles, 2 pre-converted x copy
+    int32_t fast_variant = 0;          // 0 direct, 1 staged, 2 pre-converted, 3 staged pre-converted,
+                                       // 4 persistent double-buffered, 5 the same from the pre-converted copy
     int2* d_xfixed = nullptr;          // FAST order: fixed-point copy of x with guard zones
     int64_t xfixed_guard = 0;
     int2* d_xfixed_block = nullptr;    // FAST SpMM: fixed-point copy of X (guard rows), k_cap columns

@@ -335,7 +335,7 @@ def test_fast_variants_on_hpcg_grids():
         xbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
         xbuf[1:] = torch.from_numpy(x).cuda()
         xoff = xbuf[1:]
-        for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0), (3, 512), (3, 1024), (3, 2048), (4, 0)]:
+        for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0), (3, 512), (3, 1024), (3, 2048), (4, 0), (5, 0)]:
             P.spmv_set_variant(C, v, t)
             check_fast(run(C, x), y_ref, scale)
             assert np.array_equal(run(C, xi), yi_ref)
@@ -354,10 +354,10 @@ def test_autotune_keeps_results():
     x = torch.from_numpy(x_np).cuda()
     y = torch.empty_like(x)
     rows = P.spmv_autotune(C, x, y, reps=3)
-    assert rows in (1, 512, 1024, 2048)
+    assert rows in (1, 4, 5, 512, 1024, 2048)
     info = P.spmv_info(C)
-    assert info["fast_variant"] in ((2,) if rows == 1 else (1, 3))
-    if rows != 1:
+    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3))
+    if rows not in (1, 4, 5):
         assert info["fast_tile_rows"] == rows
     y_ref = oracle.spmv(rowptr, col, val, x_np)
     check_fast(run(C, x_np), y_ref, abs_row_sums(rowptr, col, val, x_np))
@@ -400,7 +400,7 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
     x = spmv_inputs.uniform_vector(n, seed=12) * xscale
     want = fast_order_exact_model(rowptr, col, mult, mult_exp, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
-    for v, t in [(0, 0), (1, 512), (1, 2048), (2, 0), (3, 1024), (3, 2048), (4, 0)]:
+    for v, t in [(0, 0), (1, 512), (1, 2048), (2, 0), (3, 1024), (3, 2048), (4, 0), (5, 0)]:
         P.spmv_set_variant(C, v, t)
         got = run(C, x)
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (v, t)
@@ -447,8 +447,13 @@ def test_fast_variant_persistent_many_tiles():
     g = (96, 96, 96)
     n = 96 ** 3
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
-    P.spmv_set_variant(C, 4, 0)
     x = spmv_inputs.uniform_vector(n, seed=13)
+    for variant in (5, 4):
+        P.spmv_set_variant(C, variant, 0)
+        check_persistent(C, g, n, x)
+
+
+def check_persistent(C, g, n, x):
     rows = np.unique(np.concatenate([np.random.default_rng(13).integers(0, n, 20000), np.arange(0, 3000),
                                      np.arange(n - 3000, n)]))
     y = run(C, x)
@@ -470,4 +475,3 @@ def test_fast_variant_persistent_many_tiles():
     assert np.array_equal(yb[~fin & ~np.isnan(yb_ref)], yb_ref[~fin & ~np.isnan(yb_ref)])
     sb = 52.0 * np.abs(xb[rows]) - oracle.hpcg_spmv_rows(*g, rows, np.abs(xb))
     assert np.max(np.abs(yb[fin] - yb_ref[fin]) / sb[fin]) <= TOL
-    assert P.spmv_info(C)["fast_variant"] == 4
