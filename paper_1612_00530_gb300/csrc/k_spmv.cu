@@ -1505,8 +1505,9 @@ cudaError_t launch_pattern_spmm_fast_x(const PatternView& a, int k, const double
     cols_emax_kernel<<<1, 64, 0, s>>>(partial, k, emax);
     convert_cols_kernel<<<kXmaxBlocks * 16, 256, 0, s>>>(X, ldx, a.n, k, emax, Xf);
     if (!(a.run_len == 3 && a.nu == 27)) return cudaErrorNotSupported;
-    // columns per thread: the widest of 8, 4, 2, 1 that divides k
-    const int kc = (k % 8 == 0) ? 8 : (k % 4 == 0) ? 4 : (k % 2 == 0) ? 2 : 1;
+    // columns per thread: 4 or 2 for narrow blocks (measured faster there);
+    // wider blocks use one thread per (row, column)
+    const int kc = (k == 4) ? 4 : (k == 2) ? 2 : 1;
     const unsigned grid = grid_of(a.n * (k / kc));
     switch (kc) {
         case 8: pattern_spmm_rows_kernel<8, 27, 3><<<grid, kBlock, 0, s>>>(a, k, X, ldx, Xf, Y, ldy, emax); break;
