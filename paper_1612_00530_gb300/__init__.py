@@ -10,7 +10,8 @@ The functions keep the C names: spmv_build, spmv_build_csr, spmv_compress,
 spmv_set_order, spmv_info, spmv_decompress, spmv_export, spmv_import,
 spmv_apply, spmv_apply_host, spmv_apply_f32, spmm_apply, spmv_batch_create,
 spmv_batch_launch, spmv_batch_free, spmv_apply_batched, cg_solve,
-spmv_device_error, spmv_autotune, spmv_set_variant, spmv_version.
+spmv_device_error, spmv_autotune, spmv_set_variant, spmv_set_tile,
+spmm_apply_noalloc, spmv_version.
 """
 from __future__ import annotations
 
@@ -46,7 +47,8 @@ class spmv_info_t(ctypes.Structure):
                 ("n_patterns", _i32), ("union_size", _i32), ("record_bytes", _i32), ("max_row_nnz", _i32),
                 ("fast_eligible", _i32), ("n_slices", _i64), ("slices_value_raw", _i64), ("slices_col_raw", _i64),
                 ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64),
-                ("fast_tile_rows", _i32), ("fast_variant", _i32)]
+                ("fast_tile_rows", _i32), ("fast_variant", _i32), ("fast_block_threads", _i32),
+                ("reserved0", _i32)]
 
 
 class spmv_cg_opts(ctypes.Structure):
@@ -98,6 +100,7 @@ def library() -> ctypes.CDLL:
             "spmv_device_error": [_p, ctypes.POINTER(_i32)],
             "spmv_autotune": [_p, _p, _p, _i32, ctypes.POINTER(_i32)],
             "spmv_set_variant": [_p, _i32, _i32],
+            "spmv_set_tile": [_p, _i32, _i32, _i32],
             "spmm_apply_noalloc": [_p, _i32, _p, _i64, _p, _i64, _p],
         }
         for name, args in sig.items():
@@ -325,8 +328,15 @@ def spmv_autotune(A: SpmvMatrix, x, y, reps: int = 10) -> int:
 
 
 def spmv_set_variant(A: SpmvMatrix, variant: int, tile_rows: int = 0) -> None:
-    """FAST kernel by hand: 0 direct, 1 staged tiles (tile_rows), 2 pre-converted x."""
+    """FAST kernel by hand: 0 direct, 1 staged tiles (tile_rows), 2 pre-converted x,
+    3 staged tiles of that copy, 4/5 persistent double-buffered tiles."""
     _check(library().spmv_set_variant(A, variant, tile_rows))
+
+
+def spmv_set_tile(A: SpmvMatrix, variant: int, tile_rows: int, block_threads: int) -> None:
+    """spmv_set_variant with the staged kernel's block size (512, or 256 for
+    variant 1 on the full 27-slot union)."""
+    _check(library().spmv_set_tile(A, variant, tile_rows, block_threads))
 
 
 def spmv_device_error(A: SpmvMatrix) -> int:

@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <utility>
 
 #include "spmvc_internal.h"
 
@@ -80,7 +81,7 @@ void free_device(spmv_mat_s* m) {
 // Autotuner cache: (device name, n, nnz, union size) -> rows per thread of
 // the staged FAST kernel.
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;          // rows per thread of the staged kernel
+std::map<std::string, int> g_tune;          // staged kernel: threads * 16 + rows per thread
 std::map<std::string, int> g_tune_variant;  // FAST kernel variant
 
 std::string tune_key(const spmv_mat_s* m) {
@@ -98,10 +99,12 @@ int tuned_variant(const spmv_mat_s* m, int fallback) {
     return it == g_tune_variant.end() ? fallback : it->second;
 }
 
-int tuned_rows_per_thread(const spmv_mat_s* m, int fallback) {
+// (threads, rows per thread) of the staged kernel chosen by the autotuner
+std::pair<int, int> tuned_stage_shape(const spmv_mat_s* m, int threads, int rows_per_thread) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(tune_key(m));
-    return it == g_tune.end() ? fallback : it->second;
+    if (it == g_tune.end()) return {threads, rows_per_thread};
+    return {it->second / 16, it->second % 16};
 }
 
 // First device use: copy the stored form to the current device.
@@ -237,9 +240,9 @@ int ensure_device(spmv_mat_s* m) {
             m->fast_variant = tuned_variant(m, 2);
         }
         if (stage_supported(v.nu)) {
-            const int prefer = tuned_rows_per_thread(m, 4);
-            for (int rpt : {prefer, 4, 2, 1})
-                if (make_stage_plan(p.uoff, rpt, 512, 12288, &m->stage)) { m->stage_ok = true; break; }
+            const std::pair<int, int> prefer = tuned_stage_shape(m, 512, 4);
+            for (std::pair<int, int> sh : {prefer, std::make_pair(512, 4), std::make_pair(512, 2), std::make_pair(512, 1)})
+                if (make_stage_plan(p.uoff, sh.second, sh.first, 12288, &m->stage)) { m->stage_ok = true; break; }
         }
         // persistent double-buffered kernel: 1024-row tiles, two buffers must fit
         m->async_ok = false;
@@ -256,6 +259,7 @@ int ensure_device(spmv_mat_s* m) {
             m->num_sms = sms > 0 ? sms : 152;
         }
         if ((m->fast_variant == 4 || m->fast_variant == 5) && !m->async_ok) m->fast_variant = 2;
+        if (m->fast_variant == 6 && !(m->stage_ok && rstage_supported(m->stage))) m->fast_variant = 1;
         if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
         if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
     } else {
@@ -423,6 +427,7 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->fast_eligible = A->pat.fast_ok ? 1 : 0;
         out->fast_tile_rows = A->stage_ok ? A->stage.rows : 0;
         out->fast_variant = A->device >= 0 ? A->fast_variant : -1;
+        out->fast_block_threads = A->stage_ok ? A->stage.rows / A->stage.rows_per_thread : 0;
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
@@ -509,6 +514,7 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
                                                                  A->d_xfixed, A->xfixed_guard, s)
             : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                            A->xfixed_guard, s)
+            : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, s)
             : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
                                    : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
     else e = launch_delta_f64(A->dlt_view, x, y, s);
@@ -602,14 +608,29 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     if (A->d_xfixed) cands.push_back(Cand{2, A->stage});
     if (A->async_ok) cands.push_back(Cand{4, A->async_plan});
     if (A->async_ok && A->d_xfixed) cands.push_back(Cand{5, A->async_plan});
-    if (A->stage_ok)
+    if (A->stage_ok) {
+        const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
         for (int rpt : {1, 2, 4}) {
             StagePlan plan;
             if (make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) {
                 cands.push_back(Cand{1, plan});
-                if (A->d_xfixed && A->pat_view.run_len == 3 && A->pat_view.nu == 27) cands.push_back(Cand{3, plan});
+                if (A->d_xfixed && full27) cands.push_back(Cand{3, plan});
             }
         }
+        // 256-thread tiles (six resident CTAs per SM) and the register-staged
+        // kernel for the full 27-point union
+        if (full27) {
+            for (int rpt : {2, 4, 8}) {
+                StagePlan plan;
+                if (make_stage_plan(A->pat.uoff, rpt, 256, 12288, &plan)) cands.push_back(Cand{1, plan});
+            }
+            for (std::pair<int, int> sh : {std::make_pair(256, 4), std::make_pair(256, 2), std::make_pair(512, 2)}) {
+                StagePlan plan;
+                if (make_stage_plan(A->pat.uoff, sh.second, sh.first, 12288, &plan) && rstage_supported(plan))
+                    cands.push_back(Cand{6, plan});
+            }
+        }
+    }
     if (cands.size() <= 1) return SPMV_OK;
     cudaEvent_t e0, e1;
     SPMVC_CUDA(cudaEventCreate(&e0));
@@ -619,6 +640,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     for (const Cand& c : cands) {
         auto launch = [&]() {
             if (c.variant == 4) return launch_pattern_fast_async(A->pat_view, c.plan, x, y, A->num_sms, nullptr);
+            if (c.variant == 6) return launch_pattern_fast_rstaged(A->pat_view, c.plan, x, y, nullptr);
             if (c.variant == 5)
                 return launch_pattern_fast_async_x(A->pat_view, c.plan, x, y, A->d_scratch_words, A->d_xfixed,
                                                    A->xfixed_guard, A->num_sms, nullptr);
@@ -641,18 +663,20 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     A->fast_variant = pick.variant;
-    if (pick.variant == 1 || pick.variant == 3) A->stage = pick.plan;
+    const bool staged_pick = pick.variant == 1 || pick.variant == 3 || pick.variant == 6;
+    if (staged_pick) A->stage = pick.plan;
     if (pick.variant == 4 || pick.variant == 5) A->async_plan = pick.plan;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_variant[tune_key(A)] = pick.variant;
-        if (pick.variant == 1 || pick.variant == 3) g_tune[tune_key(A)] = pick.plan.rows_per_thread;
+        if (staged_pick)
+            g_tune[tune_key(A)] = (pick.plan.rows / pick.plan.rows_per_thread) * 16 + pick.plan.rows_per_thread;
     }
-    if (choice) *choice = (pick.variant == 1 || pick.variant == 3) ? pick.plan.rows : (pick.variant >= 4 ? pick.variant : 1);
+    if (choice) *choice = staged_pick ? pick.plan.rows : (pick.variant >= 4 ? pick.variant : 1);
     return SPMV_OK;
 }
 
-int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows) {
+int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (A->fmt != SPMV_FMT_PATTERN || !A->pat.fast_ok) return fail(SPMV_EUNSUPPORTED, "no FAST kernels for this matrix");
     int st = ensure_device(A);
@@ -669,17 +693,32 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows) {
         A->fast_variant = variant;
         return SPMV_OK;
     }
-    if (variant != 1 && variant != 3) return fail(SPMV_EINVAL, "variant must be 0..4");
-    if (variant == 3 && !(A->d_xfixed && A->pat_view.run_len == 3 && A->pat_view.nu == 27))
+    if (variant != 1 && variant != 3 && variant != 6) return fail(SPMV_EINVAL, "variant must be 0..6");
+    const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
+    if (variant == 3 && !(A->d_xfixed && full27))
         return fail(SPMV_EUNSUPPORTED, "no staged pre-converted kernel for this union");
     if (!stage_supported(static_cast<int>(A->pat.uoff.size()))) return fail(SPMV_EUNSUPPORTED, "no staged kernel for this union size");
+    if (block_threads != 512 && block_threads != 256) return fail(SPMV_EINVAL, "block_threads must be 256 or 512");
+    if (variant == 6 && !full27) return fail(SPMV_EUNSUPPORTED, "no register-staged kernel for this union");
+    if (block_threads == 256 && !((variant == 1 || variant == 6) && full27))
+        return fail(SPMV_EUNSUPPORTED, "256-thread tiles exist for the full 27-point union only");
+    const int rpt = tile_rows / block_threads;
+    const bool shape_ok = tile_rows > 0 && tile_rows % block_threads == 0 &&
+                          (block_threads == 512 ? (rpt == 1 || rpt == 2 || rpt == 4) : (rpt == 2 || rpt == 4 || rpt == 8));
     StagePlan plan;
-    if (tile_rows % 512 != 0 || !make_stage_plan(A->pat.uoff, tile_rows / 512, 512, 12288, &plan))
+    if (!shape_ok || !make_stage_plan(A->pat.uoff, rpt, block_threads, 12288, &plan))
         return fail(SPMV_EUNSUPPORTED, "tile does not fit shared memory (tile_rows 512, 1024 or 2048)");
+    if (variant == 6 && !rstage_supported(plan))
+        return fail(SPMV_EUNSUPPORTED, "register-staged kernel: tile_rows/threads 1024/256, 512/256 or 1024/512 "
+                                       "with windows of at most 2*pairs*threads elements");
     A->stage = plan;
     A->stage_ok = true;
     A->fast_variant = variant;
     return SPMV_OK;
+}
+
+int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows) {
+    return spmv_set_tile(A, variant, tile_rows, 512);
 }
 
 int spmv_free(spmv_mat_t A) {

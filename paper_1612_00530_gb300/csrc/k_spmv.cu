@@ -418,57 +418,24 @@ __device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t e
     return make_int2(int32_t(uint32_t(X) & 0x3FFFFFFu) * s1, int32_t(uint32_t(X >> 26)) * s1);
 }
 
-template <int WORDS, int NU, int RPT, int RUN>
-__global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
-                                                                            const double* __restrict__ x,
-                                                                            double* __restrict__ y) {
-    extern __shared__ int2 sx[];
-    __shared__ uint32_t s_red[kStageThreads / 32];
-    __shared__ uint32_t smask[32];
+// Phase 3 of the staged kernels: every thread sums RPT rows (r0 + tid +
+// i*THREADS) slot by slot from the tile's converted windows in shared memory
+// (raw words on the exact path) and rounds once.  w holds the record of the
+// thread's first row (loaded by the caller before the tile's barriers, when
+// that row exists); each row's loop issues the next row's record loads
+// before it sums, so record latency overlaps the previous row's work.
+template <int WORDS, int NU, int RPT, int RUN, int THREADS, bool VEC>
+__device__ __forceinline__ void staged_rows(const PatternView& a, const StagePlan& sp, const int2* sx,
+                                            const uint32_t* smask, int64_t r0, uint32_t emax, bool exact_path,
+                                            double* __restrict__ y, uint32_t (&w)[kMaxRecordWords]) {
     const int tid = threadIdx.x;
-    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
-    const uint2* __restrict__ xw = reinterpret_cast<const uint2*>(x);
-    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
-    // phase 1: stage raw words of x and find the tile's largest exponent
-    uint32_t mx = 0;
-#pragma unroll
-    for (int sg = 0; sg < kMaxSegments; ++sg) {
-        if (sg >= sp.nseg) break;
-        const int64_t g0 = r0 + sp.seg_min[sg];
-        const int len = sp.rows + sp.seg_span[sg];
-        int2* dst = sx + sp.seg_base[sg];
-        for (int e = tid; e < len; e += kStageThreads) {
-            const int64_t idx = g0 + e;
-            uint2 b = make_uint2(0u, 0u);
-            if (uint64_t(idx) < uint64_t(a.n)) b = __ldg(xw + idx);
-            dst[e] = make_int2(int(b.x), int(b.y));
-            mx = max(mx, b.y & 0x7FFFFFFFu);
-        }
-    }
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
-    __syncthreads();
-    mx = 0;
-#pragma unroll
-    for (int w = 0; w < kStageThreads / 32; ++w) mx = max(mx, s_red[w]);
-    const uint32_t emax = mx >> 20;
-    const bool exact_path = emax < 64u || emax >= 2047u;
-    // phase 2: convert in place
-    if (!exact_path) {
-        for (int e = tid; e < sp.elems; e += kStageThreads) {
-            const int2 b = sx[e];
-            sx[e] = fixed_limbs(uint32_t(b.x), uint32_t(b.y), emax);
-        }
-    }
-    __syncthreads();
-    // phase 3: rows
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
-        const int rl = tid + i * kStageThreads;
+        const int rl = tid + i * THREADS;
         const int64_t r = r0 + rl;
         if (r >= a.n) break;
-        uint32_t w[kMaxRecordWords];
-        load_record<WORDS>(a, r, w);
+        uint32_t wn[kMaxRecordWords];
+        if (i + 1 < RPT && r + THREADS < a.n) load_record<WORDS>(a, r + THREADS, wn);
         if (exact_path) {
             // zeros/denormals only, or non-finite values: the COLUMN order
             const uint32_t mask = smask[byte_of(w, NU) & 31];
@@ -476,19 +443,21 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_staged_kernel(P
 #pragma unroll
             for (int u = 0; u < NU; ++u)
                 if ((mask >> u) & 1u) {
-                    const int2 b = sx[rl + sp.soff[u]];
+                    const int2 b = sx[rl + (VEC ? sp.soff_padded[u] : sp.soff[u])];
                     acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
                 }
             y[r] = acc;
+            if (i + 1 < RPT) {
+#pragma unroll
+                for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
+            }
             continue;
         }
-        // int8 multipliers of four codes at a time: nibble-pack the codes,
-        // then one table permute
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
         if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
 #pragma unroll
             for (int k = 0; k < NU / RUN; ++k) {
-                const int2* p = sx + rl + sp.soff[k * RUN];
+                const int2* p = sx + rl + (VEC ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) {
                     const int u = k * RUN + j;
@@ -503,7 +472,7 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_staged_kernel(P
             for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
 #pragma unroll
             for (int k = 0; k < NU / RUN; ++k) {
-                const int2* p = sx + rl + sp.soff[k * RUN];
+                const int2* p = sx + rl + (VEC ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) {
                     const int u = k * RUN + j;
@@ -516,11 +485,168 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_staged_kernel(P
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
         y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
+        if (i + 1 < RPT) {
+#pragma unroll
+            for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
+        }
     }
 }
 
+template <int WORDS, int NU, int RPT, int RUN, int THREADS, bool VEC>
+__global__ void __launch_bounds__(THREADS, 1536 / THREADS) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
+                                                                                    const double* __restrict__ x,
+                                                                                    double* __restrict__ y) {
+    extern __shared__ int4 sx4[];
+    int2* const sx = reinterpret_cast<int2*>(sx4);
+    __shared__ uint32_t s_red[THREADS / 32];
+    __shared__ uint32_t smask[32];
+    const int tid = threadIdx.x;
+    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
+    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
+    uint32_t w0[kMaxRecordWords];                  // first row's record, in flight during staging
+    if (r0 + tid < a.n) load_record<WORDS>(a, r0 + tid, w0);
+    // phase 1: stage raw words of x and find the tile's largest exponent
+    uint32_t mx = 0;
+#pragma unroll
+    for (int sg = 0; sg < kMaxSegments; ++sg) {
+        if (sg >= sp.nseg) break;
+        if constexpr (VEC) {
+            // 16-byte loads on the padded layout (x 16-byte aligned, window
+            // starts rounded down to an even element)
+            const int64_t g0 = r0 + sp.seg_min[sg] - sp.seg_pad[sg];
+            const int len2 = (sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2;
+            const uint4* __restrict__ src = reinterpret_cast<const uint4*>(x + g0);
+            int4* dst = sx4 + sp.seg_pbase[sg] / 2;
+            const int64_t lo = -g0, hi = a.n - g0;   // valid element range, relative
+            for (int e = tid; e < len2; e += THREADS) {
+                uint4 b;
+                if (2 * e >= lo && 2 * e + 1 < hi) {
+                    b = __ldg(src + e);
+                } else {
+                    b = make_uint4(0u, 0u, 0u, 0u);
+                    if (2 * e >= lo && 2 * e < hi) { const uint2 h = __ldg(reinterpret_cast<const uint2*>(x + g0 + 2 * e)); b.x = h.x; b.y = h.y; }
+                    if (2 * e + 1 >= lo && 2 * e + 1 < hi) { const uint2 h = __ldg(reinterpret_cast<const uint2*>(x + g0 + 2 * e + 1)); b.z = h.x; b.w = h.y; }
+                }
+                dst[e] = make_int4(int(b.x), int(b.y), int(b.z), int(b.w));
+                mx = max(mx, max(b.y & 0x7FFFFFFFu, b.w & 0x7FFFFFFFu));
+            }
+        } else {
+            const uint2* __restrict__ xw = reinterpret_cast<const uint2*>(x);
+            const int64_t g0 = r0 + sp.seg_min[sg];
+            const int len = sp.rows + sp.seg_span[sg];
+            int2* dst = sx + sp.seg_base[sg];
+            for (int e = tid; e < len; e += THREADS) {
+                const int64_t idx = g0 + e;
+                uint2 b = make_uint2(0u, 0u);
+                if (uint64_t(idx) < uint64_t(a.n)) b = __ldg(xw + idx);
+                dst[e] = make_int2(int(b.x), int(b.y));
+                mx = max(mx, b.y & 0x7FFFFFFFu);
+            }
+        }
+    }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) mx = max(mx, s_red[w]);
+    const uint32_t emax = mx >> 20;
+    const bool exact_path = emax < 64u || emax >= 2047u;
+    const int nel = VEC ? sp.elems_padded : sp.elems;
+    // phase 2: convert in place, two elements per 16-byte access
+    if (!exact_path) {
+        for (int e = tid; e < (nel + 1) / 2; e += THREADS) {
+            const int4 b = sx4[e];
+            const int2 l0 = fixed_limbs(uint32_t(b.x), uint32_t(b.y), emax);
+            const int2 l1 = fixed_limbs(uint32_t(b.z), uint32_t(b.w), emax);
+            sx4[e] = make_int4(l0.x, l0.y, l1.x, l1.y);
+        }
+    }
+    __syncthreads();
+    // phase 3: rows
+    staged_rows<WORDS, NU, RPT, RUN, THREADS, VEC>(a, sp, sx, smask, r0, emax, exact_path, y, w0);
+}
 
-
+// ------------------------- FAST order, register-staged tiles (27 slots) ---
+// For the full 27-point union, whose tile windows form three merged segments
+// (planes z-1, z, z+1), every thread loads its QS 16-byte pairs of each
+// window into registers at once -- all 3*QS loads in flight together -- the
+// block reduces the tile's largest exponent, and each thread converts its
+// own pairs to limbs and writes them to shared memory once.  Rows then sum
+// from shared memory as in the staged kernel.  x must be 16-byte aligned;
+// the plan must have three segments of at most 2*QS*THREADS elements each.
+template <int QS, int RPT, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(PatternView a, StagePlan sp,
+                                                                             const double* __restrict__ x,
+                                                                             double* __restrict__ y) {
+    extern __shared__ int4 sx4[];
+    __shared__ uint32_t s_red[THREADS / 32];
+    __shared__ uint32_t smask[32];
+    const int tid = threadIdx.x;
+    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
+    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
+    const uint4* __restrict__ x4 = reinterpret_cast<const uint4*>(x);
+    const uint2* __restrict__ x2 = reinterpret_cast<const uint2*>(x);
+    uint32_t w0[kMaxRecordWords];                  // first row's record, in flight during staging
+    if (r0 + tid < a.n) load_record<7>(a, r0 + tid, w0);
+    // phase 1: every pair of the three windows this thread owns, in flight together
+    uint4 b[3][QS];
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg) {
+        const int64_t g0 = r0 + sp.seg_min[sg] - sp.seg_pad[sg];   // even
+        const int len2 = (sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2;
+#pragma unroll
+        for (int j = 0; j < QS; ++j) {
+            const int q = tid + j * THREADS;
+            const int64_t g = g0 + 2 * q;                               // first element of the pair
+            b[sg][j] = make_uint4(0u, 0u, 0u, 0u);
+            if (q < len2) {
+                if (uint64_t(g) < uint64_t(a.n - 1)) {                  // 0 <= g and g + 1 < n
+                    b[sg][j] = __ldg(x4 + (g >> 1));
+                } else if (g == a.n - 1) {                              // odd n: the last element alone
+                    const uint2 h = __ldg(x2 + g);
+                    b[sg][j].x = h.x;
+                    b[sg][j].y = h.y;
+                }
+            }
+        }
+    }
+    uint32_t mx = 0;
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg)
+#pragma unroll
+        for (int j = 0; j < QS; ++j) mx = max(mx, max(b[sg][j].y & 0x7FFFFFFFu, b[sg][j].w & 0x7FFFFFFFu));
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) mx = max(mx, s_red[w]);
+    const uint32_t emax = mx >> 20;
+    const bool exact_path = emax < 64u || emax >= 2047u;
+    // phase 2: convert the pairs in registers, one shared-memory write each
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg) {
+        const int len2 = (sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2;
+        int4* dst = sx4 + sp.seg_pbase[sg] / 2;
+#pragma unroll
+        for (int j = 0; j < QS; ++j) {
+            const int q = tid + j * THREADS;
+            if (q >= len2) continue;
+            const uint4 v = b[sg][j];
+            if (exact_path) {
+                dst[q] = make_int4(int(v.x), int(v.y), int(v.z), int(v.w));
+            } else {
+                const int2 l0 = fixed_limbs(v.x, v.y, emax);
+                const int2 l1 = fixed_limbs(v.z, v.w, emax);
+                dst[q] = make_int4(l0.x, l0.y, l1.x, l1.y);
+            }
+        }
+    }
+    __syncthreads();
+    staged_rows<7, 27, RPT, 3, THREADS, true>(a, sp, reinterpret_cast<const int2*>(sx4), smask, r0, emax,
+                                              exact_path, y, w0);
+}
 
 // ------------------- FAST order, staged tiles of the pre-converted copy ---
 // As the staged kernel, but the tile's windows are copied from the
@@ -1291,31 +1417,41 @@ cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, doubl
 cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                        cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
+    // 16-byte staging needs x itself 16-byte aligned
+    const bool vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+    const int threads = sp.rows / sp.rows_per_thread;
     const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
-    const size_t smem = size_t(sp.elems) * sizeof(int2);
+    const size_t smem = size_t((std::max(sp.elems, sp.elems_padded) + 1) / 2 * 2) * sizeof(int2);
     auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      int(cudaSharedmemCarveoutMaxShared));
         if (e != cudaSuccess) return e;
-        kernel<<<grid, kStageThreads, smem, s>>>(a, sp, x, y);
+        kernel<<<grid, threads, smem, s>>>(a, sp, x, y);
         return cudaGetLastError();
     };
-    // union sizes of the 3-D 27-, 19- and 7-point stencils and the 2-D 9- and
-    // 5-point ones are compiled with a fixed slot count
-#define SPMVC_NU_CASE(NUV)                                                             \
-    case NUV:                                                                          \
-        if (sp.rows_per_thread == 1) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 1, 1>); \
-        if (sp.rows_per_thread == 2) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 2, 1>); \
-        if (sp.rows_per_thread == 4) return go(pattern_fast_staged_kernel<(NUV + 4) / 4, NUV, 4, 1>); \
-        return cudaErrorInvalidValue;
+#define SPMVC_STAGED(W, NUV, RUN, RPT, T)                                                       \
+    if (sp.rows_per_thread == RPT && threads == T)                                              \
+        return vec ? go(pattern_fast_staged_kernel<W, NUV, RPT, RUN, T, true>)                  \
+                   : go(pattern_fast_staged_kernel<W, NUV, RPT, RUN, T, false>);
     if (a.run_len == 3 && a.nu == 27) {
-        if (sp.rows_per_thread == 1) return go(pattern_fast_staged_kernel<7, 27, 1, 3>);
-        if (sp.rows_per_thread == 2) return go(pattern_fast_staged_kernel<7, 27, 2, 3>);
-        if (sp.rows_per_thread == 4) return go(pattern_fast_staged_kernel<7, 27, 4, 3>);
+        SPMVC_STAGED(7, 27, 3, 1, 512)
+        SPMVC_STAGED(7, 27, 3, 2, 512)
+        SPMVC_STAGED(7, 27, 3, 4, 512)
+        SPMVC_STAGED(7, 27, 3, 2, 256)
+        SPMVC_STAGED(7, 27, 3, 4, 256)
+        SPMVC_STAGED(7, 27, 3, 8, 256)
         return cudaErrorInvalidValue;
     }
+    // union sizes of the 3-D 27-, 19- and 7-point stencils and the 2-D 9- and
+    // 5-point ones are compiled with a fixed slot count, 512 threads
+#define SPMVC_NU_CASE(NUV)                                                                      \
+    case NUV:                                                                                   \
+        SPMVC_STAGED((NUV + 4) / 4, NUV, 1, 1, 512)                                             \
+        SPMVC_STAGED((NUV + 4) / 4, NUV, 1, 2, 512)                                             \
+        SPMVC_STAGED((NUV + 4) / 4, NUV, 1, 4, 512)                                             \
+        return cudaErrorInvalidValue;
     switch (a.nu) {
         SPMVC_NU_CASE(27)
         SPMVC_NU_CASE(19)
@@ -1325,6 +1461,7 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
         default: return cudaErrorNotSupported;
     }
 #undef SPMVC_NU_CASE
+#undef SPMVC_STAGED
 }
 
 cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
@@ -1417,6 +1554,43 @@ cudaError_t launch_pattern_fast_async_x(const PatternView& a, const StagePlan& s
     const unsigned grid = unsigned(std::min<int64_t>(ntiles, num_sms));
     kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, X, y, ntiles, partial);
     return cudaGetLastError();
+}
+
+// Register-staged shapes: (threads, rows per thread, pairs per window per thread)
+bool rstage_supported(const StagePlan& sp) {
+    const int threads = sp.rows / sp.rows_per_thread;
+    int qs = 0;
+    if (threads == 256 && sp.rows_per_thread == 4) qs = 3;
+    else if (threads == 256 && sp.rows_per_thread == 2) qs = 2;
+    else if (threads == 512 && sp.rows_per_thread == 2) qs = 2;
+    if (qs == 0 || sp.nseg != 3) return false;
+    for (int sg = 0; sg < 3; ++sg)
+        if ((sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2 > qs * threads) return false;
+    return true;
+}
+
+cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                        cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (!(a.run_len == 3 && a.nu == 27 && a.words == 7) || !rstage_supported(sp)) return cudaErrorNotSupported;
+    // the 16-byte loads need x itself 16-byte aligned: otherwise the staged
+    // kernel on the same plan
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return launch_pattern_fast_staged(a, sp, x, y, s);
+    const int threads = sp.rows / sp.rows_per_thread;
+    const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
+    const size_t smem = size_t(sp.elems_padded) * sizeof(int2);
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     int(cudaSharedmemCarveoutMaxShared));
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, threads, smem, s>>>(a, sp, x, y);
+        return cudaGetLastError();
+    };
+    if (threads == 256 && sp.rows_per_thread == 4) return go(pattern_fast_rstaged_kernel<3, 4, 256, 4>);
+    if (threads == 256 && sp.rows_per_thread == 2) return go(pattern_fast_rstaged_kernel<2, 2, 256, 5>);
+    return go(pattern_fast_rstaged_kernel<2, 2, 512, 2>);
 }
 
 bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }

@@ -157,6 +157,7 @@ struct StagePlan {
 bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
                      StagePlan* out);
 bool stage_supported(int nu);  // union sizes with a compiled staged kernel
+bool rstage_supported(const StagePlan& sp);  // plans the register-staged kernel takes
 
 // Kernel launchers (k_spmv.cu).
 cudaError_t launch_ell_f64(const EllView& a, const double* x, double* y, cudaStream_t s);
@@ -167,6 +168,8 @@ cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, doubl
                                     uint32_t* xmax_word, cudaStream_t s);
 cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                        cudaStream_t s);
+cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
+                                        cudaStream_t s);
 cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                         uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp, const double* x, double* y,

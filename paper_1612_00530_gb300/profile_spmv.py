@@ -1,7 +1,7 @@
 """Runs SpMV steps on one HPCG matrix for profiling (ncu launch lists and
 kernel captures): python -m paper_1612_00530_gb300.profile_spmv
 [--grid N] [--format ell|pattern|delta] [--order column|fast] [--steps K]
-[--warmup W].  Prints the mean step time measured with CUDA events."""
+[--warmup W] [--variant V --tile T --threads B].  Prints the mean step time measured with CUDA events."""
 from __future__ import annotations
 
 import argparse
@@ -20,8 +20,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--kind", default="hpcg", choices=("hpcg", "irregular"))
-    ap.add_argument("--variant", type=int, default=-1, help="FAST kernel: 0 direct, 1 staged, 2 pre-converted")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="FAST kernel: 0 direct, 1 staged, 2 pre-converted, 3 staged pre-converted, "
+                         "4/5 persistent, 6 register-staged")
     ap.add_argument("--tile", type=int, default=2048)
+    ap.add_argument("--threads", type=int, default=512, help="block size of the staged kernels (512 or 256)")
     ap.add_argument("--cg", choices=("fp64", "ir_fp32"), default=None,
                     help="run one CG solve (b = A 1) instead of SpMV steps")
     ap.add_argument("--cg-iters", type=int, default=40)
@@ -33,7 +36,7 @@ def main():
     x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=1)).cuda()
     y = torch.empty_like(x)
     if args.variant >= 0:
-        P.spmv_set_variant(M, args.variant, args.tile)
+        P.spmv_set_tile(M, args.variant, args.tile, args.threads)
     if args.cg:
         ones = torch.ones_like(x)
         P.spmv_apply(M, ones, y)

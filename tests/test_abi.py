@@ -63,3 +63,30 @@ def test_fast_order_refused_for_unsuitable_tables():
     with pytest.raises(P.SpmvError) as e:
         P.spmv_set_order(C, "fast")
     assert e.value.status == P.SPMV_EUNSUPPORTED
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the C compiler's size and field
+    offsets (host-only: compiles a tiny C program against include/spmvc.h)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [P.spmv_gen_desc, P.spmv_opts, P.spmv_info_t, P.spmv_cg_opts, P.spmv_cg_result]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "spmvc.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'    printf("{s.__name__} size %zu\\n", sizeof({s.__name__}));')
+        for name, _ in s._fields_:
+            lines.append(f'    printf("{s.__name__} {name} %zu\\n", offsetof({s.__name__}, {name}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for s in structs:
+        assert got[(s.__name__, "size")] == ctypes.sizeof(s), s.__name__
+        for name, _ in s._fields_:
+            assert got[(s.__name__, name)] == getattr(s, name).offset, (s.__name__, name)

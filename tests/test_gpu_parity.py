@@ -322,7 +322,9 @@ def test_fast_order_every_variant():
 
 
 def test_fast_variants_on_hpcg_grids():
-    for g in [(17, 17, 17), (33, 9, 5), (64, 48, 40)]:
+    # (25, 25, 5): odd n with three separate plane windows per 512-row tile,
+    # so the register-staged kernel meets a lone last element
+    for g in [(17, 17, 17), (33, 9, 5), (25, 25, 5), (64, 48, 40)]:
         rowptr, col, val = oracle.hpcg_csr(*g)
         n = len(rowptr) - 1
         x = spmv_inputs.uniform_vector(n, seed=1)
@@ -335,14 +337,35 @@ def test_fast_variants_on_hpcg_grids():
         xbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
         xbuf[1:] = torch.from_numpy(x).cuda()
         xoff = xbuf[1:]
-        for v, t in [(0, 0), (1, 512), (1, 1024), (1, 2048), (2, 0), (3, 512), (3, 1024), (3, 2048), (4, 0), (5, 0)]:
-            P.spmv_set_variant(C, v, t)
+        shapes = [(0, 0, 512), (1, 512, 512), (1, 1024, 512), (1, 2048, 512), (1, 512, 256), (1, 1024, 256),
+                  (1, 2048, 256), (2, 0, 512), (3, 512, 512), (3, 1024, 512), (3, 2048, 512), (4, 0, 512), (5, 0, 512)]
+        # register-staged tiles: three plane windows, each within the pairs the threads hold
+        rstaged = {(25, 25, 5): [(6, 512, 256)], (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512)]}
+        for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512)]:
+            if (v, t, bt) not in rstaged.get(g, []):
+                with pytest.raises(P.SpmvError):
+                    P.spmv_set_tile(C, v, t, bt)
+        for v, t, bt in shapes + rstaged.get(g, []):
+            P.spmv_set_tile(C, v, t, bt)
             check_fast(run(C, x), y_ref, scale)
             assert np.array_equal(run(C, xi), yi_ref)
             y = torch.empty(n, dtype=torch.float64, device="cuda")
             P.spmv_apply(C, xoff, y)
             torch.cuda.synchronize()
             check_fast(y.cpu().numpy(), y_ref, scale)
+
+
+def test_set_tile_rejects_shapes_without_kernel():
+    C = P.spmv_compress(P.spmv_build("hpcg", 16, 16, 16), format="pattern", order="fast")
+    for v, t, bt in [(1, 1024, 128), (3, 1024, 256), (1, 768, 256), (1, 4096, 256), (1, 256, 256)]:
+        with pytest.raises(P.SpmvError):
+            P.spmv_set_tile(C, v, t, bt)
+    # a union that is not the full 27-point one has 512-thread tiles only
+    rowptr, col, val = spread_offsets_csr(30000, [-600, -1, 0, 1, 600], [-1.0, -2.0, 8.0, -2.0, -1.0])
+    D = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+    P.spmv_set_tile(D, 1, 1024, 512)
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_tile(D, 1, 1024, 256)
 
 
 def test_autotune_keeps_results():
@@ -356,7 +379,7 @@ def test_autotune_keeps_results():
     rows = P.spmv_autotune(C, x, y, reps=3)
     assert rows in (1, 4, 5, 512, 1024, 2048)
     info = P.spmv_info(C)
-    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3))
+    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6))
     if rows not in (1, 4, 5):
         assert info["fast_tile_rows"] == rows
     y_ref = oracle.spmv(rowptr, col, val, x_np)
@@ -391,21 +414,25 @@ def fast_order_exact_model(rowptr, col, mult, mult_exp, x):
 def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale):
     """Bit-exact model check of every FAST kernel, including results in the
     subnormal range (rounded by the integer routine)."""
-    g = (9, 7, 6)
-    rowptr, col, val = oracle.hpcg_csr(*g)
-    n = len(rowptr) - 1
-    val = val * vscale
-    mult = np.where(val > 0, 26, -1).astype(np.int64)
-    mult_exp = int(np.round(np.log2(vscale)))
-    x = spmv_inputs.uniform_vector(n, seed=12) * xscale
-    want = fast_order_exact_model(rowptr, col, mult, mult_exp, x)
-    C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
-    for v, t in [(0, 0), (1, 512), (1, 2048), (2, 0), (3, 1024), (3, 2048), (4, 0), (5, 0)]:
-        P.spmv_set_variant(C, v, t)
-        got = run(C, x)
-        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (v, t)
-    if vscale < 1e-20:
-        assert np.any((want != 0) & (np.abs(want) < 2.2250738585072014e-308))  # subnormal results occur
+    cases = [((9, 7, 6), [(0, 0, 512), (1, 512, 512), (1, 2048, 512), (1, 1024, 256), (1, 2048, 256),
+                          (2, 0, 512), (3, 1024, 512), (3, 2048, 512), (4, 0, 512), (5, 0, 512)]),
+             # three separate plane windows per 512-row tile: the register-staged kernel
+             ((24, 24, 4), [(6, 512, 256), (1, 512, 256), (2, 0, 512)])]
+    for g, shapes in cases:
+        rowptr, col, val = oracle.hpcg_csr(*g)
+        n = len(rowptr) - 1
+        val = val * vscale
+        mult = np.where(val > 0, 26, -1).astype(np.int64)
+        mult_exp = int(np.round(np.log2(vscale)))
+        x = spmv_inputs.uniform_vector(n, seed=12) * xscale
+        want = fast_order_exact_model(rowptr, col, mult, mult_exp, x)
+        C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+        for v, t, bt in shapes:
+            P.spmv_set_tile(C, v, t, bt)
+            got = run(C, x)
+            assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (g, v, t, bt)
+        if vscale < 1e-20:
+            assert np.any((want != 0) & (np.abs(want) < 2.2250738585072014e-308))  # subnormal results occur
 
 
 @pytest.mark.parametrize("k", [1, 3, 8, 32])
@@ -441,15 +468,15 @@ def test_fast_spmm_preconverted_block(k):
 
 
 def test_fast_variant_persistent_many_tiles():
-    """The persistent double-buffered kernel walking several tiles per CTA
-    (96^3 rows = 864 tiles), on sampled rows and on A*1, plus the exact
-    fallback for non-finite x."""
+    """The persistent double-buffered kernels walking several tiles per CTA
+    (96^3 rows = 864 tiles) and the register-staged kernel, on sampled rows
+    and on A*1, plus the per-tile exact fallback for non-finite x."""
     g = (96, 96, 96)
     n = 96 ** 3
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x = spmv_inputs.uniform_vector(n, seed=13)
-    for variant in (5, 4):
-        P.spmv_set_variant(C, variant, 0)
+    for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512)]:
+        P.spmv_set_tile(C, variant, t, bt)
         check_persistent(C, g, n, x)
 
 
