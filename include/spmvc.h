@@ -151,7 +151,8 @@ typedef struct {
                                    2 pre-converted fixed-point copy of x, 3 staged
                                    tiles of that copy, 4 persistent double-buffered
                                    tiles, 5 the same from the copy, 6 register-
-                                   staged tiles; -1 before A's first device call */
+                                   staged tiles, 7 z-marching tiles; -1 before
+                                   A's first device call */
     int32_t fast_block_threads; /* FAST order: threads per block of the staged
                                    kernel (512 or 256; 0 = no staged kernel) */
     int32_t reserved0;
@@ -205,12 +206,12 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
 /* Autotuner: times the kernel configurations available to A (FAST order:
  * the pre-converted-x kernels, the persistent kernels, the shared-memory
  * staged kernel with tiles of 512, 1024 and 2048 rows of 512 or 256
- * threads, and the register-staged kernel) on the caller's device vectors
+ * threads, the register-staged and the z-marching kernels) on the caller's device vectors
  * x and y (n doubles each; y is overwritten), keeps the fastest for later
  * calls on A, and remembers it for matrices with the same signature (device
  * name, n, nnz, union size) uploaded later in this process.  reps: timed
  * launches per candidate (default 10 when <= 0).  *choice (may be NULL)
- * receives the chosen tile rows for a staged kernel (variants 1, 3, 6), 1
+ * receives the chosen tile rows for a staged kernel (variants 1, 3, 6, 7), 1
  * for the pre-converted kernel, 4 or 5 for the persistent kernels, 0 when
  * A has nothing to tune.  Synchronous, uses the legacy default stream: call
  * it outside any stream capture. */
@@ -221,15 +222,18 @@ int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_
  * pre-converted copy of x, 3 staged tiles of that copy, 4 persistent
  * double-buffered tiles, 5 the same fed from the copy, 6 register-staged
  * tiles (full 27-point union; tile_rows 1024 with spmv_set_tile's 512 or
- * 256 threads, or 512 with 256 threads); tile_rows is ignored for 0, 2, 4,
- * 5.  SPMV_EUNSUPPORTED when A has no such kernel.
+ * 256 threads, or 512 with 256 threads), 7 z-marching tiles (full 27-point
+ * union whose plane stride is a multiple of tile_rows; same shapes as 6);
+ * tile_rows is ignored for 0, 2, 4, 5.  SPMV_EUNSUPPORTED when A has no
+ * such kernel.
  * Copies A to the device if it is not there yet. */
 int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 
 /* As spmv_set_variant with 512-thread blocks, but also sets the block size
  * of the staged kernels: block_threads 512 (tile_rows 512, 1024 or 2048) or,
- * for variants 1 and 6 on the full 27-slot union of a 3-D 27-point stencil,
- * 256 (tile_rows 512, 1024 or 2048: two, four or eight rows per thread).
+ * for variants 1, 6 and 7 on the full 27-slot union of a 3-D 27-point
+ * stencil, 256 (tile_rows 512, 1024 or 2048: two, four or eight rows per
+ * thread).
  * Ignored for variants 0, 2, 4, 5.  SPMV_EINVAL for other block sizes,
  * SPMV_EUNSUPPORTED for shapes A has no kernel for. */
 int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads);

@@ -212,6 +212,17 @@ int ensure_device(spmv_mat_s* m) {
                 }
             }
         }
+        v.dom_uni = 0;
+        if (v.dom_ok && p.fast_ok && v.nu == 27 && p.uoff[13] == 0) {
+            bool uni = true;
+            for (int u = 0; u < 27; ++u)
+                if (u != 13 && v.dom_m[u] != v.dom_m[0]) uni = false;
+            if (uni) {
+                v.dom_uni = 1;
+                v.dom_mo = v.dom_m[0];
+                v.dom_mc = v.dom_m[13];
+            }
+        }
         // runs of consecutive displacements, all of one length
         v.run_len = 0;
         for (int len : {3}) {
@@ -258,6 +269,17 @@ int ensure_device(spmv_mat_s* m) {
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
             m->num_sms = sms > 0 ? sms : 152;
         }
+        m->zplan_ok = false;
+        if (p.fast_ok && v.run_len == 3 && v.nu == 27 && v.words == 7) {
+            const std::pair<int, int> zs = tuned_stage_shape(m, 256, 2);
+            for (std::pair<int, int> sh : {zs, std::make_pair(256, 2)})
+                if (make_zplan(p.uoff, m->n, sh.second, sh.first, m->num_sms, &m->zplan) &&
+                    zmarch_supported(m->zplan)) {
+                    m->zplan_ok = true;
+                    break;
+                }
+        }
+        if (m->fast_variant == 7 && !m->zplan_ok) m->fast_variant = 1;
         if ((m->fast_variant == 4 || m->fast_variant == 5) && !m->async_ok) m->fast_variant = 2;
         if (m->fast_variant == 6 && !(m->stage_ok && rstage_supported(m->stage))) m->fast_variant = 1;
         if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
@@ -425,9 +447,10 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->union_size = static_cast<int32_t>(A->pat.uoff.size());
         out->record_bytes = 4 * A->pat.words;
         out->fast_eligible = A->pat.fast_ok ? 1 : 0;
-        out->fast_tile_rows = A->stage_ok ? A->stage.rows : 0;
+        out->fast_tile_rows = A->fast_variant == 7 && A->zplan_ok ? A->zplan.rows : A->stage_ok ? A->stage.rows : 0;
         out->fast_variant = A->device >= 0 ? A->fast_variant : -1;
-        out->fast_block_threads = A->stage_ok ? A->stage.rows / A->stage.rows_per_thread : 0;
+        out->fast_block_threads = A->fast_variant == 7 && A->zplan_ok ? A->zplan.threads
+                                  : A->stage_ok ? A->stage.rows / A->stage.rows_per_thread : 0;
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
@@ -514,6 +537,7 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
                                                                  A->d_xfixed, A->xfixed_guard, s)
             : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                            A->xfixed_guard, s)
+            : A->fast_variant == 7 ? launch_pattern_fast_zmarch(A->pat_view, A->zplan, x, y, A->d_scratch_words, s)
             : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, s)
             : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
                                    : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
@@ -603,18 +627,18 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     if (st) return st;
     if (choice) *choice = 0;
     if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || A->n == 0) return SPMV_OK;
-    struct Cand { int variant; StagePlan plan; };
+    struct Cand { int variant; StagePlan plan; ZPlan zplan; };
     std::vector<Cand> cands;
-    if (A->d_xfixed) cands.push_back(Cand{2, A->stage});
-    if (A->async_ok) cands.push_back(Cand{4, A->async_plan});
-    if (A->async_ok && A->d_xfixed) cands.push_back(Cand{5, A->async_plan});
+    if (A->d_xfixed) cands.push_back(Cand{2, A->stage, {}});
+    if (A->async_ok) cands.push_back(Cand{4, A->async_plan, {}});
+    if (A->async_ok && A->d_xfixed) cands.push_back(Cand{5, A->async_plan, {}});
     if (A->stage_ok) {
         const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
         for (int rpt : {1, 2, 4}) {
             StagePlan plan;
             if (make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) {
-                cands.push_back(Cand{1, plan});
-                if (A->d_xfixed && full27) cands.push_back(Cand{3, plan});
+                cands.push_back(Cand{1, plan, {}});
+                if (A->d_xfixed && full27) cands.push_back(Cand{3, plan, {}});
             }
         }
         // 256-thread tiles (six resident CTAs per SM) and the register-staged
@@ -622,12 +646,18 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         if (full27) {
             for (int rpt : {2, 4, 8}) {
                 StagePlan plan;
-                if (make_stage_plan(A->pat.uoff, rpt, 256, 12288, &plan)) cands.push_back(Cand{1, plan});
+                if (make_stage_plan(A->pat.uoff, rpt, 256, 12288, &plan)) cands.push_back(Cand{1, plan, {}});
             }
             for (std::pair<int, int> sh : {std::make_pair(256, 4), std::make_pair(256, 2), std::make_pair(512, 2)}) {
                 StagePlan plan;
                 if (make_stage_plan(A->pat.uoff, sh.second, sh.first, 12288, &plan) && rstage_supported(plan))
-                    cands.push_back(Cand{6, plan});
+                    cands.push_back(Cand{6, plan, {}});
+            }
+            for (std::pair<int, int> sh : {std::make_pair(256, 2), std::make_pair(256, 4), std::make_pair(512, 2)}) {
+                ZPlan zp;
+                if (A->pat_view.words == 7 && make_zplan(A->pat.uoff, A->n, sh.second, sh.first, A->num_sms, &zp) &&
+                    zmarch_supported(zp))
+                    cands.push_back(Cand{7, {}, zp});
             }
         }
     }
@@ -641,6 +671,8 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         auto launch = [&]() {
             if (c.variant == 4) return launch_pattern_fast_async(A->pat_view, c.plan, x, y, A->num_sms, nullptr);
             if (c.variant == 6) return launch_pattern_fast_rstaged(A->pat_view, c.plan, x, y, nullptr);
+            if (c.variant == 7)
+                return launch_pattern_fast_zmarch(A->pat_view, c.zplan, x, y, A->d_scratch_words, nullptr);
             if (c.variant == 5)
                 return launch_pattern_fast_async_x(A->pat_view, c.plan, x, y, A->d_scratch_words, A->d_xfixed,
                                                    A->xfixed_guard, A->num_sms, nullptr);
@@ -666,13 +698,20 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     const bool staged_pick = pick.variant == 1 || pick.variant == 3 || pick.variant == 6;
     if (staged_pick) A->stage = pick.plan;
     if (pick.variant == 4 || pick.variant == 5) A->async_plan = pick.plan;
+    if (pick.variant == 7) {
+        A->zplan = pick.zplan;
+        A->zplan_ok = true;
+    }
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_variant[tune_key(A)] = pick.variant;
-        if (staged_pick)
+        if (pick.variant == 7)
+            g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.rows_per_thread;
+        else if (staged_pick)
             g_tune[tune_key(A)] = (pick.plan.rows / pick.plan.rows_per_thread) * 16 + pick.plan.rows_per_thread;
     }
-    if (choice) *choice = staged_pick ? pick.plan.rows : (pick.variant >= 4 ? pick.variant : 1);
+    if (choice) *choice = staged_pick ? pick.plan.rows : pick.variant == 7 ? pick.zplan.rows
+                        : (pick.variant >= 4 ? pick.variant : 1);
     return SPMV_OK;
 }
 
@@ -693,7 +732,20 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
         A->fast_variant = variant;
         return SPMV_OK;
     }
-    if (variant != 1 && variant != 3 && variant != 6) return fail(SPMV_EINVAL, "variant must be 0..6");
+    if (variant == 7) {
+        ZPlan zp;
+        const int rpt = block_threads > 0 ? tile_rows / block_threads : 0;
+        if (block_threads != 256 && block_threads != 512) return fail(SPMV_EINVAL, "block_threads must be 256 or 512");
+        if (A->pat_view.words != 7 || tile_rows <= 0 || tile_rows % block_threads != 0 ||
+            !make_zplan(A->pat.uoff, A->n, rpt, block_threads, A->num_sms, &zp) || !zmarch_supported(zp))
+            return fail(SPMV_EUNSUPPORTED, "no z-marching kernel for this union and tile (tile_rows/threads "
+                                           "512/256, 1024/256 or 1024/512, plane stride a multiple of tile_rows)");
+        A->zplan = zp;
+        A->zplan_ok = true;
+        A->fast_variant = 7;
+        return SPMV_OK;
+    }
+    if (variant != 1 && variant != 3 && variant != 6) return fail(SPMV_EINVAL, "variant must be 0..7");
     const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
     if (variant == 3 && !(A->d_xfixed && full27))
         return fail(SPMV_EUNSUPPORTED, "no staged pre-converted kernel for this union");

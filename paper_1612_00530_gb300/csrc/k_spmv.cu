@@ -232,9 +232,9 @@ __device__ __noinline__ double fixed_to_double_int(int64_t acc, int S) {
 __device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
     const double d = __ll2double_rn(acc);
     const int32_t hi = __double2hiint(d);
-    const int e = ((hi >> 20) & 0x7FF) + S;
-    if (acc != 0 && (e < 1 || e > 2046)) return fixed_to_double_int(acc, S);
-    return acc == 0 ? 0.0 : __hiloint2double(hi + (S << 20), __double2loint(d));
+    const int ef = (hi >> 20) & 0x7FF;          // 0 exactly when acc == 0
+    if (ef != 0 && uint32_t(ef + S - 1) < 2046u) return __hiloint2double(hi + (S << 20), __double2loint(d));
+    return ef == 0 ? d : fixed_to_double_int(acc, S);
 }
 
 template <int WORDS>
@@ -418,16 +418,17 @@ __device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t e
     return make_int2(int32_t(uint32_t(X) & 0x3FFFFFFu) * s1, int32_t(uint32_t(X >> 26)) * s1);
 }
 
-// Phase 3 of the staged kernels: every thread sums RPT rows (r0 + tid +
+// Row phase of the staged kernels: every thread sums RPT rows (r0 + tid +
 // i*THREADS) slot by slot from the tile's converted windows in shared memory
-// (raw words on the exact path) and rounds once.  w holds the record of the
+// (raw words on the exact path) and rounds once.  off(u): shared-memory
+// index of slot u's element for the tile's first row.  w holds the record of the
 // thread's first row (loaded by the caller before the tile's barriers, when
 // that row exists); each row's loop issues the next row's record loads
 // before it sums, so record latency overlaps the previous row's work.
-template <int WORDS, int NU, int RPT, int RUN, int THREADS, bool VEC>
-__device__ __forceinline__ void staged_rows(const PatternView& a, const StagePlan& sp, const int2* sx,
-                                            const uint32_t* smask, int64_t r0, uint32_t emax, bool exact_path,
-                                            double* __restrict__ y, uint32_t (&w)[kMaxRecordWords]) {
+template <int WORDS, int NU, int RPT, int RUN, int THREADS, typename Off>
+__device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const int2* sx, const uint32_t* smask,
+                                          int64_t r0, uint32_t emax, bool exact_path, double* __restrict__ y,
+                                          uint32_t (&w)[kMaxRecordWords]) {
     const int tid = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -443,7 +444,7 @@ __device__ __forceinline__ void staged_rows(const PatternView& a, const StagePla
 #pragma unroll
             for (int u = 0; u < NU; ++u)
                 if ((mask >> u) & 1u) {
-                    const int2 b = sx[rl + (VEC ? sp.soff_padded[u] : sp.soff[u])];
+                    const int2 b = sx[rl + off(u)];
                     acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
                 }
             y[r] = acc;
@@ -454,10 +455,34 @@ __device__ __forceinline__ void staged_rows(const PatternView& a, const StagePla
             continue;
         }
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
-        if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+        const bool dom = __all_sync(__activemask(), is_dominant<WORDS>(a, w));
+        if (NU == 27 && RUN == 3 && dom && a.dom_uni) {
+            // uniform neighbour weights: sum the 26 neighbour limbs exactly in
+            // 32-bit integers (|xh| < 2^27: two partial sums of 13 terms;
+            // |xl| < 2^26: one of 26), then scale once
+            int32_t sh0 = 0, sh1 = 0, sl = 0;
+            int2 vc = make_int2(0, 0);
 #pragma unroll
             for (int k = 0; k < NU / RUN; ++k) {
-                const int2* p = sx + rl + (VEC ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
+                const int2* p = sx + rl + off(k * RUN);
+#pragma unroll
+                for (int j = 0; j < RUN; ++j) {
+                    const int u = k * RUN + j;
+                    const int2 v = p[j];
+                    if (u == 13) { vc = v; continue; }
+                    if (u < 13) sh0 += v.y;
+                    else sh1 += v.y;
+                    sl += v.x;
+                }
+            }
+            ah[0] = int64_t(a.dom_mo) * sh0 + int64_t(a.dom_mo) * sh1;
+            ah[1] = int64_t(a.dom_mc) * vc.y;
+            al[0] = int64_t(a.dom_mo) * sl;
+            al[1] = int64_t(a.dom_mc) * vc.x;
+        } else if (dom) {
+#pragma unroll
+            for (int k = 0; k < NU / RUN; ++k) {
+                const int2* p = sx + rl + off(k * RUN);
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) {
                     const int u = k * RUN + j;
@@ -472,7 +497,7 @@ __device__ __forceinline__ void staged_rows(const PatternView& a, const StagePla
             for (int k = 0; k < (NU + 3) / 4; ++k) mw[k] = prmt(a.mult_lo, a.mult_hi, prmt(w[k] | (w[k] >> 4), 0u, 0x0020u));
 #pragma unroll
             for (int k = 0; k < NU / RUN; ++k) {
-                const int2* p = sx + rl + (VEC ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
+                const int2* p = sx + rl + off(k * RUN);
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) {
                     const int u = k * RUN + j;
@@ -564,7 +589,8 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) pattern_fast_staged_k
     }
     __syncthreads();
     // phase 3: rows
-    staged_rows<WORDS, NU, RPT, RUN, THREADS, VEC>(a, sp, sx, smask, r0, emax, exact_path, y, w0);
+    tile_rows<WORDS, NU, RPT, RUN, THREADS>(a, [&](int u) { return VEC ? sp.soff_padded[u] : sp.soff[u]; }, sx,
+                                            smask, r0, emax, exact_path, y, w0);
 }
 
 // ------------------------- FAST order, register-staged tiles (27 slots) ---
@@ -644,8 +670,107 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
         }
     }
     __syncthreads();
-    staged_rows<7, 27, RPT, 3, THREADS, true>(a, sp, reinterpret_cast<const int2*>(sx4), smask, r0, emax,
-                                              exact_path, y, w0);
+    tile_rows<7, 27, RPT, 3, THREADS>(a, [&](int u) { return sp.soff_padded[u]; },
+                                      reinterpret_cast<const int2*>(sx4), smask, r0, emax, exact_path, y, w0);
+}
+
+// ------------------------------------- FAST order, z-marching tiles ------
+// The full 27-point union's tile windows are three copies of one window
+// shape spaced by the plane stride S.  A CTA keeps the windows of planes
+// z-1, z, z+1 of its column block converted in a ring of three shared-memory
+// slots and walks z upward: each step computes plane z's rows while the
+// 16-byte loads of window W(z+2) are in flight, then converts W(z+2) into
+// the slot W(z-1) leaves.  Every x element is loaded and converted about
+// once per column block instead of three times.  The exponent is the
+// vector's largest one (a pre-pass), so all windows share one scale.
+template <int QS, int THREADS>
+__device__ __forceinline__ void zmarch_load(const PatternView& a, const ZPlan& zp, const double* __restrict__ x,
+                                            int64_t z, int64_t col0, uint4 (&b)[QS]) {
+    const int64_t g = z * zp.S + col0 + zp.m1;
+    const int64_t g0 = g - (g & 1);                       // even: 16-byte aligned
+    const uint4* __restrict__ x4 = reinterpret_cast<const uint4*>(x);
+    const uint2* __restrict__ x2 = reinterpret_cast<const uint2*>(x);
+#pragma unroll
+    for (int j = 0; j < QS; ++j) {
+        const int q = threadIdx.x + j * THREADS;
+        const int64_t e = g0 + 2 * q;
+        b[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (q < zp.pairs) {
+            if (uint64_t(e) < uint64_t(a.n - 1)) {
+                b[j] = __ldg(x4 + (e >> 1));
+            } else if (e == a.n - 1) {
+                const uint2 h = __ldg(x2 + e);
+                b[j].x = h.x;
+                b[j].y = h.y;
+            }
+        }
+    }
+}
+
+template <int QS, int THREADS>
+__device__ __forceinline__ void zmarch_store(const ZPlan& zp, int4* sx4, int64_t z, const uint4 (&b)[QS],
+                                             uint32_t emax, bool exact_path) {
+    int4* dst = sx4 + int((z + 3) % 3) * (zp.slot / 2);
+#pragma unroll
+    for (int j = 0; j < QS; ++j) {
+        const int q = threadIdx.x + j * THREADS;
+        if (q >= zp.pairs) continue;
+        const uint4 v = b[j];
+        if (exact_path) {
+            dst[q] = make_int4(int(v.x), int(v.y), int(v.z), int(v.w));
+        } else {
+            const int2 l0 = fixed_limbs(v.x, v.y, emax);
+            const int2 l1 = fixed_limbs(v.z, v.w, emax);
+            dst[q] = make_int4(l0.x, l0.y, l1.x, l1.y);
+        }
+    }
+}
+
+template <int RPT, int THREADS, int MINB, int QS>
+__global__ void __launch_bounds__(THREADS, MINB) pattern_fast_zmarch_kernel(PatternView a, ZPlan zp,
+                                                                            const double* __restrict__ x,
+                                                                            double* __restrict__ y,
+                                                                            const uint32_t* __restrict__ partial) {
+    extern __shared__ int4 sx4[];
+    __shared__ uint32_t smask[32];
+    __shared__ int s_emax;
+    const int tid = threadIdx.x;
+    const int blk = int(blockIdx.x % unsigned(zp.nblk));
+    const int64_t z0 = int64_t(blockIdx.x / unsigned(zp.nblk)) * zp.zc;
+    const int64_t z1 = min(zp.nplanes, z0 + zp.zc);
+    const int64_t col0 = int64_t(blk) * zp.rows;
+    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
+    const uint32_t emax = uint32_t(block_emax(partial, &s_emax));   // also orders smask
+    const bool exact_path = emax < 64u || emax >= 2047u;
+    uint4 b[QS];
+    // the ring starts with W(z0-1), W(z0), W(z0+1)
+    for (int64_t z = z0 - 1; z <= z0 + 1; ++z) {
+        zmarch_load<QS, THREADS>(a, zp, x, z, col0, b);
+        zmarch_store<QS, THREADS>(zp, sx4, z, b, emax, exact_path);
+    }
+    __syncthreads();
+    const int2* sx = reinterpret_cast<const int2*>(sx4);
+    uint32_t w0[kMaxRecordWords];                        // first row's record of the step
+    if (z0 * zp.S + col0 + tid < a.n) load_record<7>(a, z0 * zp.S + col0 + tid, w0);
+    for (int64_t z = z0; z < z1; ++z) {
+        const bool more = z + 2 <= z1;                   // plane z+1 is this CTA's: it needs W(z+2)
+        if (more) zmarch_load<QS, THREADS>(a, zp, x, z + 2, col0, b);
+        const int64_t r0 = z * zp.S + col0;
+        // shared-memory index of each segment's window start for local row 0
+        int base[3];
+#pragma unroll
+        for (int sg = 0; sg < 3; ++sg) {
+            const int64_t zz = z - 1 + sg;
+            base[sg] = int((zz + 3) % 3) * zp.slot + int((zz * zp.S + col0 + zp.m1) & 1);
+        }
+        tile_rows<7, 27, RPT, 3, THREADS>(a, [&](int u) { return base[u / 9] + zp.rel[u]; }, sx, smask, r0, emax,
+                                          exact_path, y, w0);
+        // the next step's first record, in flight across the barriers
+        if (z + 1 < z1 && r0 + zp.S + tid < a.n) load_record<7>(a, r0 + zp.S + tid, w0);
+        __syncthreads();                                 // W(z-1)'s slot is free
+        if (more) zmarch_store<QS, THREADS>(zp, sx4, z + 2, b, emax, exact_path);
+        __syncthreads();
+    }
 }
 
 // ------------------- FAST order, staged tiles of the pre-converted copy ---
@@ -1591,6 +1716,72 @@ cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& s
     if (threads == 256 && sp.rows_per_thread == 4) return go(pattern_fast_rstaged_kernel<3, 4, 256, 4>);
     if (threads == 256 && sp.rows_per_thread == 2) return go(pattern_fast_rstaged_kernel<2, 2, 256, 5>);
     return go(pattern_fast_rstaged_kernel<2, 2, 512, 2>);
+}
+
+bool make_zplan(const std::vector<int32_t>& uoff, int64_t n, int rows_per_thread, int threads, int num_sms,
+                ZPlan* out) {
+    if (uoff.size() != 27 || n <= 0) return false;
+    StagePlan sp;
+    if (!make_stage_plan(uoff, rows_per_thread, threads, 1 << 30, &sp) || sp.nseg != 3) return false;
+    ZPlan z{};
+    z.rows = sp.rows;
+    z.rows_per_thread = rows_per_thread;
+    z.threads = threads;
+    const int64_t S = int64_t(sp.seg_min[1]) - sp.seg_min[0];
+    if (S <= 0 || int64_t(sp.seg_min[2]) - sp.seg_min[1] != S) return false;
+    if (sp.seg_span[0] != sp.seg_span[1] || sp.seg_span[1] != sp.seg_span[2]) return false;
+    if (S % sp.rows != 0) return false;
+    // nine slots per segment, in order
+    for (int u = 0; u < 27; ++u) {
+        const int sg = u / 9;
+        if (uoff[u] < sp.seg_min[sg] || uoff[u] > sp.seg_min[sg] + sp.seg_span[sg]) return false;
+        z.rel[u] = uoff[u] - sp.seg_min[sg];
+    }
+    z.S = S;
+    z.m1 = sp.seg_min[1];
+    z.pairs = (sp.rows + sp.seg_span[1] + 1 + 1) / 2;
+    z.slot = 2 * z.pairs;
+    if (3 * int64_t(z.slot) * 8 > 200 * 1024) return false;
+    z.nplanes = (n + S - 1) / S;
+    z.nblk = int32_t(S / sp.rows);
+    // about four CTAs per SM in one wave
+    int64_t chunks = std::max<int64_t>(1, (int64_t(num_sms) * 4 + z.nblk / 2) / z.nblk);
+    chunks = std::min<int64_t>(chunks, z.nplanes);
+    z.zc = int32_t((z.nplanes + chunks - 1) / chunks);
+    z.nchunks = int32_t((z.nplanes + z.zc - 1) / z.zc);
+    if (int64_t(z.nblk) * z.nchunks >= (int64_t(1) << 31)) return false;
+    *out = z;
+    return true;
+}
+
+bool zmarch_supported(const ZPlan& zp) {
+    if (zp.threads == 256 && zp.rows_per_thread == 2) return zp.pairs <= 2 * 256;
+    if (zp.threads == 256 && zp.rows_per_thread == 4) return zp.pairs <= 3 * 256;
+    if (zp.threads == 512 && zp.rows_per_thread == 2) return zp.pairs <= 2 * 512;
+    return false;
+}
+
+cudaError_t launch_pattern_fast_zmarch(const PatternView& a, const ZPlan& zp, const double* x, double* y,
+                                       uint32_t* partial, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (!(a.run_len == 3 && a.nu == 27 && a.words == 7) || !zmarch_supported(zp)) return cudaErrorNotSupported;
+    // the 16-byte loads need x 16-byte aligned: otherwise the direct kernel
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return launch_pattern_fast_f64(a, x, y, partial, s);
+    xmax_kernel<<<kXmaxBlocks, 1024, 0, s>>>(x, a.n, partial);
+    const unsigned grid = unsigned(int64_t(zp.nblk) * zp.nchunks);
+    const size_t smem = size_t(3) * zp.slot * sizeof(int2);
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     int(cudaSharedmemCarveoutMaxShared));
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, zp.threads, smem, s>>>(a, zp, x, y, partial);
+        return cudaGetLastError();
+    };
+    if (zp.threads == 256 && zp.rows_per_thread == 2) return go(pattern_fast_zmarch_kernel<2, 256, 4, 2>);
+    if (zp.threads == 256 && zp.rows_per_thread == 4) return go(pattern_fast_zmarch_kernel<4, 256, 4, 3>);
+    return go(pattern_fast_zmarch_kernel<2, 512, 2, 2>);
 }
 
 bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }

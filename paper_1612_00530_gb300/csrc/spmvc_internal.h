@@ -119,6 +119,10 @@ struct PatternView {
     uint32_t dom_w[kMaxRecordWords];
     int32_t dom_m[32];              // FAST order: int8 multipliers of its slots
     float dom_v32[32];              // binary32: its slot values
+    // FAST order, full 27-slot union: the dominant record's multipliers are
+    // dom_mc at the middle slot (displacement 0) and one value dom_mo at all
+    // 26 others (a stencil with uniform neighbour weights)
+    int32_t dom_uni, dom_mo, dom_mc;
     int32_t* err;                   // sticky device error word
 };
 
@@ -154,6 +158,24 @@ struct StagePlan {
     int32_t soff_padded[32];
     int32_t elems_padded;
 };
+// z-marching plan of the full 27-point union: its tile windows are three
+// copies of one window shape spaced by the plane stride S (the displacement
+// between consecutive segments).  A CTA owns a column block of `rows`
+// consecutive rows inside a plane and walks planes z0 .. z0+zc-1: plane z
+// needs the windows W(z-1), W(z), W(z+1), so each step loads one new window
+// into a ring of three shared-memory slots.
+struct ZPlan {
+    int32_t rows, rows_per_thread, threads;
+    int32_t pairs;                  // 16-byte pairs per window (covers an odd start)
+    int32_t slot;                   // int2 entries per ring slot (2 * pairs)
+    int32_t nblk, zc, nchunks;      // column blocks per plane, planes per CTA, CTAs per block column
+    int32_t m1;                     // first displacement of the middle segment
+    int32_t rel[27];                // slot u: displacement minus its segment's first one
+    int64_t S, nplanes;
+};
+bool make_zplan(const std::vector<int32_t>& uoff, int64_t n, int rows_per_thread, int threads, int num_sms,
+                ZPlan* out);
+bool zmarch_supported(const ZPlan& zp);  // shapes with a compiled z-marching kernel
 bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
                      StagePlan* out);
 bool stage_supported(int nu);  // union sizes with a compiled staged kernel
@@ -170,6 +192,8 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
                                        cudaStream_t s);
 cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                         cudaStream_t s);
+cudaError_t launch_pattern_fast_zmarch(const PatternView& a, const ZPlan& zp, const double* x, double* y,
+                                       uint32_t* partial, cudaStream_t s);
 cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                         uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp, const double* x, double* y,
@@ -231,6 +255,8 @@ struct spmv_mat_s {
     int32_t* d_err = nullptr;
     spmvc::StagePlan stage{};          // FAST order: shared-memory staging plan
     bool stage_ok = false;
+    spmvc::ZPlan zplan{};              // FAST order, z-marching kernel
+    bool zplan_ok = false;
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;

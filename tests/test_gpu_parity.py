@@ -340,8 +340,11 @@ def test_fast_variants_on_hpcg_grids():
         shapes = [(0, 0, 512), (1, 512, 512), (1, 1024, 512), (1, 2048, 512), (1, 512, 256), (1, 1024, 256),
                   (1, 2048, 256), (2, 0, 512), (3, 512, 512), (3, 1024, 512), (3, 2048, 512), (4, 0, 512), (5, 0, 512)]
         # register-staged tiles: three plane windows, each within the pairs the threads hold
-        rstaged = {(25, 25, 5): [(6, 512, 256)], (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512)]}
-        for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512)]:
+        # and z-marching tiles: plane stride (here 3072) a multiple of the tile
+        rstaged = {(25, 25, 5): [(6, 512, 256)],
+                   (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512),
+                                  (7, 512, 256), (7, 1024, 256), (7, 1024, 512)]}
+        for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512), (7, 512, 256), (7, 1024, 256), (7, 1024, 512)]:
             if (v, t, bt) not in rstaged.get(g, []):
                 with pytest.raises(P.SpmvError):
                     P.spmv_set_tile(C, v, t, bt)
@@ -353,6 +356,58 @@ def test_fast_variants_on_hpcg_grids():
             P.spmv_apply(C, xoff, y)
             torch.cuda.synchronize()
             check_fast(y.cpu().numpy(), y_ref, scale)
+
+
+def weighted_27_point_csr(g):
+    """The 27-point grid graph with weights by neighbour kind: face -1,
+    edge -0.5, corner -0.25, centre 12 (the dominant record's multipliers
+    are not all equal off the centre)."""
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    nx, ny, _ = g
+    rows = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    d = [np.abs(rows % nx - col % nx), np.abs(rows // nx % ny - col // nx % ny), np.abs(rows // (nx * ny) - col // (nx * ny))]
+    kind = d[0] + d[1] + d[2]
+    w = np.choose(kind, [12.0, -1.0, -0.5, -0.25])
+    return rowptr, col, w
+
+
+def test_fast_27_point_non_uniform_weights():
+    """Full 27-slot union whose dominant record has several off-centre
+    multipliers: the per-slot dominant path of the staged kernels."""
+    g = (40, 36, 12)
+    rowptr, col, val = weighted_27_point_csr(g)
+    n = len(rowptr) - 1
+    x = spmv_inputs.uniform_vector(n, seed=21)
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    scale = abs_row_sums(rowptr, col, val, x)
+    C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (2, 0, 512), (6, 1024, 256), (6, 512, 256)]:
+        P.spmv_set_tile(C, v, t, bt)
+        check_fast(run(C, x), y_ref, scale)
+    # plane stride 2048: the z-marching kernel on the same weights
+    g = (32, 64, 6)
+    rowptr, col, val = weighted_27_point_csr(g)
+    n = len(rowptr) - 1
+    x = spmv_inputs.uniform_vector(n, seed=22)
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    scale = abs_row_sums(rowptr, col, val, x)
+    C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (7, 1024, 512)]:
+        P.spmv_set_tile(C, v, t, bt)
+        check_fast(run(C, x), y_ref, scale)
+
+
+def test_fast_zmarch_several_planes_per_cta():
+    """The z-marching kernel on 64x64x160, where each CTA walks two or three
+    planes, on sampled rows, A*1 and a non-finite entry."""
+    # 64x64x160: three planes per CTA
+    g = (64, 64, 160)
+    n = 64 * 64 * 160
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    x = spmv_inputs.uniform_vector(n, seed=24)
+    for v, t, bt in [(7, 512, 256), (7, 1024, 256)]:
+        P.spmv_set_tile(C, v, t, bt)
+        check_persistent(C, g, n, x)
 
 
 def test_set_tile_rejects_shapes_without_kernel():
@@ -379,7 +434,7 @@ def test_autotune_keeps_results():
     rows = P.spmv_autotune(C, x, y, reps=3)
     assert rows in (1, 4, 5, 512, 1024, 2048)
     info = P.spmv_info(C)
-    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6))
+    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6, 7))
     if rows not in (1, 4, 5):
         assert info["fast_tile_rows"] == rows
     y_ref = oracle.spmv(rowptr, col, val, x_np)
@@ -417,7 +472,9 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
     cases = [((9, 7, 6), [(0, 0, 512), (1, 512, 512), (1, 2048, 512), (1, 1024, 256), (1, 2048, 256),
                           (2, 0, 512), (3, 1024, 512), (3, 2048, 512), (4, 0, 512), (5, 0, 512)]),
              # three separate plane windows per 512-row tile: the register-staged kernel
-             ((24, 24, 4), [(6, 512, 256), (1, 512, 256), (2, 0, 512)])]
+             ((24, 24, 4), [(6, 512, 256), (1, 512, 256), (2, 0, 512)]),
+             # plane stride 2048: z-marching tiles
+             ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512)])]
     for g, shapes in cases:
         rowptr, col, val = oracle.hpcg_csr(*g)
         n = len(rowptr) - 1
@@ -475,7 +532,8 @@ def test_fast_variant_persistent_many_tiles():
     n = 96 ** 3
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x = spmv_inputs.uniform_vector(n, seed=13)
-    for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512)]:
+    for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512),
+                           (7, 512, 256), (7, 1024, 256), (7, 1024, 512)]:
         P.spmv_set_tile(C, variant, t, bt)
         check_persistent(C, g, n, x)
 
