@@ -410,6 +410,25 @@ def test_fast_zmarch_several_planes_per_cta():
         check_persistent(C, g, n, x)
 
 
+def test_fast_uniform_stencil_with_odd_rows():
+    """Grid graph with uniform weights (the uniform-neighbour paths) where a
+    few interior and boundary rows carry other values: their warps take the
+    per-slot path, every other warp the full or restricted uniform one."""
+    g = (32, 64, 6)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    val = val.copy()
+    n = len(rowptr) - 1
+    for r in (0, 5, 4000, 4001, 7777, n - 1):
+        val[rowptr[r]] = 2.0 if val[rowptr[r]] < 0 else 25.0
+    x = spmv_inputs.uniform_vector(n, seed=25)
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    scale = abs_row_sums(rowptr, col, val, x)
+    C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (6, 1024, 256), (7, 512, 256), (7, 1024, 512)]:
+        P.spmv_set_tile(C, v, t, bt)
+        check_fast(run(C, x), y_ref, scale)
+
+
 def test_set_tile_rejects_shapes_without_kernel():
     C = P.spmv_compress(P.spmv_build("hpcg", 16, 16, 16), format="pattern", order="fast")
     for v, t, bt in [(1, 1024, 128), (3, 1024, 256), (1, 768, 256), (1, 4096, 256), (1, 256, 256)]:
