@@ -63,9 +63,15 @@ typedef void *spmv_stream_t;
 #define SPMV_FMT_PATTERN 2     /* uint8 value codes + stencil-pattern number per row */
 #define SPMV_FMT_DELTA 3       /* per 32-row slice: int16 delta or int32 column,
                                   uint8 code or FP64 value */
+#define SPMV_FMT_DIT 4         /* Sec. V "Data+Index Table": per row a type (a
+                                  registered value-grouped displacement list)
+                                  and its value-group ends; Listing 1 decode */
 
 #define SPMV_ORDER_COLUMN 0    /* y_i = fma chain over ascending columns from 0:
-                                  bit-identical to the plain CSR product */
+                                  bit-identical to the plain CSR product (the
+                                  Data+Index Table format: Listing 1's chain,
+                                  value groups ascending, columns ascending
+                                  inside a group) */
 #define SPMV_ORDER_FAST 1      /* pattern format only: exact fixed-point sums,
                                   one rounding per row (error bound below) */
 
@@ -102,7 +108,8 @@ int spmv_build_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
 
 /* ---- compression (Sec. V) -------------------------------------------- */
 typedef struct {
-    int32_t format;        /* SPMV_FMT_AUTO, SPMV_FMT_PATTERN or SPMV_FMT_DELTA */
+    int32_t format;        /* SPMV_FMT_AUTO, SPMV_FMT_PATTERN, SPMV_FMT_DELTA or
+                              SPMV_FMT_DIT (never chosen by AUTO) */
     int32_t order;         /* SPMV_ORDER_COLUMN or SPMV_ORDER_FAST */
     int32_t max_dict;      /* largest value table, 1..254 (default 254 when 0) */
     int32_t min_count;     /* delta format: a value enters the table only if it
@@ -117,8 +124,14 @@ typedef struct {
  * every value is in V; each row is stored as one uint8 code per union slot
  * plus its 5-bit pattern number.  Delta format: rows in slices of 32, each
  * slice storing int16 column deltas (or raw int32 columns) and uint8 codes
- * (or raw FP64 values).  opts may be NULL (AUTO, COLUMN).  Errors:
- * SPMV_EUNSUPPORTED when the requested format cannot hold A. */
+ * (or raw FP64 values).  Data+Index Table (Sec. V, Fig. 2, Listing 1): each
+ * row's entries sorted by value (columns ascending inside a value), made
+ * relative to the row and registered as one of at most 256 types; the row
+ * keeps a uint8 type and one uint8 group end per value (at most 255 values
+ * and 255 entries a row).  It serves spmv_apply, spmv_apply_host,
+ * spmv_decompress and FP64 cg_solve; other calls return SPMV_EUNSUPPORTED.
+ * opts may be NULL (AUTO, COLUMN).  Errors: SPMV_EUNSUPPORTED when the
+ * requested format cannot hold A. */
 int spmv_compress(spmv_mat_t A, const spmv_opts *opts, spmv_mat_t *out);
 
 /* Selects the summation order used by later spmv_apply/spmm_apply calls on a

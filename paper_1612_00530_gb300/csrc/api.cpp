@@ -17,6 +17,7 @@ namespace spmvc {
 int decompress_ell(int64_t n, const EllFormat& e, Csr* out);
 int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out);
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out);
+int decompress_dit(int64_t n, const DitFormat& d, Csr* out);
 uint64_t checksum_of(const spmv_mat_s& m);
 int export_stream(const spmv_mat_s& m, void* buf, size_t* len);
 int import_stream(const void* buf, size_t len, spmv_mat_s* m);
@@ -284,6 +285,25 @@ int ensure_device(spmv_mat_s* m) {
         if (m->fast_variant == 6 && !(m->stage_ok && rstage_supported(m->stage))) m->fast_variant = 1;
         if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
         if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
+    } else if (m->fmt == SPMV_FMT_DIT) {
+        const DitFormat& d = m->dit;
+        DitView& v = m->dit_view;
+        v.n = m->n;
+        v.nv = static_cast<int32_t>(d.dict.size());
+        v.ntypes = static_cast<int32_t>(d.tlen.size());
+        v.maxlen = std::max<int32_t>(d.maxlen, 1);
+        uint8_t *ty, *en;
+        int32_t* ds;
+        double* dd;
+        if ((st = dev_copy(m, d.type.data(), d.type.size(), &ty))) return st;
+        if ((st = dev_copy(m, d.ends.data(), d.ends.size(), &en))) return st;
+        if ((st = dev_copy(m, d.disp.data(), d.disp.size(), &ds))) return st;
+        if ((st = dev_copy(m, d.dict.data(), d.dict.size(), &dd))) return st;
+        v.type = ty;
+        v.ends = en;
+        v.disp = ds;
+        v.dict = dd;
+        v.err = m->d_err;
     } else {
         const DeltaFormat& d = m->dlt;
         DeltaView& v = m->dlt_view;
@@ -344,6 +364,7 @@ int to_csr(spmv_mat_s* a, Csr* c) {
     }
     if (a->fmt == SPMV_FMT_ELL) return decompress_ell(a->n, a->ell, c);
     if (a->fmt == SPMV_FMT_PATTERN) return decompress_pattern(a->n, a->pat, c);
+    if (a->fmt == SPMV_FMT_DIT) return decompress_dit(a->n, a->dit, c);
     return decompress_delta(a->n, a->dlt, c);
 }
 
@@ -387,8 +408,9 @@ int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
     if (o.max_dict <= 0) o.max_dict = 254;
     if (o.min_count <= 0) o.min_count = 64;
     if (o.max_dict > 254) return fail(SPMV_EINVAL, "max_dict above 254");
-    if (o.format != SPMV_FMT_AUTO && o.format != SPMV_FMT_PATTERN && o.format != SPMV_FMT_DELTA)
-        return fail(SPMV_EINVAL, "compress format must be AUTO, PATTERN or DELTA");
+    if (o.format != SPMV_FMT_AUTO && o.format != SPMV_FMT_PATTERN && o.format != SPMV_FMT_DELTA &&
+        o.format != SPMV_FMT_DIT)
+        return fail(SPMV_EINVAL, "compress format must be AUTO, PATTERN, DELTA or DIT");
     Csr c;
     int st = to_csr(A, &c);
     if (st) return st;
@@ -396,7 +418,11 @@ int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
     if ((st = new_handle(out, &m))) return st;
     stats_from_csr(m, c);
     st = SPMV_EUNSUPPORTED;
-    if (o.format == SPMV_FMT_AUTO || o.format == SPMV_FMT_PATTERN) {
+    if (o.format == SPMV_FMT_DIT) {
+        st = compress_dit(c, &m->dit);
+        if (st) { delete m; return st; }
+        m->fmt = SPMV_FMT_DIT;
+    } else if (o.format == SPMV_FMT_AUTO || o.format == SPMV_FMT_PATTERN) {
         st = compress_pattern(c, o.max_dict, &m->pat);
         if (st == SPMV_OK) m->fmt = SPMV_FMT_PATTERN;
         else if (o.format == SPMV_FMT_PATTERN) { delete m; return st; }
@@ -454,6 +480,13 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
+    } else if (A->fmt == SPMV_FMT_DIT) {
+        out->dict_size = static_cast<int32_t>(A->dit.dict.size());
+        out->n_patterns = static_cast<int32_t>(A->dit.tlen.size());
+        out->union_size = A->dit.maxlen;
+        out->record_bytes = 1 + out->dict_size;
+        out->format_bytes = A->n * out->record_bytes;
+        out->device_bytes = out->format_bytes + static_cast<int64_t>(A->dit.disp.size() * 4 + A->dit.dict.size() * 8);
     } else {
         out->dict_size = static_cast<int32_t>(A->dlt.dict.size());
         out->n_slices = A->dlt.nslices;
@@ -482,6 +515,7 @@ int spmv_decompress(spmv_mat_t A, int64_t* rowptr, int32_t* col, double* val) {
     int st;
     if (A->fmt == SPMV_FMT_ELL) st = decompress_ell(A->n, A->ell, &c);
     else if (A->fmt == SPMV_FMT_PATTERN) st = decompress_pattern(A->n, A->pat, &c);
+    else if (A->fmt == SPMV_FMT_DIT) st = decompress_dit(A->n, A->dit, &c);
     else st = decompress_delta(A->n, A->dlt, &c);
     if (st) return st;
     if (c.nnz() != A->nnz) return fail(SPMV_ECORRUPT, "decompressed nonzero count differs");
@@ -541,6 +575,7 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
             : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, s)
             : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
                                    : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
+    else if (A->fmt == SPMV_FMT_DIT) e = launch_dit_f64(A->dit_view, x, y, s);
     else e = launch_delta_f64(A->dlt_view, x, y, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
     return SPMV_OK;
@@ -566,6 +601,7 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
 
 int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no binary32 product for the Data+Index Table format");
     if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
     int st = ensure_device(A);
     if (st) return st;
@@ -592,6 +628,7 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y,
                spmv_stream_t stream) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (k < 1 || k > 64 || ldx < k || ldy < k) return fail(SPMV_EINVAL, "need 1 <= k <= 64, ldx >= k, ldy >= k");
+    if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no SpMM for the Data+Index Table format");
     if (A->n > 0 && (!X || !Y)) return fail(SPMV_EINVAL, "null block");
     int st = ensure_device(A);
     if (st) return st;

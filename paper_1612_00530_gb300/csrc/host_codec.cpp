@@ -2,6 +2,7 @@
 // copied, never recomputed), stream checksums, and export/import of a
 // matrix's stored form.  Decompression checks every decoded index, so it is
 // also how an imported stream is validated before any kernel can see it.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -12,6 +13,7 @@ namespace spmvc {
 int decompress_ell(int64_t n, const EllFormat& e, Csr* out);
 int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out);
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out);
+int decompress_dit(int64_t n, const DitFormat& d, Csr* out);
 uint64_t checksum_of(const spmv_mat_s& m);
 int export_stream(const spmv_mat_s& m, void* buf, size_t* len);
 int import_stream(const void* buf, size_t len, spmv_mat_s* m);
@@ -107,6 +109,45 @@ int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out) {
     return finish_csr(out);
 }
 
+// Data+Index Table -> CSR: walk each row's value groups (Listing 1), then
+// put the entries back in column order.  Every index is checked.
+int decompress_dit(int64_t n, const DitFormat& d, Csr* out) {
+    const int nv = static_cast<int>(d.dict.size());
+    const int64_t ntypes = static_cast<int64_t>(d.tlen.size());
+    const int64_t stride = std::max<int32_t>(d.maxlen, 1);
+    if (static_cast<int64_t>(d.type.size()) != n || static_cast<int64_t>(d.ends.size()) != n * nv ||
+        static_cast<int64_t>(d.disp.size()) != ntypes * stride)
+        return corrupt("Data+Index Table sizes");
+    out->n = n;
+    out->rowptr.assign(static_cast<size_t>(n) + 1, 0);
+    out->col.clear();
+    out->val.clear();
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t t = d.type[r];
+        if (t >= ntypes) return corrupt("row type");
+        row.clear();
+        int idx = 0;
+        for (int v = 0; v < nv; ++v) {
+            const int end = d.ends[static_cast<size_t>(v) * n + r];
+            if (end < idx || end > d.tlen[t]) return corrupt("value group end");
+            for (; idx < end; ++idx) {
+                const int64_t c = r + d.disp[t * stride + idx];
+                if (c < 0 || c >= n) return corrupt("column outside the matrix");
+                row.emplace_back(static_cast<int32_t>(c), d.dict[v]);
+            }
+        }
+        if (idx != d.tlen[t]) return corrupt("row length");
+        std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (const auto& e : row) {
+            out->col.push_back(e.first);
+            out->val.push_back(e.second);
+        }
+        out->rowptr[r + 1] = static_cast<int64_t>(out->col.size());
+    }
+    return finish_csr(out);
+}
+
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out) {
     if (d.nslices != (n + kSliceRows - 1) / kSliceRows || (int64_t)d.hdr.size() != d.nslices || d.dict.size() > 255)
         return corrupt("delta slice table size");
@@ -174,6 +215,13 @@ uint64_t checksum_of(const spmv_mat_s& m) {
         f.vec(m.pat.pmask);
         f.pod(m.pat.words);
         f.vec(m.pat.rec);
+    } else if (m.fmt == SPMV_FMT_DIT) {
+        f.vec(m.dit.dict);
+        f.pod(m.dit.maxlen);
+        f.vec(m.dit.disp);
+        f.vec(m.dit.tlen);
+        f.vec(m.dit.type);
+        f.vec(m.dit.ends);
     } else {
         f.vec(m.dlt.dict);
         f.vec(m.dlt.hdr);
@@ -223,6 +271,7 @@ const char kTag[8] = {'S', 'P', 'M', 'V', 'C', 0, 'v', '1'};
 }  // namespace
 
 int export_stream(const spmv_mat_s& m, void* buf, size_t* len) {
+    if (m.fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "the Data+Index Table format has no stream form");
     Writer w{static_cast<uint8_t*>(buf), 0, buf ? *len : 0, buf == nullptr};
     w.put(kTag, 8);
     w.pod(m.fmt);

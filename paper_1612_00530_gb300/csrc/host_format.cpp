@@ -192,6 +192,56 @@ int compress_pattern(const Csr& a, int max_dict, PatternFormat* out) {
     return SPMV_OK;
 }
 
+// ------------------------------------------------------ Data+Index Table ---
+// Sec. V: each row's nonzeros sorted by value (columns ascending inside a
+// value), made relative to the row (column - row), and the displacement
+// list registered as a type; the row keeps its type and the end of each
+// value group (Fig. 2's terminal indices, stored exclusive).
+int compress_dit(const Csr& a, DitFormat* out) {
+    const int64_t n = a.n;
+    std::unordered_map<uint64_t, int64_t> counts;
+    int st = value_table(a.val, &out->dict, &counts);
+    if (st) return st;
+    const int nv = static_cast<int>(out->dict.size());
+    if (nv > 255) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: more than 255 distinct values");
+    std::unordered_map<uint64_t, int> code_of;
+    for (int v = 0; v < nv; ++v) code_of[bits_of(out->dict[v])] = v;
+    std::map<std::vector<int32_t>, int> types;
+    std::vector<std::vector<int32_t>> lists;
+    out->type.assign(static_cast<size_t>(n), 0);
+    out->ends.assign(static_cast<size_t>(n) * nv, 0);
+    std::vector<std::vector<int32_t>> groups(nv);
+    std::vector<int32_t> disp;
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t len = a.rowptr[r + 1] - a.rowptr[r];
+        if (len > 255) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: a row holds more than 255 entries");
+        for (auto& g : groups) g.clear();
+        for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k)
+            groups[code_of[bits_of(a.val[k])]].push_back(static_cast<int32_t>(a.col[k] - r));
+        disp.clear();
+        for (int v = 0; v < nv; ++v) {
+            disp.insert(disp.end(), groups[v].begin(), groups[v].end());
+            out->ends[static_cast<size_t>(v) * n + r] = static_cast<uint8_t>(disp.size());
+        }
+        auto it = types.find(disp);
+        if (it == types.end()) {
+            if (types.size() == 256) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: more than 256 row types");
+            it = types.emplace(disp, static_cast<int>(lists.size())).first;
+            lists.push_back(disp);
+        }
+        out->type[r] = static_cast<uint8_t>(it->second);
+    }
+    out->maxlen = 0;
+    for (const auto& l : lists) out->maxlen = std::max<int32_t>(out->maxlen, static_cast<int32_t>(l.size()));
+    out->disp.assign(lists.size() * static_cast<size_t>(std::max(out->maxlen, 1)), 0);
+    out->tlen.assign(lists.size(), 0);
+    for (size_t t = 0; t < lists.size(); ++t) {
+        std::copy(lists[t].begin(), lists[t].end(), out->disp.begin() + t * std::max(out->maxlen, 1));
+        out->tlen[t] = static_cast<int32_t>(lists[t].size());
+    }
+    return SPMV_OK;
+}
+
 // ---------------------------------------------------------------- delta ---
 int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) {
     const int64_t n = a.n;

@@ -418,6 +418,13 @@ __device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t e
     return make_int2(int32_t(uint32_t(X) & 0x3FFFFFFu) * s1, int32_t(uint32_t(X >> 26)) * s1);
 }
 
+// 16-byte cp.async copy global -> shared of the first nbytes (0..16) of the
+// source, zero-filling the rest (nbytes == 0 reads nothing).
+__device__ __forceinline__ void cp16_zfill(void* sdst, const void* gsrc, uint32_t nbytes) {
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(sdst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(nbytes));
+}
+
 // Row phase of the staged kernels: every thread sums RPT rows (r0 + tid +
 // i*THREADS) slot by slot from the tile's converted windows in shared memory
 // (raw words on the exact path) and rounds once.  off(u): shared-memory
@@ -425,10 +432,11 @@ __device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t e
 // thread's first row (loaded by the caller before the tile's barriers, when
 // that row exists); each row's loop issues the next row's record loads
 // before it sums, so record latency overlaps the previous row's work.
-template <int WORDS, int NU, int RPT, int RUN, int THREADS, typename Off>
+template <int WORDS, int NU, int RPT, int RUN, int THREADS, typename Off, bool SREC = false>
 __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const int2* sx, const uint32_t* smask,
                                           int64_t r0, uint32_t emax, bool exact_path, double* __restrict__ y,
-                                          uint32_t (&w)[kMaxRecordWords]) {
+                                          uint32_t (&w)[kMaxRecordWords], const uint32_t* srec = nullptr,
+                                          int srows = 0) {
     const int tid = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -436,7 +444,17 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
         const int64_t r = r0 + rl;
         if (r >= a.n) break;
         uint32_t wn[kMaxRecordWords];
-        if (i + 1 < RPT && r + THREADS < a.n) load_record<WORDS>(a, r + THREADS, wn);
+        if constexpr (SREC) {
+            // the tile's records were copied to shared memory: words 0..3, 4..5, 6
+            static_assert(WORDS == 7, "shared-memory records are laid out for 7 words");
+            const uint4 v = reinterpret_cast<const uint4*>(srec)[rl];
+            const uint2 v2 = reinterpret_cast<const uint2*>(srec + 4 * srows)[rl];
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+            w[4] = v2.x; w[5] = v2.y;
+            w[6] = srec[6 * srows + rl];
+        } else {
+            if (i + 1 < RPT && r + THREADS < a.n) load_record<WORDS>(a, r + THREADS, wn);
+        }
         if (exact_path) {
             // zeros/denormals only, or non-finite values: the COLUMN order
             const uint32_t mask = smask[byte_of(w, NU) & 31];
@@ -448,7 +466,7 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
                     acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
                 }
             y[r] = acc;
-            if (i + 1 < RPT) {
+            if (!SREC && i + 1 < RPT) {
 #pragma unroll
                 for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
             }
@@ -510,7 +528,7 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
         y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
-        if (i + 1 < RPT) {
+        if (!SREC && i + 1 < RPT) {
 #pragma unroll
             for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
         }
@@ -613,8 +631,28 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
     if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
     const uint4* __restrict__ x4 = reinterpret_cast<const uint4*>(x);
     const uint2* __restrict__ x2 = reinterpret_cast<const uint2*>(x);
-    uint32_t w0[kMaxRecordWords];                  // first row's record, in flight during staging
-    if (r0 + tid < a.n) load_record<7>(a, r0 + tid, w0);
+    // the tile's records (planes of 16, 8 and 4 bytes per row) go to shared
+    // memory behind the windows by cp.async, in flight during the staging;
+    // rows past n read as zero
+    uint32_t* srec = reinterpret_cast<uint32_t*>(sx4 + sp.elems_padded / 2);
+    {
+        const int64_t left = a.n - r0;             // rows of this tile that exist (>= 1)
+        for (int c = tid; c < sp.rows; c += THREADS)
+            cp16_zfill(srec + 4 * c, c < left ? static_cast<const void*>(a.p16a + r0 + c) : a.p16a,
+                       c < left ? 16u : 0u);
+        for (int c = tid; c < sp.rows / 2; c += THREADS) {
+            const int64_t k = min(max(left - 2 * int64_t(c), int64_t(0)), int64_t(2));
+            cp16_zfill(srec + 4 * sp.rows + 4 * c, k ? static_cast<const void*>(a.p8 + r0 + 2 * c) : a.p8,
+                       uint32_t(k) * 8u);
+        }
+        for (int c = tid; c < sp.rows / 4; c += THREADS) {
+            const int64_t k = min(max(left - 4 * int64_t(c), int64_t(0)), int64_t(4));
+            cp16_zfill(srec + 6 * sp.rows + 4 * c, k ? static_cast<const void*>(a.p4 + r0 + 4 * c) : a.p4,
+                       uint32_t(k) * 4u);
+        }
+        asm volatile("cp.async.commit_group;");
+    }
+    uint32_t w0[kMaxRecordWords];
     // phase 1: every pair of the three windows this thread owns, in flight together
     uint4 b[3][QS];
 #pragma unroll
@@ -669,9 +707,11 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
             }
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    tile_rows<7, 27, RPT, 3, THREADS>(a, [&](int u) { return sp.soff_padded[u]; },
-                                      reinterpret_cast<const int2*>(sx4), smask, r0, emax, exact_path, y, w0);
+    auto off = [&](int u) { return sp.soff_padded[u]; };
+    tile_rows<7, 27, RPT, 3, THREADS, decltype(off), true>(a, off, reinterpret_cast<const int2*>(sx4), smask, r0,
+                                                           emax, exact_path, y, w0, srec, sp.rows);
 }
 
 // ------------------------------------- FAST order, z-marching tiles ------
@@ -1691,7 +1731,7 @@ bool rstage_supported(const StagePlan& sp) {
     if (qs == 0 || sp.nseg != 3) return false;
     for (int sg = 0; sg < 3; ++sg)
         if ((sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2 > qs * threads) return false;
-    return true;
+    return int64_t(sp.elems_padded) * 8 + int64_t(sp.rows) * 28 <= 200 * 1024;   // windows + records
 }
 
 cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
@@ -1703,7 +1743,8 @@ cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& s
     if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return launch_pattern_fast_staged(a, sp, x, y, s);
     const int threads = sp.rows / sp.rows_per_thread;
     const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
-    const size_t smem = size_t(sp.elems_padded) * sizeof(int2);
+    // converted windows, then the tile's records (28 bytes a row)
+    const size_t smem = size_t(sp.elems_padded) * sizeof(int2) + size_t(sp.rows) * 28;
     auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e == cudaSuccess)
@@ -1830,6 +1871,53 @@ bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int 
     }
     *out = p;
     return true;
+}
+
+// ------------------------------------------------- Data+Index Table ------
+// Listing 1 on the GPU, one thread per row: the row's type selects its
+// value-grouped displacement list (staged in shared memory when the table
+// fits), and the value groups are walked in ascending order with one fma per
+// entry, so the result is bit-identical to Listing 1's chain.  x is read
+// through the read-only cache.  A displacement leaving [0, n) can only come
+// from a corrupt table: it sets the matrix's error word and is skipped.
+constexpr int kDitSmemInts = 8192;   // 32 KB of displacements
+
+__global__ void __launch_bounds__(kBlock) dit_kernel(DitView a, const double* __restrict__ x,
+                                                    double* __restrict__ y) {
+    __shared__ int32_t sdisp[kDitSmemInts];
+    __shared__ double sdict[256];
+    const int table = a.ntypes * a.maxlen;
+    const bool staged = table <= kDitSmemInts;
+    if (staged)
+        for (int i = threadIdx.x; i < table; i += blockDim.x) sdisp[i] = __ldg(a.disp + i);
+    for (int i = threadIdx.x; i < a.nv; i += blockDim.x) sdict[i] = __ldg(a.dict + i);
+    __syncthreads();
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    const int t = __ldg(a.type + r);
+    const int32_t* d = (staged ? static_cast<const int32_t*>(sdisp) : a.disp) + t * a.maxlen;
+    int idx = 0;
+    double acc = 0.0;
+    for (int v = 0; v < a.nv; ++v) {
+        const double av = sdict[v];
+        const int end = __ldg(a.ends + int64_t(v) * a.n + r);
+        for (; idx < end; ++idx) {
+            const int64_t j = r + (staged ? d[idx] : __ldg(d + idx));
+            if (uint64_t(j) >= uint64_t(a.n)) {
+                atomicOr(a.err, 1);
+                continue;
+            }
+            acc = fma(av, __ldg(x + j), acc);
+        }
+    }
+    y[r] = acc;
+}
+
+cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (a.nv > 256) return cudaErrorInvalidValue;
+    dit_kernel<<<grid_of(a.n), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s) {

@@ -87,6 +87,22 @@ struct DeltaFormat {
 };
 int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out);
 
+// The "Data+Index Table" of Sec. V as Listing 1 reads it: the value table V;
+// for every row its type, the number of a registered list of column
+// displacements in value-grouped order (groups by ascending value, columns
+// ascending inside a group), and the exclusive end of each value group in
+// that list.  Types are uint8 (at most 256), ends uint8 (rows of at most 255
+// entries) stored value-major so that a warp reads them coalesced.
+struct DitFormat {
+    std::vector<double> dict;
+    int32_t maxlen = 0;
+    std::vector<int32_t> disp;      // ntypes x maxlen, unused tail zero
+    std::vector<int32_t> tlen;      // entries of each type
+    std::vector<uint8_t> type;      // n
+    std::vector<uint8_t> ends;      // nv x n
+};
+int compress_dit(const Csr& a, DitFormat* out);
+
 // --------------------------------------------------------- device views --
 struct EllView {
     int64_t n, nslices;
@@ -124,6 +140,16 @@ struct PatternView {
     // 26 others (a stencil with uniform neighbour weights)
     int32_t dom_uni, dom_mo, dom_mc;
     int32_t* err;                   // sticky device error word
+};
+
+struct DitView {
+    int64_t n;
+    int32_t nv, ntypes, maxlen;
+    const uint8_t* type;
+    const uint8_t* ends;            // nv x n
+    const int32_t* disp;            // ntypes x maxlen
+    const double* dict;
+    int32_t* err;
 };
 
 struct DeltaView {
@@ -204,6 +230,7 @@ cudaError_t launch_pattern_fast_async_x(const PatternView& a, const StagePlan& s
 cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s);
 // SpMM (k right-hand sides, row-major).
 cudaError_t launch_pattern_spmm_col(const PatternView& a, int k, const double* X, int64_t ldx,
@@ -244,6 +271,7 @@ struct spmv_mat_s {
     spmvc::EllFormat ell;
     spmvc::PatternFormat pat;
     spmvc::DeltaFormat dlt;
+    spmvc::DitFormat dit;
     uint64_t checksum = 0;
 
     // device side (allocated on first use)
@@ -252,6 +280,7 @@ struct spmv_mat_s {
     spmvc::EllView ell_view{};
     spmvc::PatternView pat_view{};
     spmvc::DeltaView dlt_view{};
+    spmvc::DitView dit_view{};
     int32_t* d_err = nullptr;
     spmvc::StagePlan stage{};          // FAST order: shared-memory staging plan
     bool stage_ok = false;

@@ -170,3 +170,50 @@ def test_empty_matrix():
     assert P.spmv_info(A)["n"] == 0
     C = P.spmv_compress(A, format="delta")
     assert P.spmv_decompress(C)[0].tolist() == [0]
+
+
+@pytest.mark.parametrize("g", [(1, 1, 1), (2, 3, 5), (4, 4, 4), (17, 5, 3), (32, 32, 32)])
+def test_data_index_table_round_trip_and_type_census(g):
+    """Sec. V's Data+Index Table: bit-exact round trip, one type per distinct
+    value-grouped displacement list (the oracle's registry), 1 + |V| bytes a row."""
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    D = P.spmv_compress(P.spmv_build("hpcg", *g), format="dit")
+    assert same_csr(P.spmv_decompress(D), (rowptr, col, val))
+    V = oracle.value_table(val)
+    typ, diffs, typelen, ends = oracle.data_index_table(rowptr, col, val, V)
+    info = P.spmv_info(D)
+    assert info["format_name"] == "dit"
+    assert info["n_patterns"] == len(typelen)
+    assert info["dict_size"] == len(V)
+    assert info["record_bytes"] == 1 + len(V)
+    assert info["union_size"] == typelen.max()
+
+
+def test_data_index_table_signed_zeros_and_refusals():
+    rng = np.random.default_rng(1)
+    n = 400
+    rows = [np.unique(np.concatenate([[i], rng.integers(0, n, size=rng.integers(0, 9))])) for i in range(n)]
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.choice([-0.0, 0.0, 1.5, -2.25, np.inf, 3.0e-310], size=len(col))
+    A = P.spmv_build_csr(rowptr, col, val)
+    # random columns: more than 256 value-grouped displacement lists
+    with pytest.raises(P.SpmvError) as e:
+        P.spmv_compress(A, format="dit")
+    assert e.value.status == P.SPMV_EUNSUPPORTED
+    # a banded matrix with the same values: few types, exact round trip
+    band = [np.arange(max(0, i - 2), min(n, i + 3)) for i in range(n)]
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in band])
+    col = np.concatenate(band).astype(np.int32)
+    val = np.where((col % 3) == 0, -0.0, np.where((col % 3) == 1, 0.0, 1.5))
+    D = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="dit")
+    got = P.spmv_decompress(D)
+    assert np.array_equal(got[0], rowptr) and np.array_equal(got[1], col)
+    assert np.array_equal(got[2].view(np.uint64), val.view(np.uint64))
+    # no stream form, no FAST order
+    with pytest.raises(P.SpmvError):
+        P.spmv_export(D)
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_order(D, "fast")
