@@ -164,11 +164,14 @@ typedef struct {
                                    2 pre-converted fixed-point copy of x, 3 staged
                                    tiles of that copy, 4 persistent double-buffered
                                    tiles, 5 the same from the copy, 6 register-
-                                   staged tiles, 7 z-marching tiles; -1 before
-                                   A's first device call */
+                                   staged tiles, 7 z-marching tiles, 8 register-
+                                   staged with records in shared memory, 9 the
+                                   same reading row types; -1 before A's first
+                                   device call */
     int32_t fast_block_threads; /* FAST order: threads per block of the staged
                                    kernel (512 or 256; 0 = no staged kernel) */
-    int32_t reserved0;
+    int32_t row_types;          /* pattern format: distinct row records held as
+                                   one-byte row types (variant 9), else 0 */
 } spmv_info_t;
 
 /* Fills *out with the sizes and statistics of A (host only). */
@@ -236,9 +239,13 @@ int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_
  * double-buffered tiles, 5 the same fed from the copy, 6 register-staged
  * tiles (full 27-point union; tile_rows 1024 with spmv_set_tile's 512 or
  * 256 threads, or 512 with 256 threads), 7 z-marching tiles (full 27-point
- * union whose plane stride is a multiple of tile_rows; same shapes as 6);
- * tile_rows is ignored for 0, 2, 4, 5.  SPMV_EUNSUPPORTED when A has no
- * such kernel.
+ * union whose plane stride is a multiple of tile_rows; same shapes as 6),
+ * 8 register-staged tiles whose row records are copied to shared memory by
+ * cp.async (shapes as 6), 9 register-staged tiles reading one-byte row
+ * types instead of records -- the values registered in the pattern that
+ * Sec. V proposes; the first selection builds the types (at most 256
+ * distinct records) and copies them to the device (shapes as 6); tile_rows
+ * is ignored for 0, 2, 4, 5.  SPMV_EUNSUPPORTED when A has no such kernel.
  * Copies A to the device if it is not there yet. */
 int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 

@@ -48,7 +48,7 @@ class spmv_info_t(ctypes.Structure):
                 ("fast_eligible", _i32), ("n_slices", _i64), ("slices_value_raw", _i64), ("slices_col_raw", _i64),
                 ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64),
                 ("fast_tile_rows", _i32), ("fast_variant", _i32), ("fast_block_threads", _i32),
-                ("reserved0", _i32)]
+                ("row_types", _i32)]
 
 
 class spmv_cg_opts(ctypes.Structure):

@@ -188,6 +188,9 @@ int ensure_device(spmv_mat_s* m) {
         std::memcpy(&v.mult_lo, tbl, 4);
         std::memcpy(&v.mult_hi, tbl + 4, 4);
         v.mult_exp = p.mult_exp;
+        v.rtype = nullptr;              // row types are uploaded on request (variant 9)
+        v.rtypes = nullptr;
+        v.ntypes = 0;
         v.err = m->d_err;
         // the dominant record (most frequent; its slots must all be present)
         v.dom_ok = 0;
@@ -282,7 +285,9 @@ int ensure_device(spmv_mat_s* m) {
         }
         if (m->fast_variant == 7 && !m->zplan_ok) m->fast_variant = 1;
         if ((m->fast_variant == 4 || m->fast_variant == 5) && !m->async_ok) m->fast_variant = 2;
-        if (m->fast_variant == 6 && !(m->stage_ok && rstage_supported(m->stage))) m->fast_variant = 1;
+        if (m->fast_variant == 9) m->fast_variant = 6;   // row types are built on request only
+        if ((m->fast_variant == 6 || m->fast_variant == 8) && !(m->stage_ok && rstage_supported(m->stage)))
+            m->fast_variant = 1;
         if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
         if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
     } else if (m->fmt == SPMV_FMT_DIT) {
@@ -477,6 +482,7 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->fast_variant = A->device >= 0 ? A->fast_variant : -1;
         out->fast_block_threads = A->fast_variant == 7 && A->zplan_ok ? A->zplan.threads
                                   : A->stage_ok ? A->stage.rows / A->stage.rows_per_thread : 0;
+        out->row_types = static_cast<int32_t>(A->pat.rtypes.size() / 8);
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
@@ -572,7 +578,9 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
             : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                            A->xfixed_guard, s)
             : A->fast_variant == 7 ? launch_pattern_fast_zmarch(A->pat_view, A->zplan, x, y, A->d_scratch_words, s)
-            : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, s)
+            : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 0, s)
+            : A->fast_variant == 8 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 1, s)
+            : A->fast_variant == 9 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 2, s)
             : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
                                    : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
     else if (A->fmt == SPMV_FMT_DIT) e = launch_dit_f64(A->dit_view, x, y, s);
@@ -687,8 +695,10 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
             }
             for (std::pair<int, int> sh : {std::make_pair(256, 4), std::make_pair(256, 2), std::make_pair(512, 2)}) {
                 StagePlan plan;
-                if (make_stage_plan(A->pat.uoff, sh.second, sh.first, 12288, &plan) && rstage_supported(plan))
+                if (make_stage_plan(A->pat.uoff, sh.second, sh.first, 12288, &plan) && rstage_supported(plan)) {
                     cands.push_back(Cand{6, plan, {}});
+                    cands.push_back(Cand{8, plan, {}});
+                }
             }
             for (std::pair<int, int> sh : {std::make_pair(256, 2), std::make_pair(256, 4), std::make_pair(512, 2)}) {
                 ZPlan zp;
@@ -707,7 +717,8 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     for (const Cand& c : cands) {
         auto launch = [&]() {
             if (c.variant == 4) return launch_pattern_fast_async(A->pat_view, c.plan, x, y, A->num_sms, nullptr);
-            if (c.variant == 6) return launch_pattern_fast_rstaged(A->pat_view, c.plan, x, y, nullptr);
+            if (c.variant == 6) return launch_pattern_fast_rstaged(A->pat_view, c.plan, x, y, 0, nullptr);
+            if (c.variant == 8) return launch_pattern_fast_rstaged(A->pat_view, c.plan, x, y, 1, nullptr);
             if (c.variant == 7)
                 return launch_pattern_fast_zmarch(A->pat_view, c.zplan, x, y, A->d_scratch_words, nullptr);
             if (c.variant == 5)
@@ -732,7 +743,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     A->fast_variant = pick.variant;
-    const bool staged_pick = pick.variant == 1 || pick.variant == 3 || pick.variant == 6;
+    const bool staged_pick = pick.variant == 1 || pick.variant == 3 || pick.variant == 6 || pick.variant == 8;
     if (staged_pick) A->stage = pick.plan;
     if (pick.variant == 4 || pick.variant == 5) A->async_plan = pick.plan;
     if (pick.variant == 7) {
@@ -782,14 +793,17 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
         A->fast_variant = 7;
         return SPMV_OK;
     }
-    if (variant != 1 && variant != 3 && variant != 6) return fail(SPMV_EINVAL, "variant must be 0..7");
+    if (variant != 1 && variant != 3 && variant != 6 && variant != 8 && variant != 9)
+        return fail(SPMV_EINVAL, "variant must be 0..9");
     const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
+    const bool rstaged = variant == 6 || variant == 8 || variant == 9;
     if (variant == 3 && !(A->d_xfixed && full27))
         return fail(SPMV_EUNSUPPORTED, "no staged pre-converted kernel for this union");
     if (!stage_supported(static_cast<int>(A->pat.uoff.size()))) return fail(SPMV_EUNSUPPORTED, "no staged kernel for this union size");
     if (block_threads != 512 && block_threads != 256) return fail(SPMV_EINVAL, "block_threads must be 256 or 512");
-    if (variant == 6 && !full27) return fail(SPMV_EUNSUPPORTED, "no register-staged kernel for this union");
-    if (block_threads == 256 && !((variant == 1 || variant == 6) && full27))
+    if (rstaged && !(full27 && A->pat_view.words == 7))
+        return fail(SPMV_EUNSUPPORTED, "no register-staged kernel for this union");
+    if (block_threads == 256 && !((variant == 1 || rstaged) && full27))
         return fail(SPMV_EUNSUPPORTED, "256-thread tiles exist for the full 27-point union only");
     const int rpt = tile_rows / block_threads;
     const bool shape_ok = tile_rows > 0 && tile_rows % block_threads == 0 &&
@@ -797,9 +811,21 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
     StagePlan plan;
     if (!shape_ok || !make_stage_plan(A->pat.uoff, rpt, block_threads, 12288, &plan))
         return fail(SPMV_EUNSUPPORTED, "tile does not fit shared memory (tile_rows 512, 1024 or 2048)");
-    if (variant == 6 && !rstage_supported(plan))
+    if (rstaged && !rstage_supported(plan))
         return fail(SPMV_EUNSUPPORTED, "register-staged kernel: tile_rows/threads 1024/256, 512/256 or 1024/512 "
                                        "with windows of at most 2*pairs*threads elements");
+    if (variant == 9 && !A->pat_view.rtype) {
+        // values registered in the pattern: the row types, built and uploaded once
+        if (!build_row_types(A->n, &A->pat))
+            return fail(SPMV_EUNSUPPORTED, "more than 256 distinct row records: no row types");
+        uint8_t* rt;
+        uint32_t* tt;
+        if ((st = dev_copy(A, A->pat.rtype.data(), A->pat.rtype.size(), &rt))) return st;
+        if ((st = dev_copy(A, A->pat.rtypes.data(), A->pat.rtypes.size(), &tt))) return st;
+        A->pat_view.rtype = rt;
+        A->pat_view.rtypes = tt;
+        A->pat_view.ntypes = static_cast<int32_t>(A->pat.rtypes.size() / 8);
+    }
     A->stage = plan;
     A->stage_ok = true;
     A->fast_variant = variant;

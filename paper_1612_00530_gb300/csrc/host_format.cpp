@@ -118,6 +118,32 @@ void derive_fast_order(int64_t n, PatternFormat* p) {
     p->fast_ok = worst < 1024;
 }
 
+// Values registered in the pattern (Sec. V): a row's whole record -- its
+// codes and its pattern number -- becomes one of at most 256 row types.
+bool build_row_types(int64_t n, PatternFormat* p) {
+    p->rtype.clear();
+    p->rtypes.clear();
+    if (p->words != 7) return false;
+    std::map<std::vector<uint32_t>, int> types;
+    std::vector<uint8_t> rtype(static_cast<size_t>(n));
+    std::vector<uint32_t> table;
+    std::vector<uint32_t> key(7);
+    for (int64_t r = 0; r < n; ++r) {
+        std::copy(&p->rec[static_cast<size_t>(r) * 7], &p->rec[static_cast<size_t>(r) * 7] + 7, key.begin());
+        auto it = types.find(key);
+        if (it == types.end()) {
+            if (types.size() == 256) return false;
+            it = types.emplace(key, static_cast<int>(types.size())).first;
+            table.insert(table.end(), key.begin(), key.end());
+            table.push_back(0u);                       // 8 words a type
+        }
+        rtype[r] = static_cast<uint8_t>(it->second);
+    }
+    p->rtype = std::move(rtype);
+    p->rtypes = std::move(table);
+    return true;
+}
+
 // -------------------------------------------------------------- pattern ---
 int compress_pattern(const Csr& a, int max_dict, PatternFormat* out) {
     const int64_t n = a.n;

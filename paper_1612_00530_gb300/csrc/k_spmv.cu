@@ -432,19 +432,26 @@ __device__ __forceinline__ void cp16_zfill(void* sdst, const void* gsrc, uint32_
 // thread's first row (loaded by the caller before the tile's barriers, when
 // that row exists); each row's loop issues the next row's record loads
 // before it sums, so record latency overlaps the previous row's work.
-template <int WORDS, int NU, int RPT, int RUN, int THREADS, typename Off, bool SREC = false>
+// Where a row's record comes from (RECS): 0 global memory, the next row's
+// record prefetched into registers (w holds the first row's on entry);
+// 1 the tile's record planes copied to shared memory (srec, srows rows);
+// 2 a one-byte row type indexing a table of distinct records in shared
+// memory (srec, 8 words a type; tfirst is the first row's type).
+template <int WORDS, int NU, int RPT, int RUN, int THREADS, typename Off, int RECS = 0>
 __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const int2* sx, const uint32_t* smask,
                                           int64_t r0, uint32_t emax, bool exact_path, double* __restrict__ y,
                                           uint32_t (&w)[kMaxRecordWords], const uint32_t* srec = nullptr,
-                                          int srows = 0) {
+                                          int srows = 0, uint32_t tfirst = 0) {
     const int tid = threadIdx.x;
+    uint32_t tcur = tfirst;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
         const int rl = tid + i * THREADS;
         const int64_t r = r0 + rl;
         if (r >= a.n) break;
         uint32_t wn[kMaxRecordWords];
-        if constexpr (SREC) {
+        uint32_t tnext = 0;
+        if constexpr (RECS == 1) {
             // the tile's records were copied to shared memory: words 0..3, 4..5, 6
             static_assert(WORDS == 7, "shared-memory records are laid out for 7 words");
             const uint4 v = reinterpret_cast<const uint4*>(srec)[rl];
@@ -452,6 +459,13 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
             w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
             w[4] = v2.x; w[5] = v2.y;
             w[6] = srec[6 * srows + rl];
+        } else if constexpr (RECS == 2) {
+            static_assert(WORDS == 7, "typed records are laid out for 7 words");
+            if (i + 1 < RPT && r + THREADS < a.n) tnext = __ldg(a.rtype + r + THREADS);
+            const uint4 v = reinterpret_cast<const uint4*>(srec)[2 * tcur];
+            const uint4 v2 = reinterpret_cast<const uint4*>(srec)[2 * tcur + 1];
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+            w[4] = v2.x; w[5] = v2.y; w[6] = v2.z;
         } else {
             if (i + 1 < RPT && r + THREADS < a.n) load_record<WORDS>(a, r + THREADS, wn);
         }
@@ -466,10 +480,11 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
                     acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
                 }
             y[r] = acc;
-            if (!SREC && i + 1 < RPT) {
+            if (RECS == 0 && i + 1 < RPT) {
 #pragma unroll
                 for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
             }
+            tcur = tnext;
             continue;
         }
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
@@ -528,10 +543,11 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
         y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
-        if (!SREC && i + 1 < RPT) {
+        if (RECS == 0 && i + 1 < RPT) {
 #pragma unroll
             for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
         }
+        tcur = tnext;
     }
 }
 
@@ -619,7 +635,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) pattern_fast_staged_k
 // own pairs to limbs and writes them to shared memory once.  Rows then sum
 // from shared memory as in the staged kernel.  x must be 16-byte aligned;
 // the plan must have three segments of at most 2*QS*THREADS elements each.
-template <int QS, int RPT, int THREADS, int MINB>
+template <int QS, int RPT, int THREADS, int MINB, int RECS>
 __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(PatternView a, StagePlan sp,
                                                                              const double* __restrict__ x,
                                                                              double* __restrict__ y) {
@@ -631,11 +647,16 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
     if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
     const uint4* __restrict__ x4 = reinterpret_cast<const uint4*>(x);
     const uint2* __restrict__ x2 = reinterpret_cast<const uint2*>(x);
-    // the tile's records (planes of 16, 8 and 4 bytes per row) go to shared
-    // memory behind the windows by cp.async, in flight during the staging;
-    // rows past n read as zero
     uint32_t* srec = reinterpret_cast<uint32_t*>(sx4 + sp.elems_padded / 2);
-    {
+    uint32_t w0[kMaxRecordWords];
+    uint32_t t0 = 0;
+    if constexpr (RECS == 0) {
+        // first row's record in flight during the staging
+        if (r0 + tid < a.n) load_record<7>(a, r0 + tid, w0);
+    } else if constexpr (RECS == 1) {
+        // the tile's records (planes of 16, 8 and 4 bytes per row) go to
+        // shared memory behind the windows by cp.async, in flight during the
+        // staging; rows past n read as zero
         const int64_t left = a.n - r0;             // rows of this tile that exist (>= 1)
         for (int c = tid; c < sp.rows; c += THREADS)
             cp16_zfill(srec + 4 * c, c < left ? static_cast<const void*>(a.p16a + r0 + c) : a.p16a,
@@ -651,8 +672,12 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
                        uint32_t(k) * 4u);
         }
         asm volatile("cp.async.commit_group;");
+    } else {
+        // the table of distinct records (8 words a type) behind the windows,
+        // and the first row's type
+        for (int i = tid; i < a.ntypes * 8; i += THREADS) srec[i] = __ldg(a.rtypes + i);
+        if (r0 + tid < a.n) t0 = __ldg(a.rtype + r0 + tid);
     }
-    uint32_t w0[kMaxRecordWords];
     // phase 1: every pair of the three windows this thread owns, in flight together
     uint4 b[3][QS];
 #pragma unroll
@@ -707,11 +732,11 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
             }
         }
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if constexpr (RECS == 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     auto off = [&](int u) { return sp.soff_padded[u]; };
-    tile_rows<7, 27, RPT, 3, THREADS, decltype(off), true>(a, off, reinterpret_cast<const int2*>(sx4), smask, r0,
-                                                           emax, exact_path, y, w0, srec, sp.rows);
+    tile_rows<7, 27, RPT, 3, THREADS, decltype(off), RECS>(a, off, reinterpret_cast<const int2*>(sx4), smask, r0,
+                                                           emax, exact_path, y, w0, srec, sp.rows, t0);
 }
 
 // ------------------------------------- FAST order, z-marching tiles ------
@@ -1735,16 +1760,20 @@ bool rstage_supported(const StagePlan& sp) {
 }
 
 cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
-                                        cudaStream_t s) {
+                                        int recs, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (!(a.run_len == 3 && a.nu == 27 && a.words == 7) || !rstage_supported(sp)) return cudaErrorNotSupported;
+    if (recs < 0 || recs > 2 || (recs == 2 && !(a.rtype && a.ntypes > 0 && a.ntypes <= 256)))
+        return cudaErrorInvalidValue;
     // the 16-byte loads need x itself 16-byte aligned: otherwise the staged
     // kernel on the same plan
     if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return launch_pattern_fast_staged(a, sp, x, y, s);
     const int threads = sp.rows / sp.rows_per_thread;
     const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
-    // converted windows, then the tile's records (28 bytes a row)
-    const size_t smem = size_t(sp.elems_padded) * sizeof(int2) + size_t(sp.rows) * 28;
+    // converted windows, then the tile's records (28 bytes a row) or the
+    // table of row types (32 bytes a type)
+    const size_t smem = size_t(sp.elems_padded) * sizeof(int2) +
+                        (recs == 1 ? size_t(sp.rows) * 28 : recs == 2 ? size_t(a.ntypes) * 32 : 0);
     auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e == cudaSuccess)
@@ -1754,9 +1783,16 @@ cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& s
         kernel<<<grid, threads, smem, s>>>(a, sp, x, y);
         return cudaGetLastError();
     };
-    if (threads == 256 && sp.rows_per_thread == 4) return go(pattern_fast_rstaged_kernel<3, 4, 256, 4>);
-    if (threads == 256 && sp.rows_per_thread == 2) return go(pattern_fast_rstaged_kernel<2, 2, 256, 5>);
-    return go(pattern_fast_rstaged_kernel<2, 2, 512, 2>);
+#define SPMVC_RSTAGED(QSV, RPTV, TV, MB)                                                           \
+    if (threads == TV && sp.rows_per_thread == RPTV)                                               \
+        return recs == 0 ? go(pattern_fast_rstaged_kernel<QSV, RPTV, TV, MB, 0>)                  \
+             : recs == 1 ? go(pattern_fast_rstaged_kernel<QSV, RPTV, TV, MB, 1>)                  \
+                         : go(pattern_fast_rstaged_kernel<QSV, RPTV, TV, MB, 2>);
+    SPMVC_RSTAGED(3, 4, 256, 4)
+    SPMVC_RSTAGED(2, 2, 256, 5)
+    SPMVC_RSTAGED(2, 2, 512, 2)
+#undef SPMVC_RSTAGED
+    return cudaErrorInvalidValue;
 }
 
 bool make_zplan(const std::vector<int32_t>& uoff, int64_t n, int rows_per_thread, int threads, int num_sms,

@@ -65,7 +65,14 @@ struct PatternFormat {
     int mult_exp = 0;
     std::vector<int32_t> mult;
     int64_t max_row_abs = 0;        // max over rows of sum |mult|
+    // values registered in the pattern (Sec. V): the distinct records as row
+    // types, built on demand; empty when there are more than 256
+    std::vector<uint8_t> rtype;     // n
+    std::vector<uint32_t> rtypes;   // ntypes x 8 words
 };
+// Builds p->rtype / p->rtypes from the records; false (and both left empty)
+// when the records take more than 256 distinct values or words != 7.
+bool build_row_types(int64_t n, PatternFormat* p);
 int compress_pattern(const Csr& a, int max_dict, PatternFormat* out);
 void derive_fast_order(int64_t n, PatternFormat* p);
 
@@ -139,6 +146,11 @@ struct PatternView {
     // dom_mc at the middle slot (displacement 0) and one value dom_mo at all
     // 26 others (a stencil with uniform neighbour weights)
     int32_t dom_uni, dom_mo, dom_mc;
+    // values registered in the pattern (Sec. V): a one-byte type per row
+    // indexing the table of distinct records (8 words a type, 7 used)
+    const uint8_t* rtype;
+    const uint32_t* rtypes;
+    int32_t ntypes;
     int32_t* err;                   // sticky device error word
 };
 
@@ -216,8 +228,10 @@ cudaError_t launch_pattern_fast_f64(const PatternView& a, const double* x, doubl
                                     uint32_t* xmax_word, cudaStream_t s);
 cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                        cudaStream_t s);
+// recs: 0 records from global memory (register prefetch), 1 record planes
+// staged in shared memory, 2 one-byte row types (a.rtype, a.rtypes)
 cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
-                                        cudaStream_t s);
+                                        int recs, cudaStream_t s);
 cudaError_t launch_pattern_fast_zmarch(const PatternView& a, const ZPlan& zp, const double* x, double* y,
                                        uint32_t* partial, cudaStream_t s);
 cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
@@ -289,6 +303,7 @@ struct spmv_mat_s {
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;
+    int32_t rstage_recs = 0;           // register-staged kernel: where records come from (0, 1, 2)
     int32_t fast_variant = 0;          // 0 direct, 1 staged, 2 pre-converted, 3 staged pre-converted,
                                        // 4 persistent double-buffered, 5 the same from the pre-converted copy
     int2* d_xfixed = nullptr;          // FAST order: fixed-point copy of x with guard zones

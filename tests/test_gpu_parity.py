@@ -341,10 +341,12 @@ def test_fast_variants_on_hpcg_grids():
                   (1, 2048, 256), (2, 0, 512), (3, 512, 512), (3, 1024, 512), (3, 2048, 512), (4, 0, 512), (5, 0, 512)]
         # register-staged tiles: three plane windows, each within the pairs the threads hold
         # and z-marching tiles: plane stride (here 3072) a multiple of the tile
-        rstaged = {(25, 25, 5): [(6, 512, 256)],
+        rstaged = {(25, 25, 5): [(6, 512, 256), (8, 512, 256), (9, 512, 256)],
                    (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512),
-                                  (7, 512, 256), (7, 1024, 256), (7, 1024, 512)]}
-        for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512), (7, 512, 256), (7, 1024, 256), (7, 1024, 512)]:
+                                  (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
+                                  (8, 512, 256), (8, 1024, 256), (9, 512, 256), (9, 1024, 256), (9, 1024, 512)]}
+        for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512), (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
+                         (8, 512, 256), (9, 1024, 256)]:
             if (v, t, bt) not in rstaged.get(g, []):
                 with pytest.raises(P.SpmvError):
                     P.spmv_set_tile(C, v, t, bt)
@@ -381,9 +383,11 @@ def test_fast_27_point_non_uniform_weights():
     y_ref = oracle.spmv(rowptr, col, val, x)
     scale = abs_row_sums(rowptr, col, val, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
-    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (2, 0, 512), (6, 1024, 256), (6, 512, 256)]:
+    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (2, 0, 512), (6, 1024, 256), (6, 512, 256), (8, 512, 256),
+                     (9, 1024, 256)]:
         P.spmv_set_tile(C, v, t, bt)
         check_fast(run(C, x), y_ref, scale)
+    assert P.spmv_info(C)["row_types"] == 27
     # plane stride 2048: the z-marching kernel on the same weights
     g = (32, 64, 6)
     rowptr, col, val = weighted_27_point_csr(g)
@@ -424,7 +428,8 @@ def test_fast_uniform_stencil_with_odd_rows():
     y_ref = oracle.spmv(rowptr, col, val, x)
     scale = abs_row_sums(rowptr, col, val, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
-    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (6, 1024, 256), (7, 512, 256), (7, 1024, 512)]:
+    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (6, 1024, 256), (7, 512, 256), (7, 1024, 512),
+                     (8, 512, 256), (9, 512, 256)]:
         P.spmv_set_tile(C, v, t, bt)
         check_fast(run(C, x), y_ref, scale)
 
@@ -491,7 +496,7 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
     cases = [((9, 7, 6), [(0, 0, 512), (1, 512, 512), (1, 2048, 512), (1, 1024, 256), (1, 2048, 256),
                           (2, 0, 512), (3, 1024, 512), (3, 2048, 512), (4, 0, 512), (5, 0, 512)]),
              # three separate plane windows per 512-row tile: the register-staged kernel
-             ((24, 24, 4), [(6, 512, 256), (1, 512, 256), (2, 0, 512)]),
+             ((24, 24, 4), [(6, 512, 256), (8, 512, 256), (9, 512, 256), (1, 512, 256), (2, 0, 512)]),
              # plane stride 2048: z-marching tiles
              ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512)])]
     for g, shapes in cases:
@@ -552,7 +557,8 @@ def test_fast_variant_persistent_many_tiles():
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x = spmv_inputs.uniform_vector(n, seed=13)
     for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512),
-                           (7, 512, 256), (7, 1024, 256), (7, 1024, 512)]:
+                           (7, 512, 256), (7, 1024, 256), (7, 1024, 512), (8, 1024, 256), (8, 512, 256),
+                           (9, 512, 256), (9, 1024, 512)]:
         P.spmv_set_tile(C, variant, t, bt)
         check_persistent(C, g, n, x)
 
