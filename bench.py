@@ -221,7 +221,24 @@ def run_suite(args):
                     "slices_value_raw_frac": ic["slices_value_raw"] / ic["n_slices"],
                     "slices_col_raw_frac": ic["slices_col_raw"] / ic["n_slices"]},
           "peak_gbs": peaks["hbm_gbs"], "order": "column (bit-exact)"})
-    del A, C, x, y
+    # the same matrix with locality reordering inside spmv_compress
+    t0 = time.perf_counter()
+    R = P.spmv_compress(A, reorder=True)
+    t_reorder = time.perf_counter() - t0
+    ir = P.spmv_info(R)
+    t_r = time_ms(lambda: P.spmv_apply(R, x, y), 200)
+    emit({"workload": "irregular_128^3_seed2_reordered", "rows": n, "nnz": nnz,
+          "reordered_delta": {"gflops": 2 * nnz / t_r / 1e6, "ms": t_r,
+                              "gbs": (ir["format_bytes"] + 16 * n + 40 * n) / t_r / 1e6,
+                              "format_bytes_per_nnz": ir["format_bytes"] / nnz, "dict_size": ir["dict_size"],
+                              "bandwidth": ir["bandwidth"], "bandwidth_unordered": ic["bandwidth"],
+                              "slices_value_raw_frac": ir["slices_value_raw"] / ir["n_slices"],
+                              "slices_col_raw_frac": ir["slices_col_raw"] / ir["n_slices"],
+                              "compress_seconds": t_reorder},
+          "speedup_vs_ell": t_ell / t_r, "speedup_vs_unordered_delta": t_d / t_r,
+          "note": "gbs counts the gather of x and scatter of y (40 B/row) around the product",
+          "order": "column order of the reordered matrix"})
+    del A, C, R, x, y
 
     # --- Table II's three layouts on 192^3: plain ELL ("Original"), the
     # pattern format and the Data+Index Table decoded as Listing 1
@@ -241,7 +258,25 @@ def run_suite(args):
                                "gbs": dit_bytes / t_dit / 1e6, "frac_of_hbm": dit_bytes / t_dit / 1e6 / peaks["hbm_gbs"],
                                "order": "Listing 1 (value groups ascending, fma per entry; bit-exact)"},
           "speedup_vs_ell": t_ell / t_dit, "peak_gbs": peaks["hbm_gbs"]})
-    del D, x, y
+    del D
+
+    # --- values registered in the pattern (Sec. V): one byte a row instead of
+    # the 28-byte record, same FAST kernel family, best tile shape
+    T = P.spmv_compress(A, format="pattern", order="fast")
+    best = None
+    for t, bt in ((1024, 256), (512, 256), (1024, 512)):
+        P.spmv_set_tile(T, 9, t, bt)
+        ms = time_ms(lambda: P.spmv_apply(T, x, y), 200)
+        if best is None or ms < best[0]:
+            best = (ms, t, bt)
+    it = P.spmv_info(T)
+    typed_bytes = n * 1 + 16 * n
+    emit({"workload": "hpcg_192^3_row_types", "rows": n, "nnz": nnz, "row_types": it["row_types"],
+          "gflops": 2 * nnz / best[0] / 1e6, "ms": best[0], "tile_rows": best[1], "threads": best[2],
+          "bytes_per_row": 1 + 16, "gbs": typed_bytes / best[0] / 1e6,
+          "frac_of_hbm": typed_bytes / best[0] / 1e6 / peaks["hbm_gbs"], "speedup_vs_ell": t_ell / best[0],
+          "order": "fast (<= 1e-14)"})
+    del T, x, y
 
     # --- CG vs IR-CG on 192^3, b = A 1, x0 = 0, tol 1e-10
     C = P.spmv_compress(A, format="pattern", order="fast")

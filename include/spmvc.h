@@ -114,6 +114,10 @@ typedef struct {
     int32_t max_dict;      /* largest value table, 1..254 (default 254 when 0) */
     int32_t min_count;     /* delta format: a value enters the table only if it
                               occurs at least this often (default 64 when 0) */
+    int32_t reorder;       /* 0: keep the numbering; 1: locality reordering
+                              (reverse Cuthill-McKee, table-coded rows ahead of
+                              the others inside each level), stored as
+                              B = P A P^T, products gather x and scatter y */
 } spmv_opts;
 
 /* Compresses plain matrix A into a new handle *out (A is unchanged and stays
@@ -133,6 +137,15 @@ typedef struct {
  * opts may be NULL (AUTO, COLUMN).  Errors: SPMV_EUNSUPPORTED when the
  * requested format cannot hold A. */
 int spmv_compress(spmv_mat_t A, const spmv_opts *opts, spmv_mat_t *out);
+
+/* The permutation of a handle compressed with reorder = 1: perm[new] = old
+ * for n entries (caller-owned host buffer).  The handle stores B = P A P^T;
+ * spmv_apply, spmv_apply_host, spmv_decompress and FP64 cg_solve still take
+ * and return A's numbering (a gather of x and a scatter of y around the
+ * product, two extra passes of 20 bytes a row); its products sum each row in
+ * B's column order.  SPMV_EINVAL when A is not reordered.  Reordered handles
+ * serve no binary32, SpMM, batch or stream call (SPMV_EUNSUPPORTED). */
+int spmv_permutation(spmv_mat_t A, int32_t *perm);
 
 /* Selects the summation order used by later spmv_apply/spmm_apply calls on a
  * pattern-format handle.  SPMV_ORDER_FAST needs every value to be a small
@@ -172,6 +185,9 @@ typedef struct {
                                    kernel (512 or 256; 0 = no staged kernel) */
     int32_t row_types;          /* pattern format: distinct row records held as
                                    one-byte row types (variant 9), else 0 */
+    int32_t reordered;          /* 1 if compressed with reorder = 1 */
+    int32_t reserved0;
+    int64_t bandwidth;          /* max |column - row| of the stored matrix */
 } spmv_info_t;
 
 /* Fills *out with the sizes and statistics of A (host only). */

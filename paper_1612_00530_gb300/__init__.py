@@ -10,7 +10,7 @@ The functions keep the C names: spmv_build, spmv_build_csr, spmv_compress,
 spmv_set_order, spmv_info, spmv_decompress, spmv_export, spmv_import,
 spmv_apply, spmv_apply_host, spmv_apply_f32, spmm_apply, spmv_batch_create,
 spmv_batch_launch, spmv_batch_free, spmv_apply_batched, cg_solve,
-spmv_device_error, spmv_autotune, spmv_set_variant, spmv_set_tile,
+spmv_device_error, spmv_autotune, spmv_set_variant, spmv_set_tile, spmv_permutation,
 spmm_apply_noalloc, spmv_version.
 """
 from __future__ import annotations
@@ -39,7 +39,7 @@ class spmv_gen_desc(ctypes.Structure):
 
 
 class spmv_opts(ctypes.Structure):
-    _fields_ = [("format", _i32), ("order", _i32), ("max_dict", _i32), ("min_count", _i32)]
+    _fields_ = [("format", _i32), ("order", _i32), ("max_dict", _i32), ("min_count", _i32), ("reorder", _i32)]
 
 
 class spmv_info_t(ctypes.Structure):
@@ -48,7 +48,7 @@ class spmv_info_t(ctypes.Structure):
                 ("fast_eligible", _i32), ("n_slices", _i64), ("slices_value_raw", _i64), ("slices_col_raw", _i64),
                 ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64),
                 ("fast_tile_rows", _i32), ("fast_variant", _i32), ("fast_block_threads", _i32),
-                ("row_types", _i32)]
+                ("row_types", _i32), ("reordered", _i32), ("reserved0", _i32), ("bandwidth", _i64)]
 
 
 class spmv_cg_opts(ctypes.Structure):
@@ -81,6 +81,7 @@ def library() -> ctypes.CDLL:
             "spmv_build": [ctypes.POINTER(spmv_gen_desc), ctypes.POINTER(_p)],
             "spmv_build_csr": [_i64, _p, _p, _p, ctypes.POINTER(_p)],
             "spmv_compress": [_p, ctypes.POINTER(spmv_opts), ctypes.POINTER(_p)],
+            "spmv_permutation": [_p, _p],
             "spmv_set_order": [_p, _i32],
             "spmv_info": [_p, ctypes.POINTER(spmv_info_t)],
             "spmv_decompress": [_p, _p, _p, _p],
@@ -171,9 +172,16 @@ def spmv_build_csr(rowptr, col, val) -> SpmvMatrix:
 
 
 def spmv_compress(A: SpmvMatrix, format: str = "auto", order: str = "column", max_dict: int = 254,
-                  min_count: int = 64) -> SpmvMatrix:
-    o = spmv_opts(FORMATS[format], ORDERS[order], max_dict, min_count)
+                  min_count: int = 64, reorder: bool = False) -> SpmvMatrix:
+    o = spmv_opts(FORMATS[format], ORDERS[order], max_dict, min_count, 1 if reorder else 0)
     return _new(library().spmv_compress, A, ctypes.byref(o))
+
+
+def spmv_permutation(A: SpmvMatrix) -> np.ndarray:
+    """perm[new] = old of a handle compressed with reorder=True."""
+    perm = np.zeros(max(spmv_info(A)["n"], 1), np.int32)
+    _check(library().spmv_permutation(A, perm.ctypes.data))
+    return perm[: spmv_info(A)["n"]]
 
 
 def spmv_set_order(A: SpmvMatrix, order: str) -> None:

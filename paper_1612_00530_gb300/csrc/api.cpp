@@ -122,6 +122,11 @@ int ensure_device(spmv_mat_s* m) {
     std::vector<uint32_t> zeros(kPartialWords, 0u);
     if ((st = dev_copy(m, zeros.data(), zeros.size(), &m->d_scratch_words))) return st;
     m->scratch_words = kPartialWords;
+    if (!m->perm.empty()) {
+        if ((st = dev_copy(m, m->perm.data(), m->perm.size(), &m->d_perm))) return st;
+        if ((st = dev_copy<double>(m, nullptr, static_cast<size_t>(m->n), &m->d_xp))) return st;
+        if ((st = dev_copy<double>(m, nullptr, static_cast<size_t>(m->n), &m->d_yp))) return st;
+    }
     if (m->fmt == SPMV_FMT_ELL) {
         EllView& v = m->ell_view;
         v.n = m->n;
@@ -348,8 +353,12 @@ void stats_from_csr(spmv_mat_s* m, const Csr& c) {
     m->n = c.n;
     m->nnz = c.nnz();
     m->max_row_nnz = 0;
-    for (int64_t i = 0; i < c.n; ++i)
+    m->bandwidth = 0;
+    for (int64_t i = 0; i < c.n; ++i) {
         m->max_row_nnz = std::max<int32_t>(m->max_row_nnz, static_cast<int32_t>(c.rowptr[i + 1] - c.rowptr[i]));
+        for (int64_t k = c.rowptr[i]; k < c.rowptr[i + 1]; ++k)
+            m->bandwidth = std::max<int64_t>(m->bandwidth, c.col[k] > i ? c.col[k] - i : i - c.col[k]);
+    }
 }
 
 int finish_plain(spmv_mat_s* m, spmv_mat_t* out) {
@@ -362,7 +371,8 @@ int finish_plain(spmv_mat_s* m, spmv_mat_t* out) {
     return SPMV_OK;
 }
 
-int to_csr(spmv_mat_s* a, Csr* c) {
+// The stored matrix as CSR (B = P A P^T for a reordered handle).
+int stored_csr(spmv_mat_s* a, Csr* c) {
     if (a->fmt == SPMV_FMT_ELL && a->csr.n == a->n && !a->csr.rowptr.empty()) {
         *c = a->csr;
         return SPMV_OK;
@@ -373,7 +383,43 @@ int to_csr(spmv_mat_s* a, Csr* c) {
     return decompress_delta(a->n, a->dlt, c);
 }
 
+// A itself, in its own numbering.
+int to_csr(spmv_mat_s* a, Csr* c) {
+    int st = stored_csr(a, c);
+    if (st || a->perm.empty()) return st;
+    Csr orig;
+    unpermute_csr(*c, a->perm, &orig);
+    *c = std::move(orig);
+    return SPMV_OK;
+}
+
 cudaStream_t as_stream(spmv_stream_t s) { return static_cast<cudaStream_t>(s); }
+
+// The stored matrix's product on device vectors (no permutation).
+int apply_stored(spmv_mat_s* A, const double* x, double* y, cudaStream_t s) {
+    cudaError_t e;
+    if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
+    else if (A->fmt == SPMV_FMT_PATTERN)
+        e = A->order != SPMV_ORDER_FAST ? launch_pattern_col_f64(A->pat_view, x, y, s)
+            : A->fast_variant == 5 ? launch_pattern_fast_async_x(A->pat_view, A->async_plan, x, y, A->d_scratch_words,
+                                                                 A->d_xfixed, A->xfixed_guard, A->num_sms, s)
+            : A->fast_variant == 4 ? launch_pattern_fast_async(A->pat_view, A->async_plan, x, y, A->num_sms, s)
+            : A->fast_variant == 3 ? launch_pattern_fast_xstaged(A->pat_view, A->stage, x, y, A->d_scratch_words,
+                                                                 A->d_xfixed, A->xfixed_guard, s)
+            : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
+                                                           A->xfixed_guard, s)
+            : A->fast_variant == 7 ? launch_pattern_fast_zmarch(A->pat_view, A->zplan, x, y, A->d_scratch_words, s)
+            : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 0, s)
+            : A->fast_variant == 8 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 1, s)
+            : A->fast_variant == 9 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 2, s)
+            : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
+                                   : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
+    else if (A->fmt == SPMV_FMT_DIT) e = launch_dit_f64(A->dit_view, x, y, s);
+    else e = launch_delta_f64(A->dlt_view, x, y, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
+    return SPMV_OK;
+}
+
 
 }  // namespace
 }  // namespace spmvc
@@ -408,8 +454,9 @@ int spmv_build_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const d
 
 int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
-    spmv_opts o{SPMV_FMT_AUTO, SPMV_ORDER_COLUMN, 254, 64};
+    spmv_opts o{SPMV_FMT_AUTO, SPMV_ORDER_COLUMN, 254, 64, 0};
     if (opts) o = *opts;
+    if (o.reorder != 0 && o.reorder != 1) return fail(SPMV_EINVAL, "reorder must be 0 or 1");
     if (o.max_dict <= 0) o.max_dict = 254;
     if (o.min_count <= 0) o.min_count = 64;
     if (o.max_dict > 254) return fail(SPMV_EINVAL, "max_dict above 254");
@@ -419,8 +466,19 @@ int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
     Csr c;
     int st = to_csr(A, &c);
     if (st) return st;
+    std::vector<int32_t> perm;
+    if (o.reorder) {
+        // B = P A P^T: reverse Cuthill-McKee with table-coded rows clustered
+        std::vector<double> dict;
+        delta_dictionary(c.val, o.max_dict, o.min_count, &dict);
+        if ((st = reorder_rcm(c, dict, &perm))) return st;
+        Csr b;
+        permute_csr(c, perm, &b);
+        c = std::move(b);
+    }
     spmv_mat_s* m;
     if ((st = new_handle(out, &m))) return st;
+    m->perm = std::move(perm);
     stats_from_csr(m, c);
     st = SPMV_EUNSUPPORTED;
     if (o.format == SPMV_FMT_DIT) {
@@ -466,6 +524,8 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
     out->order = A->order;
     out->max_row_nnz = A->max_row_nnz;
     out->checksum = A->checksum;
+    out->reordered = A->perm.empty() ? 0 : 1;
+    out->bandwidth = A->bandwidth;
     if (A->fmt == SPMV_FMT_ELL) {
         out->n_slices = A->ell.nslices;
         out->format_bytes = static_cast<int64_t>(A->ell.val.size() * 12 + A->ell.slice_off.size() * 8 +
@@ -518,11 +578,7 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
 int spmv_decompress(spmv_mat_t A, int64_t* rowptr, int32_t* col, double* val) {
     if (!valid(A) || !rowptr || (A->nnz > 0 && (!col || !val))) return fail(SPMV_EINVAL, "invalid argument");
     Csr c;
-    int st;
-    if (A->fmt == SPMV_FMT_ELL) st = decompress_ell(A->n, A->ell, &c);
-    else if (A->fmt == SPMV_FMT_PATTERN) st = decompress_pattern(A->n, A->pat, &c);
-    else if (A->fmt == SPMV_FMT_DIT) st = decompress_dit(A->n, A->dit, &c);
-    else st = decompress_delta(A->n, A->dlt, &c);
+    int st = to_csr(A, &c);
     if (st) return st;
     if (c.nnz() != A->nnz) return fail(SPMV_ECORRUPT, "decompressed nonzero count differs");
     std::memcpy(rowptr, c.rowptr.data(), sizeof(int64_t) * (A->n + 1));
@@ -535,6 +591,7 @@ int spmv_decompress(spmv_mat_t A, int64_t* rowptr, int32_t* col, double* val) {
 
 int spmv_export(spmv_mat_t A, void* buf, size_t* len) {
     if (!valid(A) || !len) return fail(SPMV_EINVAL, "invalid argument");
+    if (!A->perm.empty()) return fail(SPMV_EUNSUPPORTED, "a reordered handle has no stream form");
     return export_stream(*A, buf, len);
 }
 
@@ -567,25 +624,24 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
     if (st) return st;
     cudaError_t e;
     const cudaStream_t s = as_stream(stream);
-    if (A->fmt == SPMV_FMT_ELL) e = launch_ell_f64(A->ell_view, x, y, s);
-    else if (A->fmt == SPMV_FMT_PATTERN)
-        e = A->order != SPMV_ORDER_FAST ? launch_pattern_col_f64(A->pat_view, x, y, s)
-            : A->fast_variant == 5 ? launch_pattern_fast_async_x(A->pat_view, A->async_plan, x, y, A->d_scratch_words,
-                                                                 A->d_xfixed, A->xfixed_guard, A->num_sms, s)
-            : A->fast_variant == 4 ? launch_pattern_fast_async(A->pat_view, A->async_plan, x, y, A->num_sms, s)
-            : A->fast_variant == 3 ? launch_pattern_fast_xstaged(A->pat_view, A->stage, x, y, A->d_scratch_words,
-                                                                 A->d_xfixed, A->xfixed_guard, s)
-            : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
-                                                           A->xfixed_guard, s)
-            : A->fast_variant == 7 ? launch_pattern_fast_zmarch(A->pat_view, A->zplan, x, y, A->d_scratch_words, s)
-            : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 0, s)
-            : A->fast_variant == 8 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 1, s)
-            : A->fast_variant == 9 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 2, s)
-            : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
-                                   : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
-    else if (A->fmt == SPMV_FMT_DIT) e = launch_dit_f64(A->dit_view, x, y, s);
-    else e = launch_delta_f64(A->dlt_view, x, y, s);
-    if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
+    if (!A->perm.empty() && A->n > 0) {
+        // reordered: xp = P x, yp = B xp, y = P^T yp
+        if ((e = launch_gather(A->d_perm, A->n, x, A->d_xp, s)) != cudaSuccess) return cuda_fail(e, "gather launch");
+        x = A->d_xp;
+        double* const y_user = y;
+        y = A->d_yp;
+        st = apply_stored(A, x, y, s);
+        if (st) return st;
+        if ((e = launch_scatter(A->d_perm, A->n, A->d_yp, y_user, s)) != cudaSuccess) return cuda_fail(e, "scatter launch");
+        return SPMV_OK;
+    }
+    return apply_stored(A, x, y, s);
+}
+
+int spmv_permutation(spmv_mat_t A, int32_t* perm) {
+    if (!valid(A) || (A->n > 0 && !perm)) return fail(SPMV_EINVAL, "invalid argument");
+    if (A->perm.empty()) return fail(SPMV_EINVAL, "the handle is not reordered");
+    std::memcpy(perm, A->perm.data(), sizeof(int32_t) * A->perm.size());
     return SPMV_OK;
 }
 
@@ -610,6 +666,7 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
 int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no binary32 product for the Data+Index Table format");
+    if (!A->perm.empty()) return fail(SPMV_EUNSUPPORTED, "no binary32 product for a reordered handle");
     if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
     int st = ensure_device(A);
     if (st) return st;
@@ -637,6 +694,7 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y,
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (k < 1 || k > 64 || ldx < k || ldy < k) return fail(SPMV_EINVAL, "need 1 <= k <= 64, ldx >= k, ldy >= k");
     if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no SpMM for the Data+Index Table format");
+    if (!A->perm.empty()) return fail(SPMV_EUNSUPPORTED, "no SpMM for a reordered handle");
     if (A->n > 0 && (!X || !Y)) return fail(SPMV_EINVAL, "null block");
     int st = ensure_device(A);
     if (st) return st;

@@ -269,17 +269,16 @@ int compress_dit(const Csr& a, DitFormat* out) {
 }
 
 // ---------------------------------------------------------------- delta ---
-int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) {
-    const int64_t n = a.n;
+// The delta format's value table: the most frequent values with at least
+// min_count uses, at most max_dict of them, in ascending order.
+void delta_dictionary(const std::vector<double>& val, int max_dict, int min_count, std::vector<double>* dict) {
     std::unordered_map<uint64_t, int64_t> counts;
     std::vector<double> all;
-    int st = value_table(a.val, &all, &counts);
-    if (st) {
+    if (value_table(val, &all, &counts)) {
         // NaN values: no table at all, every slice raw
         all.clear();
         counts.clear();
     }
-    // the table keeps the most frequent values (at least min_count uses)
     std::vector<std::pair<int64_t, double>> freq;
     for (double v : all) {
         const int64_t c = counts[bits_of(v)];
@@ -290,12 +289,17 @@ int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) 
         return x.second < y.second;
     });
     if (static_cast<int>(freq.size()) > max_dict) freq.resize(max_dict);
-    out->dict.clear();
-    for (const auto& f : freq) out->dict.push_back(f.second);
-    std::sort(out->dict.begin(), out->dict.end(), [](double x, double y) {
+    dict->clear();
+    for (const auto& f : freq) dict->push_back(f.second);
+    std::sort(dict->begin(), dict->end(), [](double x, double y) {
         if (x != y) return x < y;
         return std::signbit(x) > std::signbit(y);
     });
+}
+
+int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) {
+    const int64_t n = a.n;
+    delta_dictionary(a.val, max_dict, min_count, &out->dict);
     std::unordered_map<uint64_t, int> code_of;
     for (size_t v = 0; v < out->dict.size(); ++v) code_of[bits_of(out->dict[v])] = static_cast<int>(v);
 

@@ -142,7 +142,8 @@ int spmv_batch_create(int32_t count, const spmv_mat_t* mats, const double* const
     for (int32_t b = 0; b < count; ++b) {
         spmv_mat_s* m = mats[b];
         if (!api_valid(m)) return fail(SPMV_EINVAL, "invalid matrix handle in batch");
-        if (m->fmt != SPMV_FMT_PATTERN) return fail(SPMV_EUNSUPPORTED, "batches take pattern-format matrices");
+        if (m->fmt != SPMV_FMT_PATTERN || !m->perm.empty())
+            return fail(SPMV_EUNSUPPORTED, "batches take pattern-format matrices in their own numbering");
         if (words >= 0 && m->pat.words != words) return fail(SPMV_EUNSUPPORTED, "batch records must have equal size");
         if (m->n > 0 && (!xs[b] || !ys[b])) return fail(SPMV_EINVAL, "null vector in batch");
         words = m->pat.words;

@@ -60,8 +60,8 @@ extern "C" int spmm_apply_noalloc(spmv_mat_t A, int32_t k, const double* X, int6
                                         "(the size of its static scratch)");
     if (ldx < k || ldy < k) return spmvc::fail(SPMV_EINVAL, "need ldx >= k and ldy >= k");
     if (A->n > 0 && (!X || !Y)) return spmvc::fail(SPMV_EINVAL, "null block");
-    if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST)
-        return spmvc::fail(SPMV_EUNSUPPORTED, "spmm_apply_noalloc needs a pattern-format matrix in FAST order");
+    if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || !A->perm.empty())
+        return spmvc::fail(SPMV_EUNSUPPORTED, "spmm_apply_noalloc needs a pattern-format matrix in FAST order, not reordered");
     int dev = 0;
     cudaGetDevice(&dev);
     if (A->device < 0 || A->device != dev)

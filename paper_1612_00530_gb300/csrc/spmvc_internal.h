@@ -93,6 +93,15 @@ struct DeltaFormat {
     std::vector<uint8_t> payload;
 };
 int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out);
+void delta_dictionary(const std::vector<double>& val, int max_dict, int min_count, std::vector<double>* dict);
+
+// Locality reordering (host_reorder.cpp): reverse Cuthill-McKee over the
+// matrix graph, then inside each breadth-first level the rows whose values
+// all sit in the value table ahead of the others, so that table-coded slices
+// and raw-value slices cluster.  perm[new] = old.
+int reorder_rcm(const Csr& a, const std::vector<double>& dict, std::vector<int32_t>* perm);
+void permute_csr(const Csr& a, const std::vector<int32_t>& perm, Csr* out);      // P A P^T
+void unpermute_csr(const Csr& b, const std::vector<int32_t>& perm, Csr* out);    // P^T B P
 
 // The "Data+Index Table" of Sec. V as Listing 1 reads it: the value table V;
 // for every row its type, the number of a registered list of column
@@ -245,6 +254,9 @@ cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double*
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s);
+// k_perm.cu: xp[i] = x[perm[i]] and y[perm[i]] = yp[i]
+cudaError_t launch_gather(const int32_t* perm, int64_t n, const double* x, double* xp, cudaStream_t s);
+cudaError_t launch_scatter(const int32_t* perm, int64_t n, const double* yp, double* y, cudaStream_t s);
 cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s);
 // SpMM (k right-hand sides, row-major).
 cudaError_t launch_pattern_spmm_col(const PatternView& a, int k, const double* X, int64_t ldx,
@@ -281,7 +293,14 @@ struct spmv_mat_s {
     int32_t order = SPMV_ORDER_COLUMN;
     int64_t n = 0, nnz = 0;
     int32_t max_row_nnz = 0;
+    int64_t bandwidth = 0;              // max |column - row| of the stored matrix
     spmvc::Csr csr;                     // plain handles keep the CSR
+    // locality reordering: the stored matrix is P A P^T with perm[new] = old
+    // (empty: not reordered); products gather x and scatter y around it
+    std::vector<int32_t> perm;
+    int32_t* d_perm = nullptr;
+    double* d_xp = nullptr;
+    double* d_yp = nullptr;
     spmvc::EllFormat ell;
     spmvc::PatternFormat pat;
     spmvc::DeltaFormat dlt;

@@ -641,3 +641,74 @@ def test_data_index_table_cg():
     r = P.cg_solve(D, b, x, tol=1e-10, max_iter=500, mode="fp64")
     assert r["status"] == 0 and r["rel_residual"] <= 1e-10
     assert float((x - 1).abs().max()) < 1e-8
+
+
+def permuted_csr(rowptr, col, val, perm):
+    """P A P^T with perm[new] = old, columns ascending (numpy, test side)."""
+    n = len(rowptr) - 1
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    lens = np.diff(rowptr)[perm]
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    c2 = np.empty_like(col)
+    v2 = np.empty_like(val)
+    for i in range(n):
+        o = perm[i]
+        cs = inv[col[rowptr[o]:rowptr[o + 1]]]
+        order = np.argsort(cs, kind="stable")
+        c2[rp[i]:rp[i + 1]] = cs[order]
+        v2[rp[i]:rp[i + 1]] = val[rowptr[o]:rowptr[o + 1]][order]
+    return rp, c2, v2
+
+
+def test_reordered_delta_product():
+    """Reordered irregular matrix: y = P^T (B (P x)) is bit-identical to the
+    oracle's CSR product of B = P A P^T on P x and within 1e-14 of A x,
+    through device and host buffers and FP64 CG."""
+    g = (24, 24, 24)
+    rowptr, col, val, _ = oracle.irregular_csr(*g, seed=2)
+    n = len(rowptr) - 1
+    C = P.spmv_compress(P.spmv_build("irregular", *g, seed=2), format="delta", reorder=True)
+    perm = P.spmv_permutation(C)
+    rp, c2, v2 = permuted_csr(rowptr, col, val, perm)
+    x = spmv_inputs.uniform_vector(n, seed=41)
+    y = run(C, x)
+    yb = np.empty(n)
+    yb[perm] = oracle.spmv(rp, c2, v2, x[perm])
+    assert np.array_equal(y.view(np.uint64), yb.view(np.uint64))
+    check_fast(y, oracle.spmv(rowptr, col, val, x), abs_row_sums(rowptr, col, val, x))
+    yh = np.zeros(n)
+    P.spmv_apply_host(C, np.ascontiguousarray(x), yh)
+    assert np.array_equal(yh, y)
+    ones = torch.ones(n, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    P.spmv_apply(C, ones, b)
+    xs = torch.zeros_like(ones)
+    r = P.cg_solve(C, b, xs, tol=1e-10, max_iter=2000, mode="fp64")
+    assert r["status"] == 0 and float((xs - 1).abs().max()) < 1e-7
+    for call in (lambda: P.spmv_apply_f32(C, torch.zeros(n, dtype=torch.float32, device="cuda"),
+                                          torch.zeros(n, dtype=torch.float32, device="cuda")),
+                 lambda: P.spmm_apply(C, torch.zeros(n, 2, dtype=torch.float64, device="cuda"),
+                                      torch.zeros(n, 2, dtype=torch.float64, device="cuda"))):
+        with pytest.raises(P.SpmvError):
+            call()
+
+
+def test_reordered_dit_and_delta_products():
+    """Reordering composes with the Data+Index Table and delta formats; it
+    breaks a grid's displacement patterns, so the pattern format refuses a
+    reordered grid of any size."""
+    g = (4, 4, 4)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    A = P.spmv_build("hpcg", *g)
+    x = spmv_inputs.uniform_vector(n, seed=43)
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    scale = abs_row_sums(rowptr, col, val, x)
+    for fmt in ("dit", "delta"):
+        C = P.spmv_compress(A, format=fmt, reorder=True)
+        check_fast(run(C, x), y_ref, scale)
+        got = P.spmv_decompress(C)
+        assert all(np.array_equal(u, v) for u, v in zip(got, (rowptr, col, val)))
+    with pytest.raises(P.SpmvError):
+        P.spmv_compress(P.spmv_build("hpcg", 12, 10, 9), format="pattern", reorder=True)

@@ -217,3 +217,32 @@ def test_data_index_table_signed_zeros_and_refusals():
         P.spmv_export(D)
     with pytest.raises(P.SpmvError):
         P.spmv_set_order(D, "fast")
+
+
+@pytest.mark.parametrize("g,seed", [((8, 8, 8), 2), ((16, 16, 16), 5)])
+def test_reorder_round_trip_and_locality(g, seed):
+    """Locality reordering inside spmv_compress: a permutation, the exact
+    original matrix back from decompress, a narrower band, and fewer
+    raw-value slices than the random numbering gives."""
+    A = P.spmv_build("irregular", *g, seed=seed)
+    C0 = P.spmv_compress(A, format="delta")
+    C = P.spmv_compress(A, format="delta", reorder=True)
+    n = P.spmv_info(C)["n"]
+    perm = P.spmv_permutation(C)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    assert same_csr(P.spmv_decompress(C), P.spmv_decompress(A))
+    i0, i1 = P.spmv_info(C0), P.spmv_info(C)
+    assert i1["reordered"] == 1 and i0["reordered"] == 0
+    assert i1["bandwidth"] < i0["bandwidth"] / 2
+    assert i1["slices_value_raw"] < i0["slices_value_raw"]
+    assert i1["format_bytes"] < i0["format_bytes"]
+    # the stored matrix is P A P^T: its band is what info reports
+    rowptr, col, val = P.spmv_decompress(A)
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    assert np.abs(inv[col] - inv[rows]).max() == i1["bandwidth"]
+    with pytest.raises(P.SpmvError):
+        P.spmv_export(C)
+    with pytest.raises(P.SpmvError):
+        P.spmv_permutation(C0)
