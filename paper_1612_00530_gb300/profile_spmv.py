@@ -1,6 +1,6 @@
 """Runs SpMV steps on one HPCG matrix for profiling (ncu launch lists and
 kernel captures): python -m paper_1612_00530_gb300.profile_spmv
-[--grid N] [--format ell|pattern|delta] [--order column|fast] [--steps K]
+[--grid N] [--format ell|pattern|delta|dit] [--reorder] [--order column|fast] [--steps K]
 [--warmup W] [--variant V --tile T --threads B].  Prints the mean step time measured with CUDA events."""
 from __future__ import annotations
 
@@ -15,7 +15,8 @@ import spmv_inputs
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", type=int, default=192)
-    ap.add_argument("--format", default="pattern", choices=("ell", "pattern", "delta"))
+    ap.add_argument("--format", default="pattern", choices=("ell", "pattern", "delta", "dit"))
+    ap.add_argument("--reorder", action="store_true", help="locality reordering inside spmv_compress")
     ap.add_argument("--order", default="fast", choices=("column", "fast"))
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -31,7 +32,8 @@ def main():
     args = ap.parse_args()
     g = args.grid
     A = P.spmv_build(args.kind, g, g, g, seed=2)
-    M = A if args.format == "ell" else P.spmv_compress(A, format=args.format, order=args.order)
+    M = A if args.format == "ell" else P.spmv_compress(A, format=args.format, order=args.order,
+                                                       reorder=args.reorder)
     n = P.spmv_info(M)["n"]
     x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=1)).cuda()
     y = torch.empty_like(x)
