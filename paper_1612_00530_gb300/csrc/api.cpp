@@ -74,6 +74,11 @@ void free_device(spmv_mat_s* m) {
     m->dev_allocs.clear();
     if (m->own_stream) cudaStreamDestroy(m->own_stream);
     m->own_stream = nullptr;
+    if (m->h2d_stream) cudaStreamDestroy(m->h2d_stream);
+    if (m->d2h_stream) cudaStreamDestroy(m->d2h_stream);
+    m->h2d_stream = m->d2h_stream = nullptr;
+    for (cudaEvent_t e : m->host_events) cudaEventDestroy(e);
+    m->host_events.clear();
     m->device = -1;
     m->d_ell_val32 = nullptr;
     m->d_hx = m->d_hy = nullptr;
@@ -656,10 +661,61 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
         if ((st = dev_copy<double>(A, nullptr, A->n, &A->d_hy))) return st;
     }
     const size_t bytes = sizeof(double) * A->n;
-    SPMVC_CUDA(cudaMemcpyAsync(A->d_hx, x, bytes, cudaMemcpyHostToDevice, A->own_stream));
-    if ((st = spmv_apply(A, A->d_hx, A->d_hy, A->own_stream))) return st;
-    SPMVC_CUDA(cudaMemcpyAsync(y, A->d_hy, bytes, cudaMemcpyDeviceToHost, A->own_stream));
-    SPMVC_CUDA(cudaStreamSynchronize(A->own_stream));
+    const bool tiled = A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty() &&
+                       A->stage_ok && (A->fast_variant == 1 || A->fast_variant == 6 || A->fast_variant == 8 ||
+                                       A->fast_variant == 9);
+    constexpr int kChunks = 8;
+    if (!tiled || A->n < int64_t(kChunks) * 4 * A->stage.rows) {
+        SPMVC_CUDA(cudaMemcpyAsync(A->d_hx, x, bytes, cudaMemcpyHostToDevice, A->own_stream));
+        if ((st = spmv_apply(A, A->d_hx, A->d_hy, A->own_stream))) return st;
+        SPMVC_CUDA(cudaMemcpyAsync(y, A->d_hy, bytes, cudaMemcpyDeviceToHost, A->own_stream));
+        SPMVC_CUDA(cudaStreamSynchronize(A->own_stream));
+        return SPMV_OK;
+    }
+    // Pipelined by row chunks (multiples of the tile): x chunk j goes in on
+    // one stream; the rows of chunk i are computed once every x chunk up to
+    // row end + the largest displacement has arrived; y chunk i goes out on
+    // a third stream while later chunks are still coming in.  The tiles
+    // are those of the one-shot product, so the result is the same bits.
+    if (!A->h2d_stream) SPMVC_CUDA(cudaStreamCreateWithFlags(&A->h2d_stream, cudaStreamNonBlocking));
+    if (!A->d2h_stream) SPMVC_CUDA(cudaStreamCreateWithFlags(&A->d2h_stream, cudaStreamNonBlocking));
+    while (A->host_events.size() < 2 * kChunks) {
+        cudaEvent_t e;
+        SPMVC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        A->host_events.push_back(e);
+    }
+    const int64_t n = A->n, rows = A->stage.rows;
+    const int64_t chunk = (n + kChunks * rows - 1) / (kChunks * rows) * rows;
+    int64_t halo = 0;
+    for (int32_t d : A->pat.uoff) halo = std::max<int64_t>(halo, d < 0 ? -int64_t(d) : int64_t(d));
+    for (int j = 0; j < kChunks; ++j) {
+        const int64_t b = std::min(n, j * chunk), e = std::min(n, (j + 1) * chunk);
+        if (e > b)
+            SPMVC_CUDA(cudaMemcpyAsync(A->d_hx + b, x + b, sizeof(double) * (e - b), cudaMemcpyHostToDevice,
+                                       A->h2d_stream));
+        SPMVC_CUDA(cudaEventRecord(A->host_events[j], A->h2d_stream));
+    }
+    for (int i = 0; i < kChunks; ++i) {
+        const int64_t b = std::min(n, i * chunk), e = std::min(n, (i + 1) * chunk);
+        if (e <= b) break;
+        const int64_t need = std::min(n, e + halo);
+        const int jx = int((need - 1) / chunk);
+        SPMVC_CUDA(cudaStreamWaitEvent(A->own_stream, A->host_events[std::min(jx, kChunks - 1)], 0));
+        StagePlan plan = A->stage;
+        plan.tile0 = b / rows;
+        plan.ntiles = (e - b + rows - 1) / rows;
+        const cudaError_t ce =
+            A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, plan, A->d_hx, A->d_hy, A->own_stream)
+                                 : launch_pattern_fast_rstaged(A->pat_view, plan, A->d_hx, A->d_hy,
+                                                               A->fast_variant == 6 ? 0 : A->fast_variant == 8 ? 1 : 2,
+                                                               A->own_stream);
+        if (ce != cudaSuccess) return cuda_fail(ce, "spmv chunk launch");
+        SPMVC_CUDA(cudaEventRecord(A->host_events[kChunks + i], A->own_stream));
+        SPMVC_CUDA(cudaStreamWaitEvent(A->d2h_stream, A->host_events[kChunks + i], 0));
+        SPMVC_CUDA(cudaMemcpyAsync(y + b, A->d_hy + b, sizeof(double) * (e - b), cudaMemcpyDeviceToHost,
+                                   A->d2h_stream));
+    }
+    SPMVC_CUDA(cudaStreamSynchronize(A->d2h_stream));
     return SPMV_OK;
 }
 

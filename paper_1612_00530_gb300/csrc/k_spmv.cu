@@ -551,8 +551,11 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
     }
 }
 
+// Eight rows a thread keep more values live than the 40-register budget of
+// six resident 256-thread CTAs allows; that shape gets three CTAs' worth.
 template <int WORDS, int NU, int RPT, int RUN, int THREADS, bool VEC>
-__global__ void __launch_bounds__(THREADS, 1536 / THREADS) pattern_fast_staged_kernel(PatternView a, StagePlan sp,
+__global__ void __launch_bounds__(THREADS, RPT >= 8 ? 768 / THREADS : 1536 / THREADS)
+    pattern_fast_staged_kernel(PatternView a, StagePlan sp,
                                                                                     const double* __restrict__ x,
                                                                                     double* __restrict__ y) {
     extern __shared__ int4 sx4[];
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(THREADS, 1536 / THREADS) pattern_fast_staged_k
     __shared__ uint32_t s_red[THREADS / 32];
     __shared__ uint32_t smask[32];
     const int tid = threadIdx.x;
-    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
+    const int64_t r0 = (sp.tile0 + int64_t(blockIdx.x)) * sp.rows;
     if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
     uint32_t w0[kMaxRecordWords];                  // first row's record, in flight during staging
     if (r0 + tid < a.n) load_record<WORDS>(a, r0 + tid, w0);
@@ -643,7 +646,7 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
     __shared__ uint32_t s_red[THREADS / 32];
     __shared__ uint32_t smask[32];
     const int tid = threadIdx.x;
-    const int64_t r0 = int64_t(blockIdx.x) * sp.rows;
+    const int64_t r0 = (sp.tile0 + int64_t(blockIdx.x)) * sp.rows;
     if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
     const uint4* __restrict__ x4 = reinterpret_cast<const uint4*>(x);
     const uint2* __restrict__ x2 = reinterpret_cast<const uint2*>(x);
@@ -1610,7 +1613,9 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
     // 16-byte staging needs x itself 16-byte aligned
     const bool vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
     const int threads = sp.rows / sp.rows_per_thread;
-    const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
+    const int64_t tiles = (a.n + sp.rows - 1) / sp.rows - sp.tile0;
+    if (tiles <= 0) return cudaSuccess;
+    const unsigned grid = unsigned(sp.ntiles > 0 && sp.ntiles < tiles ? sp.ntiles : tiles);
     const size_t smem = size_t((std::max(sp.elems, sp.elems_padded) + 1) / 2 * 2) * sizeof(int2);
     auto go = [&](auto kernel) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1769,7 +1774,9 @@ cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& s
     // kernel on the same plan
     if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return launch_pattern_fast_staged(a, sp, x, y, s);
     const int threads = sp.rows / sp.rows_per_thread;
-    const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
+    const int64_t tiles = (a.n + sp.rows - 1) / sp.rows - sp.tile0;
+    if (tiles <= 0) return cudaSuccess;
+    const unsigned grid = unsigned(sp.ntiles > 0 && sp.ntiles < tiles ? sp.ntiles : tiles);
     // converted windows, then the tile's records (28 bytes a row) or the
     // table of row types (32 bytes a type)
     const size_t smem = size_t(sp.elems_padded) * sizeof(int2) +
@@ -1868,6 +1875,8 @@ bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int 
     StagePlan p{};
     p.rows = rows_per_thread * threads;
     p.rows_per_thread = rows_per_thread;
+    p.tile0 = 0;
+    p.ntiles = 0;
     const int nu = int(uoff.size());
     if (nu == 0 || nu > 31) return false;
     int seg = -1;

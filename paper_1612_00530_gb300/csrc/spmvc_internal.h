@@ -204,6 +204,10 @@ struct StagePlan {
     int32_t seg_pbase[kMaxSegments];
     int32_t soff_padded[32];
     int32_t elems_padded;
+    // tiles covered by a launch: tile0, tile0 + 1, ... (ntiles of them; 0 =
+    // through the last row).  make_stage_plan: all tiles.
+    int64_t tile0;
+    int64_t ntiles;
 };
 // z-marching plan of the full 27-point union: its tile windows are three
 // copies of one window shape spaced by the plane stride S (the displacement
@@ -335,5 +339,10 @@ struct spmv_mat_s {
     double* d_hx = nullptr;
     double* d_hy = nullptr;
     cudaStream_t own_stream = nullptr;
+    // spmv_apply_host's pipeline: x chunks in on one stream, y chunks out on
+    // another, the product's row ranges on own_stream
+    cudaStream_t h2d_stream = nullptr;
+    cudaStream_t d2h_stream = nullptr;
+    std::vector<cudaEvent_t> host_events;
     float* d_ell_val32 = nullptr;
 };

@@ -246,6 +246,34 @@ def test_host_buffers_entry_point():
     assert np.array_equal(y, oracle.spmv(rowptr, col, val, x))
 
 
+def test_host_buffers_pipelined_in_row_chunks():
+    """FAST order through host buffers: the row-chunk pipeline (x in, rows
+    computed as their x windows arrive, y out) gives the device call's bits,
+    for every tiled kernel, pinned and pageable buffers, n not a multiple of
+    the chunk."""
+    g = (64, 48, 41)
+    n = 64 * 48 * 41
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    x_np = spmv_inputs.uniform_vector(n, seed=6)
+    x = torch.from_numpy(x_np).cuda()
+    hx = torch.from_numpy(x_np).pin_memory()
+    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (8, 1024, 256), (9, 1024, 256)]:
+        P.spmv_set_tile(C, v, t, bt)
+        yd = torch.empty_like(x)
+        P.spmv_apply(C, x, yd)
+        torch.cuda.synchronize()
+        want = yd.cpu().numpy()
+        hy = torch.full((n,), float("nan"), dtype=torch.float64).pin_memory()
+        P.spmv_apply_host(C, hx, hy)
+        assert np.array_equal(hy.numpy().view(np.uint64), want.view(np.uint64)), (v, t, bt)
+        y = np.full(n, np.nan)
+        P.spmv_apply_host(C, x_np, y)
+        assert np.array_equal(y.view(np.uint64), want.view(np.uint64)), (v, t, bt)
+    rows = np.unique(np.random.default_rng(3).integers(0, n, 3000))
+    check_fast(y[rows], oracle.hpcg_spmv_rows(*g, rows, x_np),
+               52.0 * np.abs(x_np[rows]) - oracle.hpcg_spmv_rows(*g, rows, np.abs(x_np)))
+
+
 def test_graph_capture_of_apply():
     g = (24, 24, 24)
     rowptr, col, val = oracle.hpcg_csr(*g)
