@@ -233,7 +233,10 @@ __device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
     const double d = __ll2double_rn(acc);
     const int32_t hi = __double2hiint(d);
     const int ef = (hi >> 20) & 0x7FF;          // 0 exactly when acc == 0
-    if (ef != 0 && uint32_t(ef + S - 1) < 2046u) return __hiloint2double(hi + (S << 20), __double2loint(d));
+    // the exponent moves by S in the high word: unsigned arithmetic, since a
+    // negative S shifted left is undefined in C++17
+    if (ef != 0 && uint32_t(ef + S - 1) < 2046u)
+        return __hiloint2double(int32_t(uint32_t(hi) + (uint32_t(S) << 20)), __double2loint(d));
     return ef == 0 ? d : fixed_to_double_int(acc, S);
 }
 
