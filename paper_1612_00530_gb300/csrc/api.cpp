@@ -672,7 +672,7 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
         SPMVC_CUDA(cudaStreamSynchronize(A->own_stream));
         return SPMV_OK;
     }
-    // Pipelined by row chunks (multiples of the tile): x chunk j goes in on
+    // Pipelined by row chunks (whole tiles): x chunk j goes in on
     // one stream; the rows of chunk i are computed once every x chunk up to
     // row end + the largest displacement has arrived; y chunk i goes out on
     // a third stream while later chunks are still coming in.  The tiles
@@ -685,22 +685,28 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
         A->host_events.push_back(e);
     }
     const int64_t n = A->n, rows = A->stage.rows;
-    const int64_t chunk = (n + kChunks * rows - 1) / (kChunks * rows) * rows;
+    // chunk ends in whole tiles, equal chunks (measured best against
+    // chunks growing from small ones: the last chunk's copy-out is the tail)
+    const int64_t tiles = (n + rows - 1) / rows;
+    int64_t bound[kChunks + 1];
+    for (int j = 0; j <= kChunks; ++j) bound[j] = std::min(n, (tiles * j + kChunks - 1) / kChunks * rows);
+    bound[kChunks] = n;
     int64_t halo = 0;
     for (int32_t d : A->pat.uoff) halo = std::max<int64_t>(halo, d < 0 ? -int64_t(d) : int64_t(d));
     for (int j = 0; j < kChunks; ++j) {
-        const int64_t b = std::min(n, j * chunk), e = std::min(n, (j + 1) * chunk);
+        const int64_t b = bound[j], e = bound[j + 1];
         if (e > b)
             SPMVC_CUDA(cudaMemcpyAsync(A->d_hx + b, x + b, sizeof(double) * (e - b), cudaMemcpyHostToDevice,
                                        A->h2d_stream));
         SPMVC_CUDA(cudaEventRecord(A->host_events[j], A->h2d_stream));
     }
     for (int i = 0; i < kChunks; ++i) {
-        const int64_t b = std::min(n, i * chunk), e = std::min(n, (i + 1) * chunk);
-        if (e <= b) break;
+        const int64_t b = bound[i], e = bound[i + 1];
+        if (e <= b) continue;
         const int64_t need = std::min(n, e + halo);
-        const int jx = int((need - 1) / chunk);
-        SPMVC_CUDA(cudaStreamWaitEvent(A->own_stream, A->host_events[std::min(jx, kChunks - 1)], 0));
+        int jx = i;
+        while (jx + 1 < kChunks && bound[jx + 1] < need) ++jx;     // last x chunk the rows read
+        SPMVC_CUDA(cudaStreamWaitEvent(A->own_stream, A->host_events[jx], 0));
         StagePlan plan = A->stage;
         plan.tile0 = b / rows;
         plan.ntiles = (e - b + rows - 1) / rows;

@@ -13,6 +13,8 @@
 //    exactly with 32x32->64-bit integer multiply-adds, and one rounding to
 //    nearest makes the double result -- no FP64 instruction per nonzero.
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include <cstdint>
 
 #include "spmvc_internal.h"
@@ -1561,6 +1563,33 @@ __global__ void fill_u32_kernel(uint32_t* p, uint32_t v, int64_t n) {
 
 unsigned grid_of(int64_t threads) { return unsigned((threads + kBlock - 1) / kBlock); }
 
+// Opens a kernel's dynamic shared memory to the device's per-block limit and
+// prefers the largest shared-memory carveout, once per kernel and device:
+// the two driver calls cost more than a launch, and a pipelined product
+// launches a kernel many times.
+cudaError_t prepare_kernel(const void* kernel) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::unordered_map<const void*, uint64_t> done;   // kernel -> devices prepared
+    std::lock_guard<std::mutex> g(mu);
+    uint64_t& mask = done[kernel];
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (mask & bit)) return cudaSuccess;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+    const int dyn = optin - int(fa.sharedSizeBytes);     // the limit counts the kernel's static shared memory
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  int(cudaSharedmemCarveoutMaxShared))) != cudaSuccess)
+        return e;
+    mask |= bit;
+    return cudaSuccess;
+}
+
 
 }  // namespace
 
@@ -1621,10 +1650,7 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
     const unsigned grid = unsigned(sp.ntiles > 0 && sp.ntiles < tiles ? sp.ntiles : tiles);
     const size_t smem = size_t((std::max(sp.elems, sp.elems_padded) + 1) / 2 * 2) * sizeof(int2);
     auto go = [&](auto kernel) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     int(cudaSharedmemCarveoutMaxShared));
+        const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
         if (e != cudaSuccess) return e;
         kernel<<<grid, threads, smem, s>>>(a, sp, x, y);
         return cudaGetLastError();
@@ -1698,10 +1724,7 @@ cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& s
     const unsigned grid = unsigned((a.n + sp.rows - 1) / sp.rows);
     const size_t smem = size_t(sp.elems_padded) * sizeof(int2);
     auto go = [&](auto kernel) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     int(cudaSharedmemCarveoutMaxShared));
+        const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
         if (e != cudaSuccess) return e;
         kernel<<<grid, kStageThreads, smem, s>>>(a, sp, x, X, y, partial);
         return cudaGetLastError();
@@ -1721,10 +1744,7 @@ cudaError_t launch_pattern_fast_async(const PatternView& a, const StagePlan& sp,
     const size_t xbytes = (size_t(sp.elems) * 8 + 15) / 16 * 16;
     const size_t smem = 2 * (xbytes + size_t(kAsyncRows) * 28);
     auto kernel = pattern_fast_async_kernel<27, 3, false>;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 int(cudaSharedmemCarveoutMaxShared));
+    const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
     if (e != cudaSuccess) return e;
     const unsigned grid = unsigned(std::min<int64_t>(ntiles, num_sms));
     kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, nullptr, y, ntiles, nullptr);
@@ -1744,10 +1764,7 @@ cudaError_t launch_pattern_fast_async_x(const PatternView& a, const StagePlan& s
     const size_t xbytes = (size_t(std::max(sp.elems, sp.elems_padded)) * 8 + 15) / 16 * 16;
     const size_t smem = 2 * (xbytes + size_t(kAsyncRows) * 28);
     auto kernel = pattern_fast_async_kernel<27, 3, true>;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 int(cudaSharedmemCarveoutMaxShared));
+    const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
     if (e != cudaSuccess) return e;
     const unsigned grid = unsigned(std::min<int64_t>(ntiles, num_sms));
     kernel<<<grid, kAsyncThreads, smem, s>>>(a, sp, x, X, y, ntiles, partial);
@@ -1785,10 +1802,7 @@ cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& s
     const size_t smem = size_t(sp.elems_padded) * sizeof(int2) +
                         (recs == 1 ? size_t(sp.rows) * 28 : recs == 2 ? size_t(a.ntypes) * 32 : 0);
     auto go = [&](auto kernel) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     int(cudaSharedmemCarveoutMaxShared));
+        const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
         if (e != cudaSuccess) return e;
         kernel<<<grid, threads, smem, s>>>(a, sp, x, y);
         return cudaGetLastError();
@@ -1858,10 +1872,7 @@ cudaError_t launch_pattern_fast_zmarch(const PatternView& a, const ZPlan& zp, co
     const unsigned grid = unsigned(int64_t(zp.nblk) * zp.nchunks);
     const size_t smem = size_t(3) * zp.slot * sizeof(int2);
     auto go = [&](auto kernel) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     int(cudaSharedmemCarveoutMaxShared));
+        const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
         if (e != cudaSuccess) return e;
         kernel<<<grid, zp.threads, smem, s>>>(a, zp, x, y, partial);
         return cudaGetLastError();
