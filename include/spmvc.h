@@ -219,8 +219,14 @@ int spmv_import(const void *buf, size_t len, spmv_mat_t *out);
 int spmv_apply(spmv_mat_t A, const double *x, double *y, spmv_stream_t stream);
 
 /* y = A x with x and y in host memory: copies x to the device, runs
- * spmv_apply on the library's own stream, copies y back and waits.
- * Uses library-owned device buffers kept with the handle. */
+ * spmv_apply on the library's own streams, copies y back and waits.
+ * Uses library-owned device buffers kept with the handle.  For the tiled
+ * FAST kernels (variants 1, 6, 8, 9) the call is pipelined in 8 row chunks
+ * of whole tiles: x chunks go in on one stream, a chunk's tiles run once
+ * every x chunk up to its last row plus the largest displacement is in,
+ * and its y goes out on another stream while later x chunks still come in
+ * (the same tiles, so the same result bits as spmv_apply).  Pinned host
+ * buffers let the copies overlap; pageable ones work but serialise. */
 int spmv_apply_host(spmv_mat_t A, const double *x, double *y);
 
 /* y = A x in binary32: x and y device pointers to n floats; values are the
@@ -238,12 +244,14 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
 /* Autotuner: times the kernel configurations available to A (FAST order:
  * the pre-converted-x kernels, the persistent kernels, the shared-memory
  * staged kernel with tiles of 512, 1024 and 2048 rows of 512 or 256
- * threads, the register-staged and the z-marching kernels) on the caller's device vectors
+ * threads, the register-staged kernels with records from global or shared
+ * memory, and the z-marching kernel; not the row types of variant 9, a
+ * different stored form) on the caller's device vectors
  * x and y (n doubles each; y is overwritten), keeps the fastest for later
  * calls on A, and remembers it for matrices with the same signature (device
  * name, n, nnz, union size) uploaded later in this process.  reps: timed
  * launches per candidate (default 10 when <= 0).  *choice (may be NULL)
- * receives the chosen tile rows for a staged kernel (variants 1, 3, 6, 7), 1
+ * receives the chosen tile rows for a tiled kernel (variants 1, 3, 6, 7, 8), 1
  * for the pre-converted kernel, 4 or 5 for the persistent kernels, 0 when
  * A has nothing to tune.  Synchronous, uses the legacy default stream: call
  * it outside any stream capture. */
@@ -267,9 +275,9 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 
 /* As spmv_set_variant with 512-thread blocks, but also sets the block size
  * of the staged kernels: block_threads 512 (tile_rows 512, 1024 or 2048) or,
- * for variants 1, 6 and 7 on the full 27-slot union of a 3-D 27-point
- * stencil, 256 (tile_rows 512, 1024 or 2048: two, four or eight rows per
- * thread).
+ * for variants 1, 6, 7, 8 and 9 on the full 27-slot union of a 3-D
+ * 27-point stencil, 256 (tile_rows 512, 1024 or 2048: two, four or eight
+ * rows per thread).
  * Ignored for variants 0, 2, 4, 5.  SPMV_EINVAL for other block sizes,
  * SPMV_EUNSUPPORTED for shapes A has no kernel for. */
 int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads);
