@@ -686,12 +686,24 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_rstaged_kernel(Pat
         for (int i = tid; i < a.ntypes * 8; i += THREADS) srec[i] = __ldg(a.rtypes + i);
         if (r0 + tid < a.n) t0 = __ldg(a.rtype + r0 + tid);
     }
-    // phase 1: every pair of the three windows this thread owns, in flight together
+    // phase 1: every pair of the three windows this thread owns, in flight
+    // together; a tile whose windows lie inside [0, n) skips the bounds tests
     uint4 b[3][QS];
+    const bool interior = r0 + sp.seg_min[0] - sp.seg_pad[0] >= 0 &&
+                          r0 + sp.seg_min[2] + sp.seg_span[2] + sp.rows + 1 < a.n;
 #pragma unroll
     for (int sg = 0; sg < 3; ++sg) {
         const int64_t g0 = r0 + sp.seg_min[sg] - sp.seg_pad[sg];   // even
         const int len2 = (sp.rows + sp.seg_span[sg] + sp.seg_pad[sg] + 1) / 2;
+        if (interior) {
+            const uint4* __restrict__ w4 = x4 + (g0 >> 1);
+#pragma unroll
+            for (int j = 0; j < QS; ++j) {
+                const int q = tid + j * THREADS;
+                b[sg][j] = q < len2 ? __ldg(w4 + q) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < QS; ++j) {
             const int q = tid + j * THREADS;
