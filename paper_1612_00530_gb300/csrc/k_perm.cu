@@ -1,7 +1,7 @@
 // Permutation passes around the product of a reordered matrix B = P A P^T
-// (perm[new] = old): xp = P x before it, y = P^T yp after it.  One thread per
-// element, 16-byte-friendly strided loops over a grid of whole waves; the
-// permuted side is coalesced, the other side is a gather or a scatter.
+// (perm[new] = old): xp = P x before it, y = P^T yp after it.  Strided loops
+// over a grid of whole waves; the permuted side is coalesced, the other side
+// is a gather or a scatter.
 #include <cstdint>
 
 #include "spmvc_internal.h"
@@ -11,21 +11,50 @@ namespace {
 
 constexpr int kPermBlock = 256;
 
+// Each thread moves kPermUnroll elements a pass, all their index loads
+// first, so that several random accesses are in flight per thread.
+constexpr int kPermUnroll = 8;
+
 __global__ void __launch_bounds__(kPermBlock) gather_kernel(const int32_t* __restrict__ perm, int64_t n,
                                                            const double* __restrict__ x, double* __restrict__ xp) {
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        xp[i] = __ldg(x + __ldg(perm + i));
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i0 < n; i0 += kPermUnroll * stride) {
+        int32_t p[kPermUnroll];
+#pragma unroll
+        for (int u = 0; u < kPermUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            p[u] = i < n ? __ldg(perm + i) : 0;
+        }
+        double v[kPermUnroll];
+#pragma unroll
+        for (int u = 0; u < kPermUnroll; ++u) v[u] = i0 + u * stride < n ? __ldg(x + p[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPermUnroll; ++u)
+            if (i0 + u * stride < n) xp[i0 + u * stride] = v[u];
+    }
 }
 
 __global__ void __launch_bounds__(kPermBlock) scatter_kernel(const int32_t* __restrict__ perm, int64_t n,
                                                             const double* __restrict__ yp, double* __restrict__ y) {
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        y[__ldg(perm + i)] = __ldg(yp + i);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i0 < n; i0 += kPermUnroll * stride) {
+        int32_t p[kPermUnroll];
+        double v[kPermUnroll];
+#pragma unroll
+        for (int u = 0; u < kPermUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            p[u] = i < n ? __ldg(perm + i) : 0;
+            v[u] = i < n ? __ldg(yp + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPermUnroll; ++u)
+            if (i0 + u * stride < n) y[p[u]] = v[u];
+    }
 }
 
 unsigned perm_grid(int64_t n) {
     const int64_t blocks = (n + kPermBlock - 1) / kPermBlock;
-    return unsigned(blocks < 152 * 16 ? blocks : 152 * 16);
+    return unsigned(blocks < 152 * 8 ? blocks : 152 * 8);
 }
 
 }  // namespace
