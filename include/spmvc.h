@@ -253,7 +253,12 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
  * launches per candidate (default 10 when <= 0).  *choice (may be NULL)
  * receives the chosen tile rows for a tiled kernel (variants 1, 3, 6, 7, 8), 1
  * for the pre-converted kernel, 4 or 5 for the persistent kernels, 0 when
- * A has nothing to tune.  Synchronous, uses the legacy default stream: call
+ * A has nothing to tune.  Each candidate's y is first compared with the
+ * COLUMN-order product on the same x (|difference| <= R max|x| 2^-46 +
+ * 2^-50 |y|, R the largest absolute row sum; non-finite entries equal): a
+ * candidate that disagrees is never chosen, and SPMV_EDEVICE is returned if
+ * none agrees.  Allocates two scratch buffers (n doubles, 16 bytes) for the
+ * duration of the call.  Synchronous, uses the legacy default stream: call
  * it outside any stream capture. */
 int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_t *choice);
 

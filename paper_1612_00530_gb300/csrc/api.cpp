@@ -829,11 +829,41 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         }
     }
     if (cands.size() <= 1) return SPMV_OK;
+    // Every candidate's result is checked against the COLUMN-order product
+    // before it may be picked: |y - y_col| <= R max|x| 2^-46 + 2^-50 |y_col|,
+    // R the largest absolute row sum of A (the FAST bound plus the COLUMN
+    // chain's own rounding, with margin).  A kernel that disagrees is never
+    // chosen.
+    double* y_ref = nullptr;
+    unsigned long long* words = nullptr;          // [0] max |x| bits, [1] mismatch count
+    SPMVC_CUDA(cudaMalloc(&y_ref, sizeof(double) * A->n));
+    struct Freer {
+        double* a = nullptr;
+        unsigned long long* b = nullptr;
+        ~Freer() { cudaFree(a); cudaFree(b); }
+    } freer;
+    freer.a = y_ref;
+    SPMVC_CUDA(cudaMalloc(&words, 2 * sizeof(unsigned long long)));
+    freer.b = words;
+    SPMVC_CUDA(cudaMemset(words, 0, 2 * sizeof(unsigned long long)));
+    {
+        const cudaError_t ce = launch_pattern_col_f64(A->pat_view, x, y_ref, nullptr);
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune reference launch");
+        const cudaError_t me = launch_absmax(x, A->n, words, nullptr);
+        if (me != cudaSuccess) return cuda_fail(me, "autotune max launch");
+    }
+    unsigned long long xbits = 0;
+    SPMVC_CUDA(cudaMemcpy(&xbits, words, sizeof(xbits), cudaMemcpyDeviceToHost));
+    double xmax;
+    std::memcpy(&xmax, &xbits, sizeof(xmax));
+    const double row_abs = std::ldexp(double(A->pat.max_row_abs), A->pat.mult_exp);
+    const double abs_tol = row_abs * xmax * std::ldexp(1.0, -46), rel_tol = std::ldexp(1.0, -50);
     cudaEvent_t e0, e1;
     SPMVC_CUDA(cudaEventCreate(&e0));
     SPMVC_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     Cand pick = cands[0];
+    bool picked = false;
     for (const Cand& c : cands) {
         auto launch = [&]() {
             if (c.variant == 4) return launch_pattern_fast_async(A->pat_view, c.plan, x, y, A->num_sms, nullptr);
@@ -852,16 +882,23 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         };
         cudaError_t e = launch();
         if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+        SPMVC_CUDA(cudaMemsetAsync(words + 1, 0, sizeof(unsigned long long), nullptr));
+        if ((e = launch_check_close(y, y_ref, A->n, abs_tol, rel_tol, words + 1, nullptr)) != cudaSuccess)
+            return cuda_fail(e, "autotune check launch");
+        unsigned long long bad = 0;
+        SPMVC_CUDA(cudaMemcpy(&bad, words + 1, sizeof(bad), cudaMemcpyDeviceToHost));
+        if (bad != 0) continue;                       // wrong results: never a candidate
         SPMVC_CUDA(cudaEventRecord(e0, nullptr));
         for (int k = 0; k < reps; ++k) launch();
         SPMVC_CUDA(cudaEventRecord(e1, nullptr));
         SPMVC_CUDA(cudaEventSynchronize(e1));
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; pick = c; }
+        if (ms < best) { best = ms; pick = c; picked = true; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (!picked) return fail(SPMV_EDEVICE, "autotune: no FAST kernel matched the COLUMN-order product");
     A->fast_variant = pick.variant;
     const bool staged_pick = pick.variant == 1 || pick.variant == 3 || pick.variant == 6 || pick.variant == 8;
     if (staged_pick) A->stage = pick.plan;

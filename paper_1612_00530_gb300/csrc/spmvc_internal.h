@@ -258,6 +258,12 @@ cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double*
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s);
+// k_check.cu: *out = max |x_j| as bits (atomicMax; *out zeroed by the
+// caller); *bad += count of i with |y_i - yref_i| > abs_tol + rel_tol |yref_i|
+// (non-finite entries must match)
+cudaError_t launch_absmax(const double* x, int64_t n, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_check_close(const double* y, const double* yref, int64_t n, double abs_tol, double rel_tol,
+                               unsigned long long* bad, cudaStream_t s);
 // k_perm.cu: xp[i] = x[perm[i]] and y[perm[i]] = yp[i]
 cudaError_t launch_gather(const int32_t* perm, int64_t n, const double* x, double* xp, cudaStream_t s);
 cudaError_t launch_scatter(const int32_t* perm, int64_t n, const double* yp, double* y, cudaStream_t s);

@@ -486,13 +486,26 @@ def test_autotune_keeps_results():
     rows = P.spmv_autotune(C, x, y, reps=3)
     assert rows in (1, 4, 5, 512, 1024, 2048)
     info = P.spmv_info(C)
-    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6, 7))
+    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6, 7, 8))
     if rows not in (1, 4, 5):
         assert info["fast_tile_rows"] == rows
     y_ref = oracle.spmv(rowptr, col, val, x_np)
     check_fast(run(C, x_np), y_ref, abs_row_sums(rowptr, col, val, x_np))
     # ELL and COLUMN order have nothing to tune
     assert P.spmv_autotune(P.spmv_build("hpcg", *g), x, y) == 0
+    # non-finite entries: every candidate takes the exact path where they
+    # reach, agrees with the COLUMN order, and one is chosen
+    xb = x_np.copy()
+    xb[5], xb[n // 2] = np.inf, np.nan
+    xd = torch.from_numpy(xb).cuda()
+    D = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    assert P.spmv_autotune(D, xd, y, reps=2) in (1, 4, 5, 512, 1024, 2048)
+    yb = run(D, xb)
+    yb_ref = oracle.spmv(rowptr, col, val, xb)
+    assert np.array_equal(np.isnan(yb), np.isnan(yb_ref))
+    fin = np.isfinite(yb_ref)
+    assert np.array_equal(yb[~fin & ~np.isnan(yb_ref)], yb_ref[~fin & ~np.isnan(yb_ref)])
+    check_fast(yb[fin], yb_ref[fin], abs_row_sums(rowptr, col, val, np.where(np.isfinite(xb), xb, 0))[fin])
 
 
 def fast_order_exact_model(rowptr, col, mult, mult_exp, x):
