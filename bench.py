@@ -289,7 +289,7 @@ def run_suite(args):
     xx = torch.zeros_like(b)
     P.spmv_autotune(C, ones, xx)
     res = {}
-    for mode, extra in (("fp64", {}), ("ir_fp32", {"inner_max_iter": 400, "inner_tol": 1e-6})):
+    for mode, extra in (("fp64", {}), ("ir_fp32", {"inner_max_iter": 200, "inner_tol": 1e-6})):
         xx.zero_()
         r = P.cg_solve(C, b, xx, tol=1e-10, mode=mode, max_iter=5000, **extra)
         err = float((xx - 1.0).abs().max())

@@ -696,8 +696,8 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     if (o.tol <= 0) o.tol = 1e-10;
     if (o.max_iter <= 0) o.max_iter = 10000;
     if (o.check_every <= 0) o.check_every = 16;
-    if (o.inner_max_iter <= 0) o.inner_max_iter = 60;
-    if (o.inner_tol <= 0) o.inner_tol = 1e-5;
+    if (o.inner_max_iter <= 0) o.inner_max_iter = 200;
+    if (o.inner_tol <= 0) o.inner_tol = 1e-6;
     if (o.nrhs <= 0) o.nrhs = 1;
     if (o.nrhs < 1 || o.nrhs > kMaxCols) return fail(SPMV_EINVAL, "nrhs must be 1..32");
     if (o.nrhs > 1 && o.mode != SPMV_CG_FP64) return fail(SPMV_EUNSUPPORTED, "several right-hand sides: FP64 mode only");
