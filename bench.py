@@ -43,25 +43,39 @@ def kernel_source_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
-    """dram read+write bytes per launch of `kernel` from the committed ncu
-    summary in profiles/, if it was taken on the current kernel source."""
+def profiled(kernel: str, tag: str = "traffic", key: str = "bytes"):
+    """A per-launch ncu figure of `kernel` recorded in the committed summary
+    in profiles/ (lines `<tag>: kernel=... source_sha256_16=... <key>=...`),
+    if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "spmv_fast_hpcg192.md")
     if not os.path.exists(path):
         return None
     fields = {}
     with open(path) as f:
         for line in f:
-            if line.startswith("traffic:"):
+            if line.startswith(tag + ":"):
                 parts = dict(p.split("=", 1) for p in line.split()[1:] if "=" in p)
                 if parts.get("kernel") == kernel:
                     fields = parts
     if fields.get("source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(fields["bytes"])
+        return float(fields[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(kernel: str):
+    """dram read+write bytes per launch of `kernel` (ncu), or None."""
+    return profiled(kernel, "traffic", "bytes")
+
+
+# GB300 rates used for the bounds the headline line reports beside the HBM
+# roofline: 4 warp-instructions issued per SM per clock (one per scheduler),
+# and the FP64 FMA rate a microbenchmark measured, 2.07 per SM per clock.
+ISSUE_PER_SM_CLK = 4.0
+FP64_FMA_PER_SM_CLK = 2.07
+NOMINAL_HBM_GBS = 7900.0
 
 
 def measured_peaks() -> dict:
@@ -119,23 +133,54 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds: float = 12.0) -> dict:
-    """The oracle's CSR SpMV (single thread, as written) on this host."""
+def cpu_baseline(seconds: float = 12.0, all_core_seconds: float = 6.0) -> dict:
+    """The oracle's CSR SpMV as written, on this host: single-threaded (the
+    reported value), and row-parallel on every host core (the same per-row
+    fma chains over disjoint row blocks, so the same bits; reported beside)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
     import spmv_inputs
 
     rowptr, col, val = oracle.hpcg_csr(NX, NY, NZ)
-    x = spmv_inputs.uniform_vector(NX * NY * NZ, seed=X_SEED)
+    n = NX * NY * NZ
+    x = spmv_inputs.uniform_vector(n, seed=X_SEED)
     nnz = int(rowptr[-1])
+    csr_bytes = 12.0 * nnz + 8.0 * (n + 1) + 16.0 * n     # col + val + rowptr + x + y
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.spmv(rowptr, col, val, x)
+        y1 = oracle.spmv(rowptr, col, val, x)
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = (time.perf_counter() - t0) / reps
-    return {"value": 2.0 * nnz / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full 192^3 CSR SpMVs (x seed 1), single thread, {reps * dt:.1f} s"}
+    out = {"value": 2.0 * nnz / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+           "gbs": csr_bytes / dt / 1e9,
+           "sample": f"{reps} full 192^3 CSR SpMVs (x seed 1), single thread, {reps * dt:.1f} s"}
+    # every core: the ctypes call releases the interpreter lock, so threads run
+    # the oracle's row-range routine side by side
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    bounds = np.linspace(0, n, cores + 1).astype(np.int64)
+
+    def block(b):
+        lo, hi = int(bounds[b]), int(bounds[b + 1])
+        return oracle.spmv_range(lo, hi, rowptr[lo:hi + 1], col, val, x)
+
+    with ThreadPoolExecutor(cores) as ex:
+        yp = np.concatenate(list(ex.map(block, range(cores))))
+        same = bool(np.array_equal(yp.view(np.uint64), y1.view(np.uint64)))
+        reps_p, t0 = 0, time.perf_counter()
+        while True:
+            list(ex.map(block, range(cores)))
+            reps_p += 1
+            if time.perf_counter() - t0 >= all_core_seconds:
+                break
+        dtp = (time.perf_counter() - t0) / reps_p
+    out["all_cores"] = {"value": 2.0 * nnz / dtp / 1e9, "unit": "GFLOP/s", "cores": cores,
+                        "gbs": csr_bytes / dtp / 1e9, "bit_identical_to_single_thread": same,
+                        "sample": f"{reps_p} full 192^3 CSR SpMVs, {cores} row blocks on {cores} threads, "
+                                  f"{reps_p * dtp:.1f} s"}
+    return out
 
 
 def dist_setup():
@@ -476,6 +521,18 @@ def main():
     alg_bytes = nnz * 1.0 + n * 5.0 / 8.0 + 16.0 * n      # codes + pattern + x + y
     ell_alg_bytes = nnz * 12.0 + 16.0 * n                  # value + column + x + y
     achieved = alg_bytes / (ms * 1e-3) / 1e9
+    # the three bounds of a compressed product: HBM (algorithmic bytes at the
+    # measured copy rate), instruction issue (the kernel's warp-instructions
+    # per launch, from ncu on this source, at the sampled SM clock), and the
+    # FP64 pipe a one-FMA-per-nonzero order would meet (the COLUMN order)
+    props = torch.cuda.get_device_properties(dev)
+    f_hz = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    warp_inst = profiled(kernel_id, "issue", "warp_inst")
+    bounds_us = {"hbm": alg_bytes / (peaks["hbm_gbs"] * 1e9) * 1e6,
+                 "issue": (warp_inst / (ISSUE_PER_SM_CLK * props.multi_processor_count * f_hz) * 1e6
+                           if warp_inst else None),
+                 "fp64_pipe_column_order": nnz / (FP64_FMA_PER_SM_CLK * props.multi_processor_count * f_hz) * 1e6,
+                 "measured": ms * 1e3}
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -487,7 +544,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(kernel_id),
                      "kernel": kernel_desc, "kernel_id": kernel_id,
-                     "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peaks["source"]},
+                     "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peaks["source"],
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                     "bounds_us": bounds_us},
         "ell": {"gflops": world * flops / (ell_ms * 1e-3) / 1e9, "ms_per_step": ell_ms,
                 "achieved_gbs": ell_alg_bytes / (ell_ms * 1e-3) / 1e9,
                 "frac": ell_alg_bytes / (ell_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
