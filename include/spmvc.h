@@ -172,15 +172,17 @@ typedef struct {
     int64_t padding_bytes;      /* of format_bytes: padding slots and records */
     uint64_t checksum;          /* FNV-1a of the compressed stream */
     int32_t fast_tile_rows;     /* FAST order: rows per shared-memory tile of the
-                                   staged kernel (0 = no staged kernel for A) */
+                                   staged kernel (z-block kernel: rows a CTA
+                                   computes, 512 per plane; 0 = no staged
+                                   kernel for A) */
     int32_t fast_variant;       /* FAST kernel in use: 0 direct, 1 staged tiles,
                                    2 pre-converted fixed-point copy of x, 3 staged
                                    tiles of that copy, 4 persistent double-buffered
                                    tiles, 5 the same from the copy, 6 register-
                                    staged tiles, 7 z-marching tiles, 8 register-
                                    staged with records in shared memory, 9 the
-                                   same reading row types; -1 before A's first
-                                   device call */
+                                   same reading row types, 10 z-block tiles;
+                                   -1 before A's first device call */
     int32_t fast_block_threads; /* FAST order: threads per block of the staged
                                    kernel (512 or 256; 0 = no staged kernel) */
     int32_t row_types;          /* pattern format: distinct row records held as
@@ -245,13 +247,15 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
  * the pre-converted-x kernels, the persistent kernels, the shared-memory
  * staged kernel with tiles of 512, 1024 and 2048 rows of 512 or 256
  * threads, the register-staged kernels with records from global or shared
- * memory, and the z-marching kernel; not the row types of variant 9, a
+ * memory, the z-marching kernel and the z-block kernel of 3 and 4 planes;
+ * not the row types of variant 9, a
  * different stored form) on the caller's device vectors
  * x and y (n doubles each; y is overwritten), keeps the fastest for later
  * calls on A, and remembers it for matrices with the same signature (device
  * name, n, nnz, union size) uploaded later in this process.  reps: timed
  * launches per candidate (default 10 when <= 0).  *choice (may be NULL)
- * receives the chosen tile rows for a tiled kernel (variants 1, 3, 6, 7, 8), 1
+ * receives the chosen tile rows for a tiled kernel (variants 1, 3, 6, 7, 8;
+ * for 10 the rows a CTA computes), 1
  * for the pre-converted kernel, 4 or 5 for the persistent kernels, 0 when
  * A has nothing to tune.  Each candidate's y is first compared with the
  * COLUMN-order product on the same x (|difference| <= R max|x| 2^-46 +
@@ -273,8 +277,14 @@ int spmv_autotune(spmv_mat_t A, const double *x, double *y, int32_t reps, int32_
  * cp.async (shapes as 6), 9 register-staged tiles reading one-byte row
  * types instead of records -- the values registered in the pattern that
  * Sec. V proposes; the first selection builds the types (at most 256
- * distinct records) and copies them to the device (shapes as 6); tile_rows
- * is ignored for 0, 2, 4, 5.  SPMV_EUNSUPPORTED when A has no such kernel.
+ * distinct records) and copies them to the device (shapes as 6), 10
+ * z-block tiles: a CTA owns a 512-row column block of tile_rows/512 (3 or
+ * 4) consecutive planes, loads and converts the planes' tile_rows/512 + 2
+ * x windows once and sums all its rows from shared memory, each x element
+ * converted (planes + 2)/planes times instead of three (full 27-point union
+ * whose plane stride is a multiple of 512; 256 threads only, so through
+ * spmv_set_tile); tile_rows is ignored for 0, 2, 4, 5.  SPMV_EUNSUPPORTED
+ * when A has no such kernel.
  * Copies A to the device if it is not there yet. */
 int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
 
@@ -282,7 +292,7 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
  * of the staged kernels: block_threads 512 (tile_rows 512, 1024 or 2048) or,
  * for variants 1, 6, 7, 8 and 9 on the full 27-slot union of a 3-D
  * 27-point stencil, 256 (tile_rows 512, 1024 or 2048: two, four or eight
- * rows per thread).
+ * rows per thread); variant 10 takes 256 with tile_rows 1536 or 2048.
  * Ignored for variants 0, 2, 4, 5.  SPMV_EINVAL for other block sizes,
  * SPMV_EUNSUPPORTED for shapes A has no kernel for. */
 int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads);

@@ -293,7 +293,13 @@ int ensure_device(spmv_mat_s* m) {
                     break;
                 }
         }
+        // z-block kernel: only when the autotuner picked it for a matrix of
+        // this shape (planes a CTA recorded with the pick)
+        m->zbplan_ok = false;
+        if (m->fast_variant == 10 && p.fast_ok && v.run_len == 3 && v.nu == 27 && v.words == 7)
+            m->zbplan_ok = make_zblock_plan(p.uoff, m->n, tuned_stage_shape(m, 256, 3).second, 256, &m->zbplan);
         if (m->fast_variant == 7 && !m->zplan_ok) m->fast_variant = 1;
+        if (m->fast_variant == 10 && !m->zbplan_ok) m->fast_variant = 1;
         if ((m->fast_variant == 4 || m->fast_variant == 5) && !m->async_ok) m->fast_variant = 2;
         if (m->fast_variant == 9) m->fast_variant = 6;   // row types are built on request only
         if ((m->fast_variant == 6 || m->fast_variant == 8) && !(m->stage_ok && rstage_supported(m->stage)))
@@ -414,6 +420,7 @@ int apply_stored(spmv_mat_s* A, const double* x, double* y, cudaStream_t s) {
             : A->fast_variant == 2 ? launch_pattern_fast_x(A->pat_view, x, y, A->d_scratch_words, A->d_xfixed,
                                                            A->xfixed_guard, s)
             : A->fast_variant == 7 ? launch_pattern_fast_zmarch(A->pat_view, A->zplan, x, y, A->d_scratch_words, s)
+            : A->fast_variant == 10 ? launch_pattern_fast_zblock(A->pat_view, A->zbplan, x, y, A->d_scratch_words, s)
             : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 0, s)
             : A->fast_variant == 8 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 1, s)
             : A->fast_variant == 9 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 2, s)
@@ -543,9 +550,12 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->union_size = static_cast<int32_t>(A->pat.uoff.size());
         out->record_bytes = 4 * A->pat.words;
         out->fast_eligible = A->pat.fast_ok ? 1 : 0;
-        out->fast_tile_rows = A->fast_variant == 7 && A->zplan_ok ? A->zplan.rows : A->stage_ok ? A->stage.rows : 0;
+        out->fast_tile_rows = A->fast_variant == 7 && A->zplan_ok ? A->zplan.rows
+                            : A->fast_variant == 10 && A->zbplan_ok ? A->zbplan.rows * A->zbplan.zc
+                            : A->stage_ok ? A->stage.rows : 0;
         out->fast_variant = A->device >= 0 ? A->fast_variant : -1;
         out->fast_block_threads = A->fast_variant == 7 && A->zplan_ok ? A->zplan.threads
+                                  : A->fast_variant == 10 && A->zbplan_ok ? A->zbplan.threads
                                   : A->stage_ok ? A->stage.rows / A->stage.rows_per_thread : 0;
         out->row_types = static_cast<int32_t>(A->pat.rtypes.size() / 8);
         out->format_bytes = A->n * 4 * A->pat.words;
@@ -661,11 +671,14 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
         if ((st = dev_copy<double>(A, nullptr, A->n, &A->d_hy))) return st;
     }
     const size_t bytes = sizeof(double) * A->n;
-    const bool tiled = A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty() &&
-                       A->stage_ok && (A->fast_variant == 1 || A->fast_variant == 6 || A->fast_variant == 8 ||
-                                       A->fast_variant == 9);
+    const bool fast = A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty();
+    const bool zblock = fast && A->fast_variant == 10 && A->zbplan_ok;
+    const bool tiled = zblock || (fast && A->stage_ok && (A->fast_variant == 1 || A->fast_variant == 6 ||
+                                                          A->fast_variant == 8 || A->fast_variant == 9));
+    // the unit a chunk is made of: a tile, or a z-block chunk of planes
+    const int64_t rows = zblock ? int64_t(A->zbplan.zc) * A->zbplan.S : int64_t(A->stage.rows);
     constexpr int kChunks = 8;
-    if (!tiled || A->n < int64_t(kChunks) * 4 * A->stage.rows) {
+    if (!tiled || A->n < int64_t(kChunks) * (zblock ? 1 : 4) * rows) {
         SPMVC_CUDA(cudaMemcpyAsync(A->d_hx, x, bytes, cudaMemcpyHostToDevice, A->own_stream));
         if ((st = spmv_apply(A, A->d_hx, A->d_hy, A->own_stream))) return st;
         SPMVC_CUDA(cudaMemcpyAsync(y, A->d_hy, bytes, cudaMemcpyDeviceToHost, A->own_stream));
@@ -684,7 +697,7 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
         SPMVC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         A->host_events.push_back(e);
     }
-    const int64_t n = A->n, rows = A->stage.rows;
+    const int64_t n = A->n;
     // chunk ends in whole tiles, equal chunks (measured best against
     // chunks growing from small ones: the last chunk's copy-out is the tail)
     const int64_t tiles = (n + rows - 1) / rows;
@@ -703,18 +716,29 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
     for (int i = 0; i < kChunks; ++i) {
         const int64_t b = bound[i], e = bound[i + 1];
         if (e <= b) continue;
-        const int64_t need = std::min(n, e + halo);
+        // the windows of a chunk's last tiles reach one element past the
+        // largest displacement (a 16-byte pair that starts on an odd
+        // element); that element enters the tile's exponent, so it must have
+        // arrived too
+        const int64_t need = std::min(n, e + halo + 2);
         int jx = i;
         while (jx + 1 < kChunks && bound[jx + 1] < need) ++jx;     // last x chunk the rows read
         SPMVC_CUDA(cudaStreamWaitEvent(A->own_stream, A->host_events[jx], 0));
-        StagePlan plan = A->stage;
-        plan.tile0 = b / rows;
-        plan.ntiles = (e - b + rows - 1) / rows;
-        const cudaError_t ce =
-            A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, plan, A->d_hx, A->d_hy, A->own_stream)
-                                 : launch_pattern_fast_rstaged(A->pat_view, plan, A->d_hx, A->d_hy,
-                                                               A->fast_variant == 6 ? 0 : A->fast_variant == 8 ? 1 : 2,
-                                                               A->own_stream);
+        cudaError_t ce;
+        if (zblock) {
+            ZPlan zp = A->zbplan;
+            zp.chunk0 = int32_t(b / rows);
+            zp.nchunks = int32_t((e - b + rows - 1) / rows);
+            ce = launch_pattern_fast_zblock(A->pat_view, zp, A->d_hx, A->d_hy, A->d_scratch_words, A->own_stream);
+        } else {
+            StagePlan plan = A->stage;
+            plan.tile0 = b / rows;
+            plan.ntiles = (e - b + rows - 1) / rows;
+            ce = A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, plan, A->d_hx, A->d_hy, A->own_stream)
+                                      : launch_pattern_fast_rstaged(A->pat_view, plan, A->d_hx, A->d_hy,
+                                                                    A->fast_variant == 6 ? 0 : A->fast_variant == 8 ? 1 : 2,
+                                                                    A->own_stream);
+        }
         if (ce != cudaSuccess) return cuda_fail(ce, "spmv chunk launch");
         SPMVC_CUDA(cudaEventRecord(A->host_events[kChunks + i], A->own_stream));
         SPMVC_CUDA(cudaStreamWaitEvent(A->d2h_stream, A->host_events[kChunks + i], 0));
@@ -826,6 +850,11 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
                     zmarch_supported(zp))
                     cands.push_back(Cand{7, {}, zp});
             }
+            for (int planes : {3, 4}) {
+                ZPlan zp;
+                if (A->pat_view.words == 7 && make_zblock_plan(A->pat.uoff, A->n, planes, 256, &zp))
+                    cands.push_back(Cand{10, {}, zp});
+            }
         }
     }
     if (cands.size() <= 1) return SPMV_OK;
@@ -871,6 +900,8 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
             if (c.variant == 8) return launch_pattern_fast_rstaged(A->pat_view, c.plan, x, y, 1, nullptr);
             if (c.variant == 7)
                 return launch_pattern_fast_zmarch(A->pat_view, c.zplan, x, y, A->d_scratch_words, nullptr);
+            if (c.variant == 10)
+                return launch_pattern_fast_zblock(A->pat_view, c.zplan, x, y, A->d_scratch_words, nullptr);
             if (c.variant == 5)
                 return launch_pattern_fast_async_x(A->pat_view, c.plan, x, y, A->d_scratch_words, A->d_xfixed,
                                                    A->xfixed_guard, A->num_sms, nullptr);
@@ -907,15 +938,22 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         A->zplan = pick.zplan;
         A->zplan_ok = true;
     }
+    if (pick.variant == 10) {
+        A->zbplan = pick.zplan;
+        A->zbplan_ok = true;
+    }
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_variant[tune_key(A)] = pick.variant;
         if (pick.variant == 7)
             g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.rows_per_thread;
+        else if (pick.variant == 10)
+            g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.zc;
         else if (staged_pick)
             g_tune[tune_key(A)] = (pick.plan.rows / pick.plan.rows_per_thread) * 16 + pick.plan.rows_per_thread;
     }
     if (choice) *choice = staged_pick ? pick.plan.rows : pick.variant == 7 ? pick.zplan.rows
+                        : pick.variant == 10 ? pick.zplan.rows * pick.zplan.zc
                         : (pick.variant >= 4 ? pick.variant : 1);
     return SPMV_OK;
 }
@@ -950,8 +988,20 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
         A->fast_variant = 7;
         return SPMV_OK;
     }
+    if (variant == 10) {
+        ZPlan zp;
+        if (block_threads != 256 && block_threads != 512) return fail(SPMV_EINVAL, "block_threads must be 256 or 512");
+        if (A->pat_view.words != 7 || tile_rows <= 0 || tile_rows % 512 != 0 ||
+            !make_zblock_plan(A->pat.uoff, A->n, tile_rows / 512, block_threads, &zp))
+            return fail(SPMV_EUNSUPPORTED, "no z-block kernel for this union and tile (tile_rows 1536 or 2048 with "
+                                           "256 threads; plane stride a multiple of 512)");
+        A->zbplan = zp;
+        A->zbplan_ok = true;
+        A->fast_variant = 10;
+        return SPMV_OK;
+    }
     if (variant != 1 && variant != 3 && variant != 6 && variant != 8 && variant != 9)
-        return fail(SPMV_EINVAL, "variant must be 0..9");
+        return fail(SPMV_EINVAL, "variant must be 0..10");
     const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
     const bool rstaged = variant == 6 || variant == 8 || variant == 9;
     if (variant == 3 && !(A->d_xfixed && full27))

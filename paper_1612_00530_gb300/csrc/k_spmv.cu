@@ -858,6 +858,105 @@ __global__ void __launch_bounds__(THREADS, MINB) pattern_fast_zmarch_kernel(Patt
     }
 }
 
+// --------------------------------------------- FAST order, z-block tiles -
+// A CTA owns a column block of zp.rows rows in ZC consecutive planes
+// z0 .. z0+ZC-1 (the z-marching plan's window shape).  Those planes need the
+// ZC+2 windows W(z0-1) .. W(z0+ZC): every thread loads its QS 16-byte pairs
+// of each window into registers at once, the block reduces the largest
+// exponent over all of them, and each thread converts its pairs and writes
+// them to shared memory once.  The ZC planes' rows then sum from shared
+// memory with no further barrier.  Each x element is loaded and converted
+// (ZC+2)/ZC times per column block instead of three times, and the exponent
+// is the CTA's own (no pre-pass).  x must be 16-byte aligned.
+template <int ZC, int QS, int RPT, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) pattern_fast_zblock_kernel(PatternView a, ZPlan zp,
+                                                                           const double* __restrict__ x,
+                                                                           double* __restrict__ y) {
+    extern __shared__ int4 sx4[];
+    __shared__ uint32_t s_red[THREADS / 32];
+    __shared__ uint32_t smask[32];
+    const int tid = threadIdx.x;
+    const int64_t z0 = (int64_t(blockIdx.x / unsigned(zp.nblk)) + zp.chunk0) * ZC;
+    const int64_t col0 = int64_t(blockIdx.x % unsigned(zp.nblk)) * zp.rows;
+    if (tid < 32) smask[tid] = tid < a.npat ? a.pmask[tid] : 0u;
+    const uint4* __restrict__ x4 = reinterpret_cast<const uint4*>(x);
+    const uint2* __restrict__ x2 = reinterpret_cast<const uint2*>(x);
+    // window W(z) covers the pairs from the even element at or below
+    // z*S + col0 + m1; a CTA whose windows all lie inside [0, n) skips the
+    // bounds tests
+    const int64_t gfirst = (z0 - 1) * zp.S + col0 + zp.m1;
+    const int64_t glast = (z0 + ZC) * zp.S + col0 + zp.m1;
+    const bool interior = gfirst >= 1 && glast + 2 * int64_t(zp.pairs) <= a.n;
+    uint4 b[ZC + 2][QS];
+#pragma unroll
+    for (int w = 0; w < ZC + 2; ++w) {
+        const int64_t g = gfirst + int64_t(w) * zp.S;
+        const int64_t g0 = g - (g & 1);
+#pragma unroll
+        for (int j = 0; j < QS; ++j) {
+            const int q = tid + j * THREADS;
+            const int64_t e = g0 + 2 * q;
+            b[w][j] = make_uint4(0u, 0u, 0u, 0u);
+            if (q < zp.pairs) {
+                if (interior || uint64_t(e) < uint64_t(a.n - 1)) {        // 0 <= e and e + 1 < n
+                    b[w][j] = __ldg(x4 + (e >> 1));
+                } else if (e == a.n - 1) {                                 // odd n: the last element alone
+                    const uint2 h = __ldg(x2 + e);
+                    b[w][j].x = h.x;
+                    b[w][j].y = h.y;
+                }
+            }
+        }
+    }
+    uint32_t mx = 0;
+#pragma unroll
+    for (int w = 0; w < ZC + 2; ++w)
+#pragma unroll
+        for (int j = 0; j < QS; ++j) mx = max(mx, max(b[w][j].y & 0x7FFFFFFFu, b[w][j].w & 0x7FFFFFFFu));
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) mx = max(mx, s_red[w]);
+    const uint32_t emax = mx >> 20;
+    const bool exact_path = emax < 64u || emax >= 2047u;
+#pragma unroll
+    for (int w = 0; w < ZC + 2; ++w) {
+        int4* dst = sx4 + w * (zp.slot / 2);
+#pragma unroll
+        for (int j = 0; j < QS; ++j) {
+            const int q = tid + j * THREADS;
+            if (q >= zp.pairs) continue;
+            const uint4 v = b[w][j];
+            if (exact_path) {
+                dst[q] = make_int4(int(v.x), int(v.y), int(v.z), int(v.w));
+            } else {
+                const int2 l0 = fixed_limbs(v.x, v.y, emax);
+                const int2 l1 = fixed_limbs(v.z, v.w, emax);
+                dst[q] = make_int4(l0.x, l0.y, l1.x, l1.y);
+            }
+        }
+    }
+    __syncthreads();
+    const int2* sx = reinterpret_cast<const int2*>(sx4);
+#pragma unroll 1
+    for (int k = 0; k < ZC; ++k) {
+        const int64_t z = z0 + k;
+        if (z >= zp.nplanes) break;
+        const int64_t r0 = z * zp.S + col0;
+        // shared-memory index of each segment's window start for local row 0
+        int base[3];
+#pragma unroll
+        for (int sg = 0; sg < 3; ++sg)
+            base[sg] = (k + sg) * zp.slot + int((gfirst + int64_t(k + sg) * zp.S) & 1);
+        uint32_t w0[kMaxRecordWords];
+        if (r0 + tid < a.n) load_record<7>(a, r0 + tid, w0);
+        tile_rows<7, 27, RPT, 3, THREADS>(a, [&](int u) { return base[u / 9] + zp.rel[u]; }, sx, smask, r0, emax,
+                                          exact_path, y, w0);
+    }
+}
+
 // ------------------- FAST order, staged tiles of the pre-converted copy ---
 // As the staged kernel, but the tile's windows are copied from the
 // fixed-point copy X (guard zones make every window index valid), so the
@@ -1892,6 +1991,45 @@ cudaError_t launch_pattern_fast_zmarch(const PatternView& a, const ZPlan& zp, co
     if (zp.threads == 256 && zp.rows_per_thread == 2) return go(pattern_fast_zmarch_kernel<2, 256, 4, 2>);
     if (zp.threads == 256 && zp.rows_per_thread == 4) return go(pattern_fast_zmarch_kernel<4, 256, 4, 3>);
     return go(pattern_fast_zmarch_kernel<2, 512, 2, 2>);
+}
+
+bool make_zblock_plan(const std::vector<int32_t>& uoff, int64_t n, int planes, int threads, ZPlan* out) {
+    // column blocks of 512 rows, two rows a thread per plane
+    if (threads != 256) return false;
+    ZPlan zp;
+    if (!make_zplan(uoff, n, 2, threads, 1, &zp)) return false;
+    zp.zc = planes;
+    zp.nchunks = int32_t((zp.nplanes + planes - 1) / planes);
+    zp.chunk0 = 0;
+    if (int64_t(zp.nblk) * zp.nchunks >= (int64_t(1) << 31)) return false;
+    *out = zp;
+    return zblock_supported(zp);
+}
+
+bool zblock_supported(const ZPlan& zp) {
+    if ((zp.zc != 3 && zp.zc != 4) || zp.rows != 512 || zp.threads != 256 || zp.rows_per_thread != 2) return false;
+    if ((zp.zc + 2) * int64_t(zp.slot) * 8 > 200 * 1024) return false;
+    return zp.pairs <= 2 * 256;
+}
+
+cudaError_t launch_pattern_fast_zblock(const PatternView& a, const ZPlan& zp, const double* x, double* y,
+                                       uint32_t* partial, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (!(a.run_len == 3 && a.nu == 27 && a.words == 7) || !zblock_supported(zp)) return cudaErrorNotSupported;
+    // the 16-byte loads need x 16-byte aligned: otherwise the direct kernel
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0) return launch_pattern_fast_f64(a, x, y, partial, s);
+    // chunks chunk0 .. chunk0 + nchunks - 1 of zc planes (all of them for a
+    // whole product; a row range of them for a pipelined one)
+    if (zp.nchunks <= 0 || zp.chunk0 < 0) return cudaSuccess;
+    const unsigned grid = unsigned(int64_t(zp.nblk) * zp.nchunks);
+    const size_t smem = size_t(zp.zc + 2) * zp.slot * sizeof(int2);
+    auto go = [&](auto kernel) -> cudaError_t {
+        const cudaError_t e = prepare_kernel(reinterpret_cast<const void*>(kernel));
+        if (e != cudaSuccess) return e;
+        kernel<<<grid, zp.threads, smem, s>>>(a, zp, x, y);
+        return cudaGetLastError();
+    };
+    return zp.zc == 3 ? go(pattern_fast_zblock_kernel<3, 2, 2, 256, 4>) : go(pattern_fast_zblock_kernel<4, 2, 2, 256, 4>);
 }
 
 bool stage_supported(int nu) { return nu == 27 || nu == 19 || nu == 9 || nu == 7 || nu == 5; }

@@ -220,6 +220,7 @@ struct ZPlan {
     int32_t pairs;                  // 16-byte pairs per window (covers an odd start)
     int32_t slot;                   // int2 entries per ring slot (2 * pairs)
     int32_t nblk, zc, nchunks;      // column blocks per plane, planes per CTA, CTAs per block column
+    int32_t chunk0;                 // z-block kernel: first chunk of zc planes this launch computes
     int32_t m1;                     // first displacement of the middle segment
     int32_t rel[27];                // slot u: displacement minus its segment's first one
     int64_t S, nplanes;
@@ -227,6 +228,12 @@ struct ZPlan {
 bool make_zplan(const std::vector<int32_t>& uoff, int64_t n, int rows_per_thread, int threads, int num_sms,
                 ZPlan* out);
 bool zmarch_supported(const ZPlan& zp);  // shapes with a compiled z-marching kernel
+// z-block plan: 512-row column blocks of `planes` (3 or 4) consecutive planes
+// a CTA, 256 threads (two rows a thread per plane); false where no compiled
+// kernel fits (the z-marching plan's conditions: three equal segments spaced
+// by the plane stride, which must be a multiple of 512)
+bool make_zblock_plan(const std::vector<int32_t>& uoff, int64_t n, int planes, int threads, ZPlan* out);
+bool zblock_supported(const ZPlan& zp);
 bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
                      StagePlan* out);
 bool stage_supported(int nu);  // union sizes with a compiled staged kernel
@@ -246,6 +253,8 @@ cudaError_t launch_pattern_fast_staged(const PatternView& a, const StagePlan& sp
 cudaError_t launch_pattern_fast_rstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                         int recs, cudaStream_t s);
 cudaError_t launch_pattern_fast_zmarch(const PatternView& a, const ZPlan& zp, const double* x, double* y,
+                                       uint32_t* partial, cudaStream_t s);
+cudaError_t launch_pattern_fast_zblock(const PatternView& a, const ZPlan& zp, const double* x, double* y,
                                        uint32_t* partial, cudaStream_t s);
 cudaError_t launch_pattern_fast_xstaged(const PatternView& a, const StagePlan& sp, const double* x, double* y,
                                         uint32_t* partial, int2* X_guarded, int64_t guard, cudaStream_t s);
@@ -329,6 +338,8 @@ struct spmv_mat_s {
     bool stage_ok = false;
     spmvc::ZPlan zplan{};              // FAST order, z-marching kernel
     bool zplan_ok = false;
+    spmvc::ZPlan zbplan{};             // FAST order, z-block kernel (set on request or by the autotuner)
+    bool zbplan_ok = false;
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;

@@ -23,7 +23,8 @@ def main():
     ap.add_argument("--kind", default="hpcg", choices=("hpcg", "irregular"))
     ap.add_argument("--variant", type=int, default=-1,
                     help="FAST kernel: 0 direct, 1 staged, 2 pre-converted, 3 staged pre-converted, "
-                         "4/5 persistent, 6 register-staged")
+                         "4/5 persistent, 6 register-staged, 7 z-marching, 8/9 register-staged with shared-memory "
+                         "records / row types, 10 z-block (tile = 512 x planes, 256 threads)")
     ap.add_argument("--tile", type=int, default=2048)
     ap.add_argument("--threads", type=int, default=512, help="block size of the staged kernels (512 or 256)")
     ap.add_argument("--cg", choices=("fp64", "ir_fp32"), default=None,

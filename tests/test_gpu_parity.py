@@ -249,15 +249,16 @@ def test_host_buffers_entry_point():
 def test_host_buffers_pipelined_in_row_chunks():
     """FAST order through host buffers: the row-chunk pipeline (x in, rows
     computed as their x windows arrive, y out) gives the device call's bits,
-    for every tiled kernel, pinned and pageable buffers, n not a multiple of
-    the chunk."""
+    for every tiled kernel (the z-block kernel in chunks of whole plane
+    groups), pinned and pageable buffers, n not a multiple of the chunk."""
     g = (64, 48, 41)
     n = 64 * 48 * 41
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x_np = spmv_inputs.uniform_vector(n, seed=6)
     x = torch.from_numpy(x_np).cuda()
     hx = torch.from_numpy(x_np).pin_memory()
-    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (8, 1024, 256), (9, 1024, 256)]:
+    for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (8, 1024, 256), (9, 1024, 256),
+                     (10, 1536, 256), (10, 2048, 256)]:
         P.spmv_set_tile(C, v, t, bt)
         yd = torch.empty_like(x)
         P.spmv_apply(C, x, yd)
@@ -372,9 +373,10 @@ def test_fast_variants_on_hpcg_grids():
         rstaged = {(25, 25, 5): [(6, 512, 256), (8, 512, 256), (9, 512, 256)],
                    (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512),
                                   (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
-                                  (8, 512, 256), (8, 1024, 256), (9, 512, 256), (9, 1024, 256), (9, 1024, 512)]}
+                                  (8, 512, 256), (8, 1024, 256), (9, 512, 256), (9, 1024, 256), (9, 1024, 512),
+                                  (10, 1536, 256), (10, 2048, 256)]}
         for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512), (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
-                         (8, 512, 256), (9, 1024, 256)]:
+                         (8, 512, 256), (9, 1024, 256), (10, 1536, 256), (10, 2048, 256)]:
             if (v, t, bt) not in rstaged.get(g, []):
                 with pytest.raises(P.SpmvError):
                     P.spmv_set_tile(C, v, t, bt)
@@ -424,20 +426,22 @@ def test_fast_27_point_non_uniform_weights():
     y_ref = oracle.spmv(rowptr, col, val, x)
     scale = abs_row_sums(rowptr, col, val, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
-    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (7, 1024, 512)]:
+    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (7, 1024, 512), (10, 1536, 256), (10, 2048, 256)]:
         P.spmv_set_tile(C, v, t, bt)
         check_fast(run(C, x), y_ref, scale)
 
 
 def test_fast_zmarch_several_planes_per_cta():
     """The z-marching kernel on 64x64x160, where each CTA walks two or three
-    planes, on sampled rows, A*1 and a non-finite entry."""
+    planes, and the z-block kernel (3 or 4 planes a CTA; 160 planes leave a
+    last chunk of one plane, or a full one), on sampled rows, A*1 and a
+    non-finite entry."""
     # 64x64x160: three planes per CTA
     g = (64, 64, 160)
     n = 64 * 64 * 160
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x = spmv_inputs.uniform_vector(n, seed=24)
-    for v, t, bt in [(7, 512, 256), (7, 1024, 256)]:
+    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (10, 1536, 256), (10, 2048, 256)]:
         P.spmv_set_tile(C, v, t, bt)
         check_persistent(C, g, n, x)
 
@@ -457,16 +461,25 @@ def test_fast_uniform_stencil_with_odd_rows():
     scale = abs_row_sums(rowptr, col, val, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
     for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (6, 1024, 256), (7, 512, 256), (7, 1024, 512),
-                     (8, 512, 256), (9, 512, 256)]:
+                     (8, 512, 256), (9, 512, 256), (10, 1536, 256), (10, 2048, 256)]:
         P.spmv_set_tile(C, v, t, bt)
         check_fast(run(C, x), y_ref, scale)
 
 
 def test_set_tile_rejects_shapes_without_kernel():
     C = P.spmv_compress(P.spmv_build("hpcg", 16, 16, 16), format="pattern", order="fast")
-    for v, t, bt in [(1, 1024, 128), (3, 1024, 256), (1, 768, 256), (1, 4096, 256), (1, 256, 256)]:
+    for v, t, bt in [(1, 1024, 128), (3, 1024, 256), (1, 768, 256), (1, 4096, 256), (1, 256, 256),
+                     (10, 1536, 256), (11, 1024, 256)]:
         with pytest.raises(P.SpmvError):
             P.spmv_set_tile(C, v, t, bt)
+    # the z-block kernel: 3 or 4 planes of 512 rows at 256 threads only
+    C = P.spmv_compress(P.spmv_build("hpcg", 32, 64, 5), format="pattern", order="fast")
+    for t, bt in [(1024, 256), (2560, 256), (1536, 512), (2048, 512), (1500, 256)]:
+        with pytest.raises(P.SpmvError):
+            P.spmv_set_tile(C, 10, t, bt)
+    P.spmv_set_tile(C, 10, 1536, 256)
+    info = P.spmv_info(C)
+    assert (info["fast_variant"], info["fast_tile_rows"], info["fast_block_threads"]) == (10, 1536, 256)
     # a union that is not the full 27-point one has 512-thread tiles only
     rowptr, col, val = spread_offsets_csr(30000, [-600, -1, 0, 1, 600], [-1.0, -2.0, 8.0, -2.0, -1.0])
     D = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
@@ -539,7 +552,7 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
              # three separate plane windows per 512-row tile: the register-staged kernel
              ((24, 24, 4), [(6, 512, 256), (8, 512, 256), (9, 512, 256), (1, 512, 256), (2, 0, 512)]),
              # plane stride 2048: z-marching tiles
-             ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512)])]
+             ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512), (10, 1536, 256), (10, 2048, 256)])]
     for g, shapes in cases:
         rowptr, col, val = oracle.hpcg_csr(*g)
         n = len(rowptr) - 1
@@ -599,6 +612,7 @@ def test_fast_variant_persistent_many_tiles():
     x = spmv_inputs.uniform_vector(n, seed=13)
     for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512),
                            (7, 512, 256), (7, 1024, 256), (7, 1024, 512), (8, 1024, 256), (8, 512, 256),
+                           (10, 1536, 256), (10, 2048, 256),
                            (9, 512, 256), (9, 1024, 512)]:
         P.spmv_set_tile(C, variant, t, bt)
         check_persistent(C, g, n, x)
