@@ -121,6 +121,33 @@ def test_binary32_products(g):
         assert np.array_equal(y.cpu().numpy(), y_ref)
 
 
+def test_binary32_rows_off_the_dominant_record():
+    """The binary32 product bit-equal to the binary32 CSR oracle on grids
+    whose warps mix the dominant record with rows of other values, with x
+    aligned and x one element into a buffer."""
+    for g in [(64, 48, 41), (32, 64, 6)]:
+        rowptr, col, val = oracle.hpcg_csr(*g)
+        val = val.copy()
+        n = len(rowptr) - 1
+        for r in (0, 5, 4000, 4001, 7777, n - 1):
+            val[rowptr[r]] = 2.0 if val[rowptr[r]] < 0 else 25.0
+        x32 = spmv_inputs.uniform_vector(n, seed=31).astype(np.float32)
+        y_ref = oracle.spmv_f32(rowptr, col, val, x32)
+        M = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern")
+        x = torch.from_numpy(x32).cuda()
+        y = torch.full_like(x, float("nan"))
+        P.spmv_apply_f32(M, x, y)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy(), y_ref), g
+        xbuf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+        xbuf[1:] = x
+        y.fill_(float("nan"))
+        P.spmv_apply_f32(M, xbuf[1:], y)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy(), y_ref), g
+        assert P.spmv_device_error(M) == 0
+
+
 def test_config2_192cubed_sampled():
     """192^3 HPCG, x ~ U[-1,1) seed 1, in the launch configuration the
     benchmark times: ELL and pattern (COLUMN) bit-exact and pattern FAST
