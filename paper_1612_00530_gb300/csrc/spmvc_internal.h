@@ -343,7 +343,6 @@ struct spmv_mat_s {
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;
-    int32_t rstage_recs = 0;           // register-staged kernel: where records come from (0, 1, 2)
     int32_t fast_variant = 0;          // 0 direct, 1 staged, 2 pre-converted, 3 staged pre-converted,
                                        // 4 persistent double-buffered, 5 the same from the pre-converted copy
     int2* d_xfixed = nullptr;          // FAST order: fixed-point copy of x with guard zones
