@@ -223,12 +223,14 @@ int spmv_apply(spmv_mat_t A, const double *x, double *y, spmv_stream_t stream);
 /* y = A x with x and y in host memory: copies x to the device, runs
  * spmv_apply on the library's own streams, copies y back and waits.
  * Uses library-owned device buffers kept with the handle.  For the tiled
- * FAST kernels (variants 1, 6, 8, 9) the call is pipelined in 8 row chunks
- * of whole tiles: x chunks go in on one stream, a chunk's tiles run once
- * every x chunk up to its last row plus the largest displacement is in,
- * and its y goes out on another stream while later x chunks still come in
- * (the same tiles, so the same result bits as spmv_apply).  Pinned host
- * buffers let the copies overlap; pageable ones work but serialise. */
+ * FAST kernels (variants 1, 6, 8, 9, and 10 in whole plane groups) the call
+ * is pipelined in 8 row chunks of whole tiles: x chunks go in on one
+ * stream, a chunk's tiles run once every x chunk up to its last row plus
+ * the largest displacement plus two is in (a tile's last 16-byte pair may
+ * reach one element further, and it enters the tile's exponent), and its y
+ * goes out on another stream while later x chunks still come in (the same
+ * tiles, so the same result bits as spmv_apply).  Pinned host buffers let
+ * the copies overlap; pageable ones work but serialise. */
 int spmv_apply_host(spmv_mat_t A, const double *x, double *y);
 
 /* y = A x in binary32: x and y device pointers to n floats; values are the
