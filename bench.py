@@ -133,10 +133,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds: float = 12.0, all_core_seconds: float = 6.0) -> dict:
+def cpu_baseline(seconds: float = 12.0, all_core_seconds: float = 6.0, y_check=None) -> dict:
     """The oracle's CSR SpMV as written, on this host: single-threaded (the
     reported value), and row-parallel on every host core (the same per-row
-    fma chains over disjoint row blocks, so the same bits; reported beside)."""
+    fma chains over disjoint row blocks, so the same bits; reported beside).
+    y_check: the timed GPU product on the same x, compared here with the
+    oracle's, normwise and row by row against sum_j |a_ij x_j|."""
     from concurrent.futures import ThreadPoolExecutor
 
     import oracle
@@ -157,6 +159,13 @@ def cpu_baseline(seconds: float = 12.0, all_core_seconds: float = 6.0) -> dict:
     out = {"value": 2.0 * nnz / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
            "gbs": csr_bytes / dt / 1e9,
            "sample": f"{reps} full 192^3 CSR SpMVs (x seed 1), single thread, {reps * dt:.1f} s"}
+    if y_check is not None:
+        d = np.abs(np.asarray(y_check, dtype=np.float64) - y1)
+        scale = oracle.spmv(rowptr, col, np.abs(val), np.abs(x))     # sum_j |a_ij x_j|
+        out["parity"] = {"normwise": float(d.max() / np.abs(y1).max()),
+                         "componentwise": float(np.max(np.where(scale > 0, d / np.where(scale > 0, scale, 1.0),
+                                                                np.where(d > 0, np.inf, 0.0)))),
+                         "bound": 1e-14, "rows": int(n)}
     # every core: the ctypes call releases the interpreter lock, so threads run
     # the oracle's row-range routine side by side
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
@@ -504,6 +513,7 @@ def main():
     ms = max_over_ranks(timed(C, args.steps), world)
     clocks = sampler.stop()
     assert P.spmv_device_error(C) == 0
+    y_fast = y.cpu().numpy()          # the timed product, checked against the oracle on the CPU leg
 
     # end to end through the host-buffer entry point: x H2D, SpMV, y D2H
     hx = torch.from_numpy(x_np).pin_memory()
@@ -540,7 +550,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64-in/out, int64 fixed-point accumulate", "data": "synthetic",
         "config": {"workload": WORKLOAD, "rows": n, "nnz": nnz, "format": "pattern", "order": "fast",
-                   "record_bytes_per_row": info_c["record_bytes"],
+                   "record_bytes_per_row": info_c["record_bytes"], "algorithmic_bytes_per_nnz": alg_bytes / nnz,
                    "l2": f"inputs {(info_c['format_bytes'] + 16 * n) / 1e6:.0f} MB > 129 MB L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -561,7 +571,7 @@ def main():
         "paper_context_gflops": {"pezy_sc_ell": 11.6, "pezy_sc_data_index_table": 32.4},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(y_check=y_fast)
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)
