@@ -323,6 +323,23 @@ def test_cg_krylov_termination_2x2x2():
     assert np.allclose(A @ x, b, rtol=0, atol=1e-13)
 
 
+def test_cg_krylov_termination_4x4x4():
+    """On 4^3 the closed-form spectrum 27 - prod_d (1 + 2 cos(k_d pi / 5))
+    has 19 distinct values, so exact CG ends within 19 steps for any b; the
+    oracle's CG reaches 1e-13 within that count."""
+    import math
+    f = [1 + 2 * math.cos(k * math.pi / 5) for k in range(1, 5)]
+    distinct = len({round(27 - a * b * c, 9) for a in f for b in f for c in f})
+    assert distinct == 19
+    rowptr, col, val = oracle.hpcg_csr(4, 4, 4)
+    A = csr_to_dense(rowptr, col, val, 64)
+    assert len(np.unique(np.round(np.linalg.eigvalsh(A), 9))) == distinct
+    b = spmv_inputs.uniform_vector(64, seed=3)
+    x, it, hist = oracle.cg(rowptr, col, val, b, tol=1e-13, maxit=200)
+    assert hist[-1] <= 1e-13 and it <= distinct
+    assert np.allclose(A @ x, b, rtol=0, atol=1e-12)
+
+
 # --------------------------------------------------------------------------
 # Irregular variant: construction invariants
 # --------------------------------------------------------------------------
