@@ -515,6 +515,22 @@ def main():
     assert P.spmv_device_error(C) == 0
     y_fast = y.cpu().numpy()          # the timed product, checked against the oracle on the CPU leg
 
+    # cold-L2 variant: each product timed alone right after writing a buffer
+    # twice the size of L2 (median of 30)
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 129 * 2 ** 20)
+    flush = torch.empty(2 * l2_bytes // 4, dtype=torch.int32, device=dev)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cold = []
+    for i in range(30):
+        flush.fill_(i)
+        c0.record(stream)
+        P.spmv_apply(C, x, y, stream)
+        c1.record(stream)
+        c1.synchronize()
+        cold.append(c0.elapsed_time(c1) * 1e3)
+    del flush
+    cold_us = statistics.median(cold)
+
     # end to end through the host-buffer entry point: x H2D, SpMV, y D2H
     hx = torch.from_numpy(x_np).pin_memory()
     hy = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -564,6 +580,8 @@ def main():
                 "frac": ell_alg_bytes / (ell_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "compressed_column_order": {"gflops": world * flops / (col_ms * 1e-3) / 1e9, "ms_per_step": col_ms},
         "speedup_vs_ell": ell_ms / ms,
+        "cold_l2": {"median_us": cold_us, "gflops": 2.0 * nnz / cold_us / 1e3, "flush_bytes": 2 * l2_bytes,
+                    "launches": 30},
         "clocks": clocks,
         "e2e": {"value": world * flops / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "steps": e2e_steps},
