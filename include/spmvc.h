@@ -51,7 +51,8 @@ extern "C" {
 #define SPMV_ECORRUPT 4        /* compressed stream fails its checksum/bounds check */
 #define SPMV_EUNSUPPORTED 5    /* matrix does not fit the requested format */
 #define SPMV_ENOTCONVERGED 6   /* cg_solve hit max_iter before the tolerance */
-#define SPMV_ETIMEOUT 7        /* a bounded device-side wait gave up */
+#define SPMV_ETIMEOUT 7        /* reserved, never returned: no kernel of the
+                                  library waits on a device-side condition */
 #define SPMV_EDEVICE 8         /* a kernel reported a decoding error */
 
 typedef struct spmv_mat_s *spmv_mat_t;
@@ -93,10 +94,28 @@ typedef struct {
 /* Builds a plain matrix from a generator.
  * HPCG (Sec. III-A): the 27-point stencil on an nx*ny*nz grid, node
  * i = ix + nx*(iy + ny*iz), diagonal 26 and -1 for every neighbour inside
- * the grid (Fig. 2 values).  IRREGULAR: the same stencil with links
- * dropped, unique values on a fraction of rows and a random renumbering
- * (the construction is spelled out in the design notes).  *out receives a
- * new handle of format SPMV_FMT_ELL. */
+ * the grid (Fig. 2 values).
+ * IRREGULAR (the paper motivates irregular grids without fixing one; this
+ * is the library's construction).  Random numbers come from SplitMix64: the
+ * stream for a purpose starts from the first output of a SplitMix64 seeded
+ * with seed XOR the purpose name's ASCII bytes read little-endian; a draw is
+ * u = (next >> 11) * 2^-53, and an index below m is min(floor(u m), m - 1).
+ * Steps:
+ *  1. "special": floor(special_frac * n) special nodes, the first picks of
+ *     a partial Fisher-Yates shuffle of 0..n-1 (slot t, from 0 up, swaps
+ *     with slot t + (an index below n - t));
+ *  2. links: every stencil pair i < j, i ascending, then j ascending; one
+ *     "drop" draw a link removes it (both a_ij and a_ji) when
+ *     u < drop_prob; a kept link then takes one "val" draw: -2 + 1.9 u (in
+ *     [-2, -0.1)) when either end is special, else the level -1.5 + k/15
+ *     with k an index below 16; a_ji = a_ij;
+ *  3. diagonal: 1.05 * s on special rows, s = sum_j |a_ij| added left to
+ *     right in ascending column order; on the others 26 (diag_rule 0) or
+ *     max(26, 1.05 * s) (diag_rule 1);
+ *  4. "perm" (permute = 1): a full Fisher-Yates shuffle p of 0..n-1 (slot t,
+ *     from n-1 down to 1, swaps with an index below t + 1), old node k
+ *     becoming node p[k]; the stored matrix is P A P^T, columns ascending.
+ * *out receives a new handle of format SPMV_FMT_ELL. */
 int spmv_build(const spmv_gen_desc *desc, spmv_mat_t *out);
 
 /* Builds a plain matrix from host CSR arrays (copied; the caller keeps
@@ -214,10 +233,20 @@ int spmv_import(const void *buf, size_t len, spmv_mat_t *out);
 
 /* y = A x.  x and y: device pointers to n doubles.  Enqueued on stream.
  * COLUMN order gives exactly the plain CSR fma chain.  FAST order (pattern
- * format) converts x to 53-bit fixed point scaled by the largest |x_j|,
- * sums each row exactly in integers and rounds once:
- * |y_i - (A x)_i| <= sum_j |a_ij| * ulp(max_j |x_j|) + ulp(y_i)/2.
- * Non-finite x falls back to the COLUMN kernel on the device. */
+ * format) converts x to 53-bit fixed point scaled by the largest exponent
+ * among the x entries a CTA reads (never above that of max_j |x_j|), sums
+ * each row exactly in integers and rounds once, so for every row
+ *   |y_i - (A x)_i| <= sum_j |a_ij| * ulp(max_j |x_j|) + ulp(y_i)/2.
+ * Componentwise accuracy is therefore relative to the largest |x_j|, not to
+ * the row's own terms: |y_i - (A x)_i| <= 1e-14 * sum_j |a_ij x_j| holds on
+ * every row with
+ *   sum_j |a_ij x_j| >= C * sum_j |a_ij| * max_j |x_j|,
+ *   C = 2^-52 / (1e-14 - 2^-53), about 0.0225,
+ * i.e. rows whose |a|-weighted mean |x_j| is at least 2.25 % of max |x|
+ * (every row, in practice, of x drawn uniformly from [-1, 1)); a row of
+ * tiny entries next to a huge one elsewhere gets only the first bound.
+ * Zero/subnormal-only or non-finite x falls back to the COLUMN order on the
+ * device (per CTA for the tiled kernels). */
 int spmv_apply(spmv_mat_t A, const double *x, double *y, spmv_stream_t stream);
 
 /* y = A x with x and y in host memory: copies x to the device, runs
@@ -241,7 +270,10 @@ int spmv_apply_f32(spmv_mat_t A, const float *x, float *y, spmv_stream_t stream)
 
 /* Y = A X for k right-hand sides, X (n x k, leading dimension ldx >= k) and
  * Y (n x k, ldy >= k) row-major device arrays of doubles, 1 <= k <= 64.
- * Each column of Y obeys spmv_apply's rule for the handle's order. */
+ * Each column of Y obeys spmv_apply's rule for the handle's order.  FAST
+ * order keeps per-column exponent words and a fixed-point copy of X with
+ * the handle: calls on one handle whose kernels can overlap on the GPU
+ * (different streams without ordering) race on them. */
 int spmm_apply(spmv_mat_t A, int32_t k, const double *X, int64_t ldx, double *Y,
                int64_t ldy, spmv_stream_t stream);
 
@@ -327,7 +359,9 @@ typedef struct spmv_batch_s *spmv_batch_t;
  * is uploaded once and the launch is captured in a CUDA graph. */
 int spmv_batch_create(int32_t count, const spmv_mat_t *mats, const double *const *xs,
                       double *const *ys, spmv_batch_t *out);
-/* Replays the plan's graph on stream (one persistent kernel launch). */
+/* Replays the plan's graph on stream (one persistent kernel launch).  Each
+ * replay resets and then draws from the plan's one work counter, so two
+ * launches of the same plan must not overlap on the GPU. */
 int spmv_batch_launch(spmv_batch_t plan, spmv_stream_t stream);
 int spmv_batch_free(spmv_batch_t plan);
 /* create + launch + wait + free, for one-off use. */

@@ -2,12 +2,16 @@
 // callers that must not allocate device memory -- for instance code running
 // inside a framework that owns every device allocation through its own
 // pool, or a latency-critical loop where the implicit device
-// synchronisation of cudaMalloc/cudaFree is not acceptable.  The kernels are
-// the ones spmm_apply uses; the only difference is where their scratch
-// lives.  The scratch -- one maximum-exponent word per (block of the
-// column-maxima pass, right-hand side) -- is a file-scope device array of
-// fixed size, so every GPU that loads the library holds it (19.5 KB) until
-// the process exits.
+// synchronisation of cudaMalloc/cudaFree is not acceptable.  It runs the
+// generic FAST SpMM path on the unconverted X: a column-maxima pass, then one
+// thread per (row, column) converting X entries as it reads them.  It does
+// not take spmm_apply's faster route for the full 27-point union (X
+// converted once into a fixed-point copy, then the row-wise kernels), since
+// that copy would need an allocation of n * k * 8 bytes; the two paths agree
+// within FAST order's error bound, not bit for bit.  The scratch -- one
+// maximum-exponent word per (block of the column-maxima pass, right-hand
+// side) -- is a file-scope device array of fixed size, so every GPU that
+// loads the library holds it (19.5 KB) until the process exits.
 #include <mutex>
 
 #include "spmvc_internal.h"
@@ -63,7 +67,8 @@ extern "C" int spmm_apply_noalloc(spmv_mat_t A, int32_t k, const double* X, int6
     if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || !A->perm.empty())
         return spmvc::fail(SPMV_EUNSUPPORTED, "spmm_apply_noalloc needs a pattern-format matrix in FAST order, not reordered");
     int dev = 0;
-    cudaGetDevice(&dev);
+    const cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return spmvc::fail(SPMV_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(de));
     if (A->device < 0 || A->device != dev)
         return spmvc::fail(SPMV_EINVAL, "the matrix is not on the current device yet: make one ordinary device call "
                                         "on it first (that call copies it and may allocate)");

@@ -23,49 +23,11 @@ namespace spmvc {
 
 namespace {
 
+#include "fast_fixed.cuh"
+
 constexpr int kBlock = 256;
 constexpr int kXmaxBlocks = 152;  // partial maxima written by the pre-pass
 
-__device__ __forceinline__ void raise_error(int32_t* err, int32_t code) {
-    if (err) atomicOr(err, code);
-}
-
-// PTX prmt in its default mode: for each result byte a 4-bit selector picks
-// one of the 8 source bytes; a set selector msb replicates that byte's sign.
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-// Signed multiplier of value code c (< 8) from the packed int8 table.
-__device__ __forceinline__ int32_t mult_of(uint32_t lo, uint32_t hi, uint32_t c) {
-    return int32_t(prmt(lo, hi, (c & 7u) * 0x1111u + 0x8880u));
-}
-
-__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[kMaxRecordWords], int u) {
-    return (w[u >> 2] >> (8 * (u & 3))) & 0xFFu;
-}
-
-// Row record of the pattern format: `WORDS` 32-bit words split over up to
-// three planes indexed by row, so each warp load is one contiguous run.
-template <int WORDS>
-__device__ __forceinline__ void load_record(const PatternView& a, int64_t r, uint32_t (&w)[kMaxRecordWords]) {
-    constexpr int q16 = WORDS / 4, rem = WORDS % 4;
-    if (q16 >= 1) {
-        const uint4 v = __ldcs(a.p16a + r);
-        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-    }
-    if (q16 >= 2) {
-        const uint4 v = __ldcs(a.p16b + r);
-        w[4] = v.x; w[5] = v.y; w[6] = v.z; w[7] = v.w;
-    }
-    if (rem >= 2) {
-        const uint2 v = __ldcs(a.p8 + r);
-        w[4 * q16] = v.x; w[4 * q16 + 1] = v.y;
-    }
-    if (rem & 1) w[WORDS - 1] = __ldcs(a.p4 + r);
-}
 
 
 // true when the row's record equals the matrix's dominant record
@@ -75,6 +37,16 @@ __device__ __forceinline__ bool is_dominant(const PatternView& a, const uint32_t
 #pragma unroll
     for (int k = 0; k < WORDS; ++k) eq = eq && (w[k] == a.dom_w[k]);
     return eq;
+}
+
+// Warp vote: true when every row of the warp carries the dominant record.
+// All 32 lanes must reach the call (callers never return or break out of a
+// row loop before it): a lane whose row lies past the matrix votes true and
+// stores nothing, so the full-warp mask is exact.
+template <int WORDS>
+__device__ __forceinline__ bool warp_dominant(const PatternView& a, const uint32_t (&w)[kMaxRecordWords],
+                                              bool valid) {
+    return __all_sync(0xFFFFFFFFu, !valid || is_dominant<WORDS>(a, w));
 }
 
 // ------------------------------------------------------------- ELL -------
@@ -185,63 +157,6 @@ __device__ __forceinline__ int block_emax(const uint32_t* __restrict__ partial, 
     return *s_emax;
 }
 
-// x -> X = sign(x) * floor(|x| * 2^(1075 - E)) as two limbs X = xh*2^26 + xl
-// (both carrying the sign), integer operations only.
-__device__ __forceinline__ void to_fixed(double xv, int emax, int32_t& xh, int32_t& xl) {
-    const uint32_t hi = uint32_t(__double2hiint(xv)), lo = uint32_t(__double2loint(xv));
-    const uint32_t k = uint32_t(emax) - ((hi >> 20) & 0x7FFu);
-    const uint64_t mant = (uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
-    uint64_t X;
-    asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"(mant), "r"(k));  // shifts >= 64 give 0
-    const int32_t sgn = int32_t(hi) >> 31;
-    xl = (int32_t(uint32_t(X) & 0x3FFFFFFu) ^ sgn) - sgn;
-    xh = (int32_t(X >> 26) ^ sgn) - sgn;
-}
-
-// acc * 2^S rounded to nearest-even, integer operations only (subnormal
-// results are rounded to their shorter precision, overflow gives +-inf).
-__device__ __noinline__ double fixed_to_double_int(int64_t acc, int S) {
-    if (acc == 0) return 0.0;
-    const uint64_t sgn = acc < 0 ? 0x8000000000000000ull : 0ull;
-    uint64_t a = acc < 0 ? uint64_t(0) - uint64_t(acc) : uint64_t(acc);
-    const int lz = __clzll(a);
-    a <<= lz;                                   // leading one at bit 63
-    const int e = 63 - lz + S + 1023;           // biased exponent if normal
-    // bits of `a` below the kept mantissa: 11 for a normal result, more for a
-    // subnormal one (the field then holds the value / 2^-1074 directly)
-    const int drop = e >= 1 ? 11 : 12 - e;
-    uint64_t mant, rest;
-    if (drop >= 65) { mant = 0; rest = 0; }             // below half the smallest subnormal
-    else if (drop == 64) { mant = 0; rest = a; }
-    else { mant = a >> drop; rest = a << (64 - drop); }
-    const uint64_t half = 0x8000000000000000ull;
-    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
-    uint64_t bits;
-    if (e >= 1) {
-        // mant in [2^52, 2^53]; a carry to 2^53 moves into the exponent field
-        bits = (uint64_t(e - 1) << 52) + mant;
-        if (e - 1 + int(mant >> 52) >= 2047) bits = 0x7FF0000000000000ull;
-    } else {
-        bits = mant;  // subnormal; a carry to 2^52 becomes the smallest normal
-    }
-    return __longlong_as_double(int64_t(sgn | bits));
-}
-
-// acc * 2^S rounded to nearest-even.  The int64 -> binary64 conversion
-// rounds once (RN); scaling by 2^S is then an exact add to the exponent
-// field unless the result leaves the normal range, which the integer
-// routine above handles.
-__device__ __forceinline__ double fixed_to_double(int64_t acc, int S) {
-    const double d = __ll2double_rn(acc);
-    const int32_t hi = __double2hiint(d);
-    const int ef = (hi >> 20) & 0x7FF;          // 0 exactly when acc == 0
-    // the exponent moves by S in the high word: unsigned arithmetic, since a
-    // negative S shifted left is undefined in C++17
-    if (ef != 0 && uint32_t(ef + S - 1) < 2046u)
-        return __hiloint2double(int32_t(uint32_t(hi) + (uint32_t(S) << 20)), __double2loint(d));
-    return ef == 0 ? d : fixed_to_double_int(acc, S);
-}
-
 template <int WORDS>
 __global__ void __launch_bounds__(kBlock) pattern_fast_kernel(PatternView a, const double* __restrict__ x,
                                                               double* __restrict__ y,
@@ -347,11 +262,15 @@ __global__ void __launch_bounds__(kBlock, 6) pattern_fast_x_kernel(PatternView a
                                                                 const uint32_t* __restrict__ partial) {
     // the largest exponent of x, left by the conversion pass
     const int emax = int(__ldg(partial + kXmaxBlocks));
-    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (r >= a.n) return;
+    const int64_t r0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    // every lane stays for the warp vote: a lane past the last row works on
+    // the last row and stores nothing
+    const bool valid = r0 < a.n;
+    const int64_t r = valid ? r0 : a.n - 1;
     uint32_t w[kMaxRecordWords];
     load_record<WORDS>(a, r, w);
     if (emax < 64 || emax >= 2047) {
+        if (!valid) return;
         const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
         double acc = 0.0;
 #pragma unroll
@@ -366,7 +285,7 @@ __global__ void __launch_bounds__(kBlock, 6) pattern_fast_x_kernel(PatternView a
     // dependency chains
     const int2* __restrict__ Xr = X + r;
     int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
-    if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+    if (warp_dominant<WORDS>(a, w, valid)) {
         // the warp's rows all carry the dominant record: multipliers are
         // kernel parameters
 #pragma unroll
@@ -398,7 +317,7 @@ __global__ void __launch_bounds__(kBlock, 6) pattern_fast_x_kernel(PatternView a
         }
     }
     const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
-    y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+    if (valid) y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
 }
 
 // ---------------------------------------------- FAST order, staged -------
@@ -411,17 +330,6 @@ __global__ void __launch_bounds__(kBlock, 6) pattern_fast_x_kernel(PatternView a
 // addressed by absent slots, whose multiplier is 0.  Everything is integer:
 // x is moved as raw 64-bit words and never touches the FP64 pipe.
 constexpr int kStageThreads = 512;
-
-// (lo, hi) words of x -> limbs (xl, xh) of X = sign(x) floor(|x| 2^(1075-E)),
-// X = xh 2^26 + xl with both limbs carrying the sign.
-__device__ __forceinline__ int2 fixed_limbs(uint32_t lo, uint32_t hi, uint32_t emax) {
-    const uint32_t k = emax - ((hi >> 20) & 0x7FFu);
-    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
-    uint64_t X;
-    asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"((uint64_t(mh) << 32) | lo), "r"(k));
-    const int32_t s1 = (int32_t(hi) >> 31) | 1;  // +1 or -1
-    return make_int2(int32_t(uint32_t(X) & 0x3FFFFFFu) * s1, int32_t(uint32_t(X >> 26)) * s1);
-}
 
 // 16-byte cp.async copy global -> shared of the first nbytes (0..16) of the
 // source, zero-filling the rest (nbytes == 0 reads nothing).
@@ -453,7 +361,10 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
     for (int i = 0; i < RPT; ++i) {
         const int rl = tid + i * THREADS;
         const int64_t r = r0 + rl;
-        if (r >= a.n) break;
+        // rows past the matrix are summed from the tile's (zero-filled)
+        // windows like the others, so the whole warp reaches the vote, and
+        // are not stored
+        const bool valid = r < a.n;
         uint32_t wn[kMaxRecordWords];
         uint32_t tnext = 0;
         if constexpr (RECS == 1) {
@@ -476,15 +387,17 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
         }
         if (exact_path) {
             // zeros/denormals only, or non-finite values: the COLUMN order
-            const uint32_t mask = smask[byte_of(w, NU) & 31];
-            double acc = 0.0;
+            if (valid) {
+                const uint32_t mask = smask[byte_of(w, NU) & 31];
+                double acc = 0.0;
 #pragma unroll
-            for (int u = 0; u < NU; ++u)
-                if ((mask >> u) & 1u) {
-                    const int2 b = sx[rl + off(u)];
-                    acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
-                }
-            y[r] = acc;
+                for (int u = 0; u < NU; ++u)
+                    if ((mask >> u) & 1u) {
+                        const int2 b = sx[rl + off(u)];
+                        acc = fma(__ldg(a.dict + (byte_of(w, u) & 7)), __hiloint2double(b.y, b.x), acc);
+                    }
+                y[r] = acc;
+            }
             if (RECS == 0 && i + 1 < RPT) {
 #pragma unroll
                 for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
@@ -493,7 +406,7 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
             continue;
         }
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
-        const bool dom = __all_sync(__activemask(), is_dominant<WORDS>(a, w));
+        const bool dom = warp_dominant<WORDS>(a, w, valid);
         if (NU == 27 && RUN == 3 && dom && a.dom_uni) {
             // uniform neighbour weights: sum the 26 neighbour limbs exactly in
             // 32-bit integers (|xh| < 2^27: two partial sums of 13 terms;
@@ -547,7 +460,7 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
             }
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
-        y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
+        if (valid) y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
         if (RECS == 0 && i + 1 < RPT) {
 #pragma unroll
             for (int k = 0; k < WORDS; ++k) w[k] = wn[k];
@@ -556,10 +469,10 @@ __device__ __forceinline__ void tile_rows(const PatternView& a, Off off, const i
     }
 }
 
-// Eight rows a thread keep more values live than the 40-register budget of
-// six resident 256-thread CTAs allows; that shape gets three CTAs' worth.
+// Every shape is held to the register budget of 1536 resident threads a SM
+// (40 registers at 256 threads); eight rows a thread then spill a little.
 template <int WORDS, int NU, int RPT, int RUN, int THREADS, bool VEC>
-__global__ void __launch_bounds__(THREADS, RPT >= 8 ? 768 / THREADS : 1536 / THREADS)
+__global__ void __launch_bounds__(THREADS, 1536 / THREADS)
     pattern_fast_staged_kernel(PatternView a, StagePlan sp,
                                                                                     const double* __restrict__ x,
                                                                                     double* __restrict__ y) {
@@ -991,11 +904,15 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_xstaged_kernel(
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
         const int rl = tid + i * kStageThreads;
-        const int64_t r = r0 + rl;
-        if (r >= a.n) break;
+        // a row past the matrix reads the last row's record, is summed from
+        // the tile's windows so the whole warp reaches the vote, and is not
+        // stored
+        const bool valid = r0 + rl < a.n;
+        const int64_t r = valid ? r0 + rl : a.n - 1;
         uint32_t w[kMaxRecordWords];
         load_record<WORDS>(a, r, w);
         if (exact_path) {
+            if (!valid) continue;
             const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
             double acc = 0.0;
 #pragma unroll
@@ -1006,7 +923,7 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_xstaged_kernel(
             continue;
         }
         int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
-        if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+        if (warp_dominant<WORDS>(a, w, valid)) {
 #pragma unroll
             for (int k = 0; k < NU / RUN; ++k) {
                 const int2* p = sx + rl + sp.soff_padded[k * RUN];
@@ -1036,7 +953,7 @@ __global__ void __launch_bounds__(kStageThreads, 3) pattern_fast_xstaged_kernel(
             }
         }
         const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
-        y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
+        if (valid) y[r] = fixed_to_double(acc, emax - 1075 + a.mult_exp);
     }
 }
 
@@ -1196,7 +1113,10 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
             __syncthreads();
         }
         const int64_t r = tile * kAsyncRows + tid;
-        if (r < a.n) {
+        // rows past the matrix read the zero-filled end of the tile's buffer,
+        // so the whole warp reaches the vote; they are not stored
+        const bool valid = r < a.n;
+        {
             uint32_t w[kMaxRecordWords];
             {
                 const uint4 v16 = cur.r16[tid];
@@ -1213,10 +1133,10 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
                         const int2 b = cur.xw[tid + sp.soff[u]];   // raw copies (unpadded layout)
                         acc = fma(sdict[byte_of(w, u) & 7], __hiloint2double(b.y, b.x), acc);
                     }
-                y[r] = acc;
+                if (valid) y[r] = acc;
             } else {
                 int64_t ah[3] = {0, 0, 0}, al[3] = {0, 0, 0};
-                if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+                if (warp_dominant<WORDS>(a, w, valid)) {
 #pragma unroll
                     for (int k = 0; k < NU / RUN; ++k) {
                         const int2* p = cur.xw + tid + (soff_shift ? sp.soff_padded[k * RUN] : sp.soff[k * RUN]);
@@ -1247,7 +1167,7 @@ __global__ void __launch_bounds__(kAsyncThreads, 1) pattern_fast_async_kernel(Pa
                     }
                 }
                 const int64_t acc = (ah[0] + ah[1] + ah[2]) * (int64_t(1) << 26) + (al[0] + al[1] + al[2]);
-                y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
+                if (valid) y[r] = fixed_to_double(acc, int(emax) - 1075 + a.mult_exp);
             }
         }
         // the barrier at the top of the next iteration keeps `cur` from being
@@ -1336,9 +1256,12 @@ __global__ void __launch_bounds__(kBlock, 2) pattern_spmm_rows_kernel(PatternVie
     constexpr int WORDS = (NU + 4) / 4;
     const int ng = k / KC;
     const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t r = idx / ng;
-    const int g = int(idx - r * ng);
-    if (r >= a.n) return;
+    const int64_t r0 = idx / ng;
+    const int g = int(idx - r0 * ng);
+    // every lane stays for the warp vote below: a lane past the last row
+    // reads the last row's record and returns after the vote
+    const bool valid = r0 < a.n;
+    const int64_t r = valid ? r0 : a.n - 1;
     const int c0 = g * KC;
     int em[KC];
     bool exact = false;
@@ -1349,6 +1272,10 @@ __global__ void __launch_bounds__(kBlock, 2) pattern_spmm_rows_kernel(PatternVie
     }
     uint32_t w[kMaxRecordWords];
     load_record<WORDS>(a, r, w);
+    // lanes on the exact path (their columns hold no finite nonzero scale)
+    // vote true: they do not use the multipliers
+    const bool dom = warp_dominant<WORDS>(a, w, valid && !exact);
+    if (!valid) return;
     if (exact) {
         const uint32_t mask = __ldg(a.pmask_dev + (byte_of(w, NU) & 31));
 #pragma unroll 1
@@ -1365,7 +1292,7 @@ __global__ void __launch_bounds__(kBlock, 2) pattern_spmm_rows_kernel(PatternVie
     // the row's multipliers, once (kernel parameters when the whole warp
     // carries the dominant record)
     int32_t mult[NU];
-    if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+    if (dom) {
 #pragma unroll
         for (int u = 0; u < NU; ++u) mult[u] = a.dom_m[u];
     } else {
@@ -1426,13 +1353,18 @@ __global__ void __launch_bounds__(kBlock) pattern_f32_kernel(PatternView a, cons
     for (int i = threadIdx.x; i < 256; i += blockDim.x) sdict[i] = i < a.dict_size ? a.dict32[i] : 0.0f;
     if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
     __syncthreads();
-    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (r >= a.n) return;
+    const int64_t r0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    // every lane stays for the warp vote: a lane past the last row reads the
+    // last row's record and returns after the vote
+    const bool valid = r0 < a.n;
+    const int64_t r = valid ? r0 : a.n - 1;
     uint32_t w[kMaxRecordWords];
     load_record<WORDS>(a, r, w);
     const float* __restrict__ xr = x + r;
     float acc = 0.0f;
-    if (__all_sync(__activemask(), is_dominant<WORDS>(a, w))) {
+    const bool dom = warp_dominant<WORDS>(a, w, valid);
+    if (!valid) return;
+    if (dom) {
         // every row of the warp carries the dominant record: all slots
         // present, values are kernel parameters
 #pragma unroll

@@ -183,6 +183,85 @@ def test_spmv_f32_matches_float_arithmetic():
     assert np.array_equal(y, oracle.spmv(rowptr, col, val, x.astype(np.float64)).astype(np.float32))
 
 
+def pow2(e):
+    from fractions import Fraction
+    return Fraction(2) ** e if e >= 0 else Fraction(1, 2 ** -e)
+
+
+def round_binary32(q):
+    """The binary32 number nearest to the rational q, ties to even (IEEE 754
+    round-to-nearest-even), subnormals included; overflow is not reached by
+    the inputs used here."""
+    from fractions import Fraction
+    if q == 0:
+        return Fraction(0)
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if pow2(e) > a:
+        e -= 1                       # now 2^e <= a < 2^(e+1)
+    e = max(e, -126)                 # subnormal range: fixed quantum 2^-149
+    quantum = pow2(e - 23)
+    m = a / quantum
+    f = m.numerator // m.denominator
+    rest = m - f
+    if rest > Fraction(1, 2) or (rest == Fraction(1, 2) and f % 2 == 1):
+        f += 1
+    return (f * quantum) if q > 0 else -(f * quantum)
+
+
+def exact_binary32_csr(rowptr, col, val, x32):
+    """Each row: s = 0; s = RN32(RN32(a_ij) * x_j + s) in ascending column
+    order, every step evaluated exactly in rationals and rounded once, which
+    is what an fmaf chain computes."""
+    from fractions import Fraction
+    xs = [Fraction(float(v)) for v in x32.tolist()]
+    vs = [round_binary32(Fraction(float(v))) for v in val.tolist()]
+    out = np.empty(len(rowptr) - 1, np.float32)
+    for i in range(len(rowptr) - 1):
+        s = Fraction(0)
+        for k in range(rowptr[i], rowptr[i + 1]):
+            s = round_binary32(vs[k] * xs[col[k]] + s)
+        out[i] = np.float32(float(s))
+    return out
+
+
+def test_round_binary32_against_numpy():
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    for d in np.concatenate([rng.uniform(-3, 3, 300), rng.uniform(-1e-40, 1e-40, 50), [1.0 + 2.0 ** -24]]):
+        assert np.float32(float(round_binary32(Fraction(float(d))))) == np.float32(d)
+
+
+@pytest.mark.parametrize("which", ["hpcg", "irregular"])
+def test_spmv_f32_rounds_every_fma_step(which):
+    """Non-integer x: the binary32 product equals the exact model of an fmaf
+    chain (one rounding per step) bit for bit.  The irregular matrix's values
+    (-1.5 + k/15, U[-2,-0.1)) are not binary32 numbers, so the rounding of
+    each value to binary32 is pinned too."""
+    if which == "hpcg":
+        rowptr, col, val = oracle.hpcg_csr(5, 4, 6)
+    else:
+        rowptr, col, val, _ = oracle.irregular_csr(6, 5, 4, seed=2)
+    n = len(rowptr) - 1
+    x32 = spmv_inputs.uniform_vector(n, seed=11).astype(np.float32)
+    want = exact_binary32_csr(rowptr, col, val, x32)
+    got = oracle.spmv_f32(rowptr, col, val, x32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    # planted slips, each of which this pin must tell apart from the model:
+    # (a) accumulation in binary64, one rounding at the end
+    v32 = val.astype(np.float32).astype(np.float64)
+    slip_a = oracle.spmv(rowptr, col, v32, x32.astype(np.float64)).astype(np.float32)
+    assert not np.array_equal(slip_a, want)
+    # (b) separate binary32 multiply and add (no fused multiply-add)
+    slip_b = np.empty(n, np.float32)
+    for i in range(n):
+        s = np.float32(0)
+        for k in range(rowptr[i], rowptr[i + 1]):
+            s = np.float32(np.float32(np.float32(val[k]) * x32[col[k]]) + s)
+        slip_b[i] = s
+    assert not np.array_equal(slip_b, want)
+
+
 def test_spmm_columns_match_spmv():
     nx, ny, nz = 7, 5, 6
     n = nx * ny * nz
@@ -356,7 +435,12 @@ def test_irregular_symmetric_and_signs(irregular_small):
     assert np.array_equal(A, A.T)
     rows = np.repeat(np.arange(n), np.diff(rowptr))
     off = val[col != rows]
-    assert np.all(off < 0) and np.all(off >= -2.0)
+    # special links are U[-2,-0.1), ordinary ones the levels -1.5 .. -0.5
+    assert np.all(off < -0.1) and np.all(off >= -2.0)
+    levels = -1.5 + np.arange(16) / 15.0
+    on_level = np.isin(off, levels)
+    assert 0 < np.sum(~on_level) < off.size
+    assert np.max(off[~on_level]) < -0.1 and np.min(off[~on_level]) >= -2.0
     assert np.all(np.diff(col)[np.diff(rows) == 0] > 0)
 
 
