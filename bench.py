@@ -460,11 +460,12 @@ def main():
     info_c = P.spmv_info(C)
     variant = info_c["fast_variant"]
     tile, threads = info_c["fast_tile_rows"], info_c["fast_block_threads"]
-    launches_per_step = {0: 2, 1: 1, 2: 3, 3: 3, 4: 1, 5: 3, 6: 1, 7: 2, 8: 1, 9: 1, 10: 1}[variant]
+    launches_per_step = {0: 2, 1: 1, 2: 3, 3: 3, 4: 1, 5: 3, 6: 1, 7: 2, 8: 1, 9: 1, 10: 1, 11: 1}[variant]
     kernel_id = {0: "direct", 1: "staged%dt%d" % (tile, threads), 2: "preconverted", 3: "xstaged%d" % tile,
                  4: "persistent", 5: "persistent_x", 6: "rstaged%dt%d" % (tile, threads),
                  7: "zmarch%dt%d" % (tile, threads), 8: "rstaged_srec%dt%d" % (tile, threads),
-                 9: "rstaged_types%dt%d" % (tile, threads), 10: "zblock%dt%d" % (tile, threads)}[variant]
+                 9: "rstaged_types%dt%d" % (tile, threads), 10: "zblock%dt%d" % (tile, threads),
+                 11: "tma%dt%d" % (tile, threads)}[variant]
     kernel_desc = {0: "xmax pre-pass + pattern_fast_kernel",
                    1: "pattern_fast_staged_kernel (%d-row shared-memory tiles, %d threads)" % (tile, threads),
                    2: "xmax + convert_x pre-passes + pattern_fast_x_kernel",
@@ -476,7 +477,9 @@ def main():
                    8: "pattern_fast_rstaged_kernel, records in shared memory (%d-row tiles, %d threads)" % (tile, threads),
                    9: "pattern_fast_rstaged_kernel, one-byte row types (%d-row tiles, %d threads)" % (tile, threads),
                    10: "pattern_fast_zblock_kernel (512-row column blocks of %d planes, %d threads)"
-                       % (tile // 512, threads)}[variant]
+                       % (tile // 512, threads),
+                   11: "pattern_fast_tma_kernel (persistent z-marching, TMA-fed %d-row column blocks, %d threads)"
+                       % (tile, threads)}[variant]
 
     def timed(M, steps):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -329,8 +329,9 @@ def cg_solve(A: SpmvMatrix, b, x, tol: float = 1e-10, max_iter: int = 10000, mod
 def spmv_autotune(A: SpmvMatrix, x, y, reps: int = 10) -> int:
     """Times A's kernel configurations on x, y (CUDA float64), each first
     checked against the COLUMN-order product; returns the chosen tile rows
-    (z-block kernel: rows a CTA computes), 1 for the pre-converted kernel,
-    4 or 5 for the persistent ones, 0 if nothing to tune."""
+    (z-block kernel: rows a CTA computes; TMA kernel: rows of its column
+    block), 1 for the pre-converted kernel, 4 or 5 for the persistent ones,
+    0 if nothing to tune."""
     c = _i32(0)
     _check(library().spmv_autotune(A, _dptr(x, "float64"), _dptr(y, "float64"), reps, ctypes.byref(c)))
     return c.value
@@ -340,15 +341,17 @@ def spmv_set_variant(A: SpmvMatrix, variant: int, tile_rows: int = 0) -> None:
     """FAST kernel by hand: 0 direct, 1 staged tiles (tile_rows), 2 pre-converted x,
     3 staged tiles of that copy, 4/5 persistent double-buffered tiles,
     6 register-staged tiles, 7 z-marching tiles, 8 register-staged with
-    records in shared memory, 9 the same reading one-byte row types
-    (shapes and conditions in spmvc.h; 10 needs spmv_set_tile)."""
+    records in shared memory, 9 the same reading one-byte row types,
+    11 the TMA z-marching kernel (shapes and conditions in spmvc.h; 10
+    needs spmv_set_tile)."""
     _check(library().spmv_set_variant(A, variant, tile_rows))
 
 
 def spmv_set_tile(A: SpmvMatrix, variant: int, tile_rows: int, block_threads: int) -> None:
     """spmv_set_variant with the staged kernel's block size (512, or 256 on
     the full 27-slot union); variant 10, the z-block kernel, takes 256 with
-    tile_rows = 512 x planes (1536 or 2048)."""
+    tile_rows = 512 x planes (1536 or 2048); variant 11 ignores both (its
+    block is whole grid lines, four rows a thread)."""
     _check(library().spmv_set_tile(A, variant, tile_rows, block_threads))
 
 

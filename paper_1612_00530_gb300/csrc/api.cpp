@@ -298,6 +298,22 @@ int ensure_device(spmv_mat_s* m) {
         m->zbplan_ok = false;
         if (m->fast_variant == 10 && p.fast_ok && v.run_len == 3 && v.nu == 27 && v.words == 7)
             m->zbplan_ok = make_zblock_plan(p.uoff, m->n, tuned_stage_shape(m, 256, 3).second, 256, &m->zbplan);
+        // TMA z-marching kernel: its plan and the table of the record each
+        // boundary class of grid position implies
+        m->tplan_ok = false;
+        {
+            std::vector<uint32_t> tab;
+            // rows a thread: the autotuner's pick for matrices of this shape, else 2
+            const int rpt = m->fast_variant == 11 ? tuned_stage_shape(m, 0, 2).second : 2;
+            if (make_tma_plan(p, v, m->n, m->num_sms, rpt, &m->tplan, &tab) ||
+                make_tma_plan(p, v, m->n, m->num_sms, 6 - rpt, &m->tplan, &tab)) {
+                uint32_t* dt;
+                if ((st = dev_copy(m, tab.data(), tab.size(), &dt))) return st;
+                m->tplan.expected = dt;
+                m->tplan_ok = true;
+            }
+        }
+        if (m->fast_variant == 11 && !m->tplan_ok) m->fast_variant = 1;
         if (m->fast_variant == 7 && !m->zplan_ok) m->fast_variant = 1;
         if (m->fast_variant == 10 && !m->zbplan_ok) m->fast_variant = 1;
         if ((m->fast_variant == 4 || m->fast_variant == 5) && !m->async_ok) m->fast_variant = 2;
@@ -406,6 +422,14 @@ int to_csr(spmv_mat_s* a, Csr* c) {
 
 cudaStream_t as_stream(spmv_stream_t s) { return static_cast<cudaStream_t>(s); }
 
+// Variant 11 needs x and y 16-byte aligned (TMA box, bulk store); other
+// vectors take the direct FAST kernel.
+cudaError_t launch_tma_or_direct(spmv_mat_s* A, const TmaPlan& tp, const double* x, double* y, cudaStream_t s) {
+    const cudaError_t e = launch_pattern_fast_tma(A->pat_view, tp, x, y, s);
+    if (e != cudaErrorNotSupported) return e;
+    return launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
+}
+
 // The stored matrix's product on device vectors (no permutation).
 int apply_stored(spmv_mat_s* A, const double* x, double* y, cudaStream_t s) {
     cudaError_t e;
@@ -421,6 +445,7 @@ int apply_stored(spmv_mat_s* A, const double* x, double* y, cudaStream_t s) {
                                                            A->xfixed_guard, s)
             : A->fast_variant == 7 ? launch_pattern_fast_zmarch(A->pat_view, A->zplan, x, y, A->d_scratch_words, s)
             : A->fast_variant == 10 ? launch_pattern_fast_zblock(A->pat_view, A->zbplan, x, y, A->d_scratch_words, s)
+            : A->fast_variant == 11 ? launch_tma_or_direct(A, A->tplan, x, y, s)
             : A->fast_variant == 6 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 0, s)
             : A->fast_variant == 8 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 1, s)
             : A->fast_variant == 9 ? launch_pattern_fast_rstaged(A->pat_view, A->stage, x, y, 2, s)
@@ -552,10 +577,12 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->fast_eligible = A->pat.fast_ok ? 1 : 0;
         out->fast_tile_rows = A->fast_variant == 7 && A->zplan_ok ? A->zplan.rows
                             : A->fast_variant == 10 && A->zbplan_ok ? A->zbplan.rows * A->zbplan.zc
+                            : A->fast_variant == 11 && A->tplan_ok ? A->tplan.C
                             : A->stage_ok ? A->stage.rows : 0;
         out->fast_variant = A->device >= 0 ? A->fast_variant : -1;
         out->fast_block_threads = A->fast_variant == 7 && A->zplan_ok ? A->zplan.threads
                                   : A->fast_variant == 10 && A->zbplan_ok ? A->zbplan.threads
+                                  : A->fast_variant == 11 && A->tplan_ok ? A->tplan.threads
                                   : A->stage_ok ? A->stage.rows / A->stage.rows_per_thread : 0;
         out->row_types = static_cast<int32_t>(A->pat.rtypes.size() / 8);
         out->format_bytes = A->n * 4 * A->pat.words;
@@ -673,10 +700,12 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
     const size_t bytes = sizeof(double) * A->n;
     const bool fast = A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty();
     const bool zblock = fast && A->fast_variant == 10 && A->zbplan_ok;
-    const bool tiled = zblock || (fast && A->stage_ok && (A->fast_variant == 1 || A->fast_variant == 6 ||
-                                                          A->fast_variant == 8 || A->fast_variant == 9));
-    // the unit a chunk is made of: a tile, or a z-block chunk of planes
-    const int64_t rows = zblock ? int64_t(A->zbplan.zc) * A->zbplan.S : int64_t(A->stage.rows);
+    const bool tma = fast && A->fast_variant == 11 && A->tplan_ok &&
+                     ((reinterpret_cast<uintptr_t>(A->d_hx) | reinterpret_cast<uintptr_t>(A->d_hy)) & 15u) == 0;
+    const bool tiled = zblock || tma || (fast && A->stage_ok && (A->fast_variant == 1 || A->fast_variant == 6 ||
+                                                                 A->fast_variant == 8 || A->fast_variant == 9));
+    // the unit a chunk is made of: a tile, a z-block chunk of planes, or a plane
+    const int64_t rows = zblock ? int64_t(A->zbplan.zc) * A->zbplan.S : tma ? A->tplan.S : int64_t(A->stage.rows);
     constexpr int kChunks = 8;
     if (!tiled || A->n < int64_t(kChunks) * (zblock ? 1 : 4) * rows) {
         SPMVC_CUDA(cudaMemcpyAsync(A->d_hx, x, bytes, cudaMemcpyHostToDevice, A->own_stream));
@@ -725,7 +754,12 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
         while (jx + 1 < kChunks && bound[jx + 1] < need) ++jx;     // last x chunk the rows read
         SPMVC_CUDA(cudaStreamWaitEvent(A->own_stream, A->host_events[jx], 0));
         cudaError_t ce;
-        if (zblock) {
+        if (tma) {
+            TmaPlan tp = A->tplan;
+            tp.z_lo = int32_t(b / rows);
+            tp.z_hi = int32_t((e + rows - 1) / rows);
+            ce = launch_pattern_fast_tma(A->pat_view, tp, A->d_hx, A->d_hy, A->own_stream);
+        } else if (zblock) {
             ZPlan zp = A->zbplan;
             zp.chunk0 = int32_t(b / rows);
             zp.nchunks = int32_t((e - b + rows - 1) / rows);
@@ -816,18 +850,18 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     if (st) return st;
     if (choice) *choice = 0;
     if (A->fmt != SPMV_FMT_PATTERN || A->order != SPMV_ORDER_FAST || A->n == 0) return SPMV_OK;
-    struct Cand { int variant; StagePlan plan; ZPlan zplan; };
+    struct Cand { int variant; StagePlan plan; ZPlan zplan; TmaPlan tplan; };
     std::vector<Cand> cands;
-    if (A->d_xfixed) cands.push_back(Cand{2, A->stage, {}});
-    if (A->async_ok) cands.push_back(Cand{4, A->async_plan, {}});
-    if (A->async_ok && A->d_xfixed) cands.push_back(Cand{5, A->async_plan, {}});
+    if (A->d_xfixed) cands.push_back(Cand{2, A->stage, {}, {}});
+    if (A->async_ok) cands.push_back(Cand{4, A->async_plan, {}, {}});
+    if (A->async_ok && A->d_xfixed) cands.push_back(Cand{5, A->async_plan, {}, {}});
     if (A->stage_ok) {
         const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
         for (int rpt : {1, 2, 4}) {
             StagePlan plan;
             if (make_stage_plan(A->pat.uoff, rpt, 512, 12288, &plan)) {
-                cands.push_back(Cand{1, plan, {}});
-                if (A->d_xfixed && full27) cands.push_back(Cand{3, plan, {}});
+                cands.push_back(Cand{1, plan, {}, {}});
+                if (A->d_xfixed && full27) cands.push_back(Cand{3, plan, {}, {}});
             }
         }
         // 256-thread tiles (six resident CTAs per SM) and the register-staged
@@ -835,26 +869,35 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         if (full27) {
             for (int rpt : {2, 4, 8}) {
                 StagePlan plan;
-                if (make_stage_plan(A->pat.uoff, rpt, 256, 12288, &plan)) cands.push_back(Cand{1, plan, {}});
+                if (make_stage_plan(A->pat.uoff, rpt, 256, 12288, &plan)) cands.push_back(Cand{1, plan, {}, {}});
             }
             for (std::pair<int, int> sh : {std::make_pair(256, 4), std::make_pair(256, 2), std::make_pair(512, 2)}) {
                 StagePlan plan;
                 if (make_stage_plan(A->pat.uoff, sh.second, sh.first, 12288, &plan) && rstage_supported(plan)) {
-                    cands.push_back(Cand{6, plan, {}});
-                    cands.push_back(Cand{8, plan, {}});
+                    cands.push_back(Cand{6, plan, {}, {}});
+                    cands.push_back(Cand{8, plan, {}, {}});
                 }
             }
             for (std::pair<int, int> sh : {std::make_pair(256, 2), std::make_pair(256, 4), std::make_pair(512, 2)}) {
                 ZPlan zp;
                 if (A->pat_view.words == 7 && make_zplan(A->pat.uoff, A->n, sh.second, sh.first, A->num_sms, &zp) &&
                     zmarch_supported(zp))
-                    cands.push_back(Cand{7, {}, zp});
+                    cands.push_back(Cand{7, {}, zp, {}});
             }
             for (int planes : {3, 4}) {
                 ZPlan zp;
                 if (A->pat_view.words == 7 && make_zblock_plan(A->pat.uoff, A->n, planes, 256, &zp))
-                    cands.push_back(Cand{10, {}, zp});
+                    cands.push_back(Cand{10, {}, zp, {}});
             }
+            if (A->tplan_ok && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0)
+                for (int rpt : {2, 4}) {
+                    TmaPlan tp;
+                    std::vector<uint32_t> tab;
+                    if (make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, rpt, &tp, &tab)) {
+                        tp.expected = A->tplan.expected;   // the same table for every shape
+                        cands.push_back(Cand{11, {}, {}, tp});
+                    }
+                }
         }
     }
     if (cands.size() <= 1) return SPMV_OK;
@@ -902,6 +945,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
                 return launch_pattern_fast_zmarch(A->pat_view, c.zplan, x, y, A->d_scratch_words, nullptr);
             if (c.variant == 10)
                 return launch_pattern_fast_zblock(A->pat_view, c.zplan, x, y, A->d_scratch_words, nullptr);
+            if (c.variant == 11) return launch_pattern_fast_tma(A->pat_view, c.tplan, x, y, nullptr);
             if (c.variant == 5)
                 return launch_pattern_fast_async_x(A->pat_view, c.plan, x, y, A->d_scratch_words, A->d_xfixed,
                                                    A->xfixed_guard, A->num_sms, nullptr);
@@ -942,6 +986,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         A->zbplan = pick.zplan;
         A->zbplan_ok = true;
     }
+    if (pick.variant == 11) A->tplan = pick.tplan;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_variant[tune_key(A)] = pick.variant;
@@ -949,11 +994,14 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
             g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.rows_per_thread;
         else if (pick.variant == 10)
             g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.zc;
+        else if (pick.variant == 11)
+            g_tune[tune_key(A)] = pick.tplan.rpt;
         else if (staged_pick)
             g_tune[tune_key(A)] = (pick.plan.rows / pick.plan.rows_per_thread) * 16 + pick.plan.rows_per_thread;
     }
     if (choice) *choice = staged_pick ? pick.plan.rows : pick.variant == 7 ? pick.zplan.rows
                         : pick.variant == 10 ? pick.zplan.rows * pick.zplan.zc
+                        : pick.variant == 11 ? A->tplan.C
                         : (pick.variant >= 4 ? pick.variant : 1);
     return SPMV_OK;
 }
@@ -1000,8 +1048,26 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
         A->fast_variant = 10;
         return SPMV_OK;
     }
+    if (variant == 11) {
+        // tile_rows: rows a thread, 2 or 4 (0: keep the current plan's)
+        if (!A->tplan_ok)
+            return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel for this matrix (the full 27-point box of an "
+                                           "nx*ny*nz grid with uniform neighbour weights, nx a multiple of 4 up "
+                                           "to 252, a column block of whole lines dividing ny)");
+        if (tile_rows != 0) {
+            TmaPlan tp;
+            std::vector<uint32_t> tab;
+            if (tile_rows != 2 && tile_rows != 4) return fail(SPMV_EINVAL, "variant 11 takes 2 or 4 rows a thread");
+            if (!make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, tile_rows, &tp, &tab))
+                return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel with that many rows a thread here");
+            tp.expected = A->tplan.expected;
+            A->tplan = tp;
+        }
+        A->fast_variant = 11;
+        return SPMV_OK;
+    }
     if (variant != 1 && variant != 3 && variant != 6 && variant != 8 && variant != 9)
-        return fail(SPMV_EINVAL, "variant must be 0..10");
+        return fail(SPMV_EINVAL, "variant must be 0..11");
     const bool full27 = A->pat_view.run_len == 3 && A->pat_view.nu == 27;
     const bool rstaged = variant == 6 || variant == 8 || variant == 9;
     if (variant == 3 && !(A->d_xfixed && full27))

@@ -236,6 +236,48 @@ bool make_zblock_plan(const std::vector<int32_t>& uoff, int64_t n, int planes, i
 bool zblock_supported(const ZPlan& zp);
 bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int threads, int max_elems,
                      StagePlan* out);
+
+// TMA z-marching plan (FAST variant 11, k_tma.cu) for a pattern-format
+// matrix whose union is the full 27-point box {dz*S + dy*nx + dx} of an
+// nx*ny*nz grid (n = nx*ny*nz, S = nx*ny) and whose dominant record has
+// uniform neighbour weights.  A column block is L whole grid lines
+// (C = L*nx rows of a plane, rpt consecutive rows a compute thread, and a
+// producer warp that keeps the copies going); persistent CTAs (one an SM)
+// walk equal shares of the (block, plane) sequence, block-major.  The x window of a block in
+// plane z is the box [nx+4 elements, L+2 lines] at (ix = -2, iy = b*L - 1,
+// z), loaded by TMA with zero fill outside the grid.  Each row's record is
+// compared with the record its grid position implies (expected[class],
+// class = 2 bits a dimension: bit 0 a lower neighbour exists, bit 1 an
+// upper one): a row that matches sums all 27 window slots with the dominant
+// weights (out-of-grid slots read zero); any other row is summed slot by
+// slot from its own record and global x.
+struct TmaPlan {
+    int32_t nx, ny, nz;
+    int32_t L, C, rpt, threads;     // lines a block, rows a block (L*nx), rows a thread (2 or 4), C/rpt threads
+    int32_t pitch;                  // nx + 4: elements of a window line
+    int32_t win_elems;              // (L + 2) * pitch
+    int32_t nblk;                   // column blocks a plane (ny / L)
+    int32_t grid;                   // persistent CTAs at most (the SM count)
+    int32_t z_lo, z_hi;             // planes a launch computes (0 and nz: all)
+    int64_t S;                      // plane stride nx*ny
+    // dynamic shared memory: ring of 4 converted windows at 0, then
+    int32_t off_raw, raw_bytes;     // 2 raw window stages
+    int32_t off_rec;                // 3 record stages of 28*C bytes
+    int32_t off_exp;                // 64 expected records x 8 words
+    int32_t off_flags;              // 3 x C/32 words of per-row match bits
+    int32_t off_words;              // exponent words, mismatch counts, abort and producer words
+    int32_t off_mbar;               // full and empty mbarriers of the 2 raw and 3 record stages
+    int32_t smem_bytes;
+    const uint32_t* expected;       // device copy of the 64 x 8-word table
+};
+// Builds the plan and the expected-record table (64 classes x 8 words);
+// false when the matrix or its grid has no compiled shape for variant 11.
+bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int rpt, TmaPlan* out,
+                   std::vector<uint32_t>* expected);
+// Launches variant 11; falls back to cudaErrorNotSupported when x or y is
+// not 16-byte aligned (the TMA box and the bulk store need it).
+cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, const double* x, double* y,
+                                    cudaStream_t s);
 bool stage_supported(int nu);  // union sizes with a compiled staged kernel
 bool rstage_supported(const StagePlan& sp);  // plans the register-staged kernel takes
 
@@ -340,6 +382,8 @@ struct spmv_mat_s {
     bool zplan_ok = false;
     spmvc::ZPlan zbplan{};             // FAST order, z-block kernel (set on request or by the autotuner)
     bool zbplan_ok = false;
+    spmvc::TmaPlan tplan{};            // FAST order, TMA z-marching kernel (variant 11)
+    bool tplan_ok = false;
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;

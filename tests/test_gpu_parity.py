@@ -130,7 +130,7 @@ def fast_order_claim(rowptr, col, val, x):
     return exact, bound, covered
 
 
-def check_fast_order_bound(rowptr, col, val, x, y):
+def check_fast_order_bound(rowptr, col, val, x, y, uncovered_above_tol=True):
     from fractions import Fraction
     exact, bound, covered = fast_order_claim(rowptr, col, val, x)
     for i in range(len(y)):
@@ -142,8 +142,9 @@ def check_fast_order_bound(rowptr, col, val, x, y):
     assert np.any(covered) and np.any(~covered)
     assert np.max(d[covered] / scale[covered]) <= TOL
     # outside the precondition the componentwise figure is not claimed, and
-    # here it is indeed above 1e-14 on some row
-    assert np.max(d[~covered] / scale[~covered]) > TOL
+    # with one scale for the whole vector it is indeed above 1e-14 somewhere
+    if uncovered_above_tol:
+        assert np.max(d[~covered] / scale[~covered]) > TOL
 
 
 @pytest.mark.parametrize("g", [(4, 4, 4), (17, 13, 11), (32, 32, 32)])
@@ -217,7 +218,7 @@ def test_config2_192cubed_sampled():
     assert P.spmv_device_error(C) == 0
 
 
-BENCH_SHAPES = [(10, 2048, 256), (10, 1536, 256)]
+BENCH_SHAPES = [(11, 2, 0), (11, 4, 0), (10, 2048, 256), (10, 1536, 256)]
 
 
 @pytest.fixture(scope="module")
@@ -379,7 +380,7 @@ def test_host_buffers_pipelined_in_row_chunks():
     x = torch.from_numpy(x_np).cuda()
     hx = torch.from_numpy(x_np).pin_memory()
     for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (8, 1024, 256), (9, 1024, 256),
-                     (10, 1536, 256), (10, 2048, 256)]:
+                     (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
         P.spmv_set_tile(C, v, t, bt)
         yd = torch.empty_like(x)
         P.spmv_apply(C, x, yd)
@@ -495,9 +496,9 @@ def test_fast_variants_on_hpcg_grids():
                    (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512),
                                   (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
                                   (8, 512, 256), (8, 1024, 256), (9, 512, 256), (9, 1024, 256), (9, 1024, 512),
-                                  (10, 1536, 256), (10, 2048, 256)]}
+                                  (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]}
         for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512), (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
-                         (8, 512, 256), (9, 1024, 256), (10, 1536, 256), (10, 2048, 256)]:
+                         (8, 512, 256), (9, 1024, 256), (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
             if (v, t, bt) not in rstaged.get(g, []):
                 with pytest.raises(P.SpmvError):
                     P.spmv_set_tile(C, v, t, bt)
@@ -562,7 +563,7 @@ def test_fast_zmarch_several_planes_per_cta():
     n = 64 * 64 * 160
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x = spmv_inputs.uniform_vector(n, seed=24)
-    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (10, 1536, 256), (10, 2048, 256)]:
+    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
         P.spmv_set_tile(C, v, t, bt)
         check_persistent(C, g, n, x)
 
@@ -582,15 +583,16 @@ def test_fast_uniform_stencil_with_odd_rows():
     scale = abs_row_sums(rowptr, col, val, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
     for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (6, 1024, 256), (7, 512, 256), (7, 1024, 512),
-                     (8, 512, 256), (9, 512, 256), (10, 1536, 256), (10, 2048, 256)]:
+                     (8, 512, 256), (9, 512, 256), (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
         P.spmv_set_tile(C, v, t, bt)
         check_fast(run(C, x), y_ref, scale)
+    assert P.spmv_device_error(C) == 0
 
 
 def test_set_tile_rejects_shapes_without_kernel():
     C = P.spmv_compress(P.spmv_build("hpcg", 16, 16, 16), format="pattern", order="fast")
     for v, t, bt in [(1, 1024, 128), (3, 1024, 256), (1, 768, 256), (1, 4096, 256), (1, 256, 256),
-                     (10, 1536, 256), (11, 1024, 256)]:
+                     (10, 1536, 256), (12, 1024, 256)]:
         with pytest.raises(P.SpmvError):
             P.spmv_set_tile(C, v, t, bt)
     # the z-block kernel: 3 or 4 planes of 512 rows at 256 threads only
@@ -618,9 +620,9 @@ def test_autotune_keeps_results():
     x = torch.from_numpy(x_np).cuda()
     y = torch.empty_like(x)
     rows = P.spmv_autotune(C, x, y, reps=3)
-    assert rows in (1, 4, 5, 512, 1024, 2048)
+    assert rows in (1, 4, 5, 512, 1024, 1536, 2048)
     info = P.spmv_info(C)
-    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6, 7, 8))
+    assert info["fast_variant"] in {1: (2,), 4: (4,), 5: (5,)}.get(rows, (1, 3, 6, 7, 8, 10, 11))
     if rows not in (1, 4, 5):
         assert info["fast_tile_rows"] == rows
     y_ref = oracle.spmv(rowptr, col, val, x_np)
@@ -633,7 +635,7 @@ def test_autotune_keeps_results():
     xb[5], xb[n // 2] = np.inf, np.nan
     xd = torch.from_numpy(xb).cuda()
     D = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
-    assert P.spmv_autotune(D, xd, y, reps=2) in (1, 4, 5, 512, 1024, 2048)
+    assert P.spmv_autotune(D, xd, y, reps=2) in (1, 4, 5, 512, 1024, 1536, 2048)
     yb = run(D, xb)
     yb_ref = oracle.spmv(rowptr, col, val, xb)
     assert np.array_equal(np.isnan(yb), np.isnan(yb_ref))
@@ -673,7 +675,10 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
              # three separate plane windows per 512-row tile: the register-staged kernel
              ((24, 24, 4), [(6, 512, 256), (8, 512, 256), (9, 512, 256), (1, 512, 256), (2, 0, 512)]),
              # plane stride 2048: z-marching tiles
-             ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512), (10, 1536, 256), (10, 2048, 256)])]
+             ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512), (10, 1536, 256), (10, 2048, 256),
+                            (11, 2, 0), (11, 4, 0)]),
+             # TMA kernel: 1536-row blocks of 24 lines, several planes a CTA
+             ((64, 48, 11), [(11, 2, 0), (11, 4, 0)])]
     for g, shapes in cases:
         rowptr, col, val = oracle.hpcg_csr(*g)
         n = len(rowptr) - 1
@@ -733,7 +738,7 @@ def test_fast_variant_persistent_many_tiles():
     x = spmv_inputs.uniform_vector(n, seed=13)
     for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512),
                            (7, 512, 256), (7, 1024, 256), (7, 1024, 512), (8, 1024, 256), (8, 512, 256),
-                           (10, 1536, 256), (10, 2048, 256),
+                           (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0),
                            (9, 512, 256), (9, 1024, 512)]:
         P.spmv_set_tile(C, variant, t, bt)
         check_persistent(C, g, n, x)
@@ -888,3 +893,62 @@ def test_reordered_dit_and_delta_products():
         assert all(np.array_equal(u, v) for u, v in zip(got, (rowptr, col, val)))
     with pytest.raises(P.SpmvError):
         P.spmv_compress(P.spmv_build("hpcg", 12, 10, 9), format="pattern", reorder=True)
+
+
+def test_tma_kernel_shapes_and_refusals():
+    """Variant 11 (TMA z-marching) exists only for the full 27-point box of a
+    grid with nx a multiple of 4 (at most 252), uniform neighbour weights
+    and a block of whole lines dividing ny; its block is what spmv_info
+    reports."""
+    for g, rows in [((192, 192, 3), 1536), ((160, 160, 3), 1280), ((64, 48, 3), 1536), ((32, 64, 3), 1024),
+                    ((96, 96, 3), 1536), ((16, 16, 16), 256)]:
+        C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+        for rpt in (2, 4):
+            P.spmv_set_tile(C, 11, rpt, 0)
+            info = P.spmv_info(C)
+            assert (info["fast_variant"], info["fast_tile_rows"], info["fast_block_threads"]) == \
+                (11, rows, rows // rpt), (g, rpt)
+        with pytest.raises(P.SpmvError):
+            P.spmv_set_tile(C, 11, 3, 0)
+    # nx not a multiple of 4; no block of whole lines that divides ny; nx
+    # above 252; no interior row (nz = 2: no dominant record without an
+    # absent slot)
+    for g in [(9, 8, 7), (30, 32, 4), (260, 4, 4), (32, 64, 2)]:
+        C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+        with pytest.raises(P.SpmvError):
+            P.spmv_set_tile(C, 11, 0, 0)
+    rowptr, col, val = weighted_27_point_csr((32, 64, 6))
+    C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_tile(C, 11, 0, 0)
+
+
+def test_tma_kernel_misaligned_vectors_and_scale_changes():
+    """Variant 11 with x or y one element into a buffer (the direct kernel
+    takes over), and with windows whose largest exponent grows plane by
+    plane (every window re-converted, the ring shifted), against the exact
+    model of FAST order."""
+    g = (32, 64, 6)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    P.spmv_set_tile(C, 11, 4, 0)
+    x = spmv_inputs.uniform_vector(n, seed=51)
+    y_ref = oracle.spmv(rowptr, col, val, x)
+    scale = abs_row_sums(rowptr, col, val, x)
+    xbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    xbuf[1:] = torch.from_numpy(x).cuda()
+    xal = torch.from_numpy(x).cuda()
+    ybuf = torch.full((n + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    for xx, yy in [(xbuf[1:], ybuf[:n]), (xal, ybuf[1:])]:
+        yy.fill_(float("nan"))
+        P.spmv_apply(C, xx, yy)
+        torch.cuda.synchronize()
+        check_fast(yy.cpu().numpy(), y_ref, scale)
+    # growing exponents: plane z scaled by 2^(3z); every plane's scale is the
+    # largest exponent of the windows seen so far, which here is that of the
+    # plane's own upper neighbour, so compare with the bound, not one model
+    xs = x * np.repeat(2.0 ** (3 * np.arange(6)), 32 * 64)
+    y = run(C, xs)
+    check_fast_order_bound(rowptr, col, val, xs, y, uncovered_above_tol=False)
+    assert P.spmv_device_error(C) == 0
