@@ -303,10 +303,11 @@ int ensure_device(spmv_mat_s* m) {
         m->tplan_ok = false;
         {
             std::vector<uint32_t> tab;
-            // rows a thread: the autotuner's pick for matrices of this shape, else 2
-            const int rpt = m->fast_variant == 11 ? tuned_stage_shape(m, 0, 2).second : 2;
-            if (make_tma_plan(p, v, m->n, m->num_sms, rpt, &m->tplan, &tab) ||
-                make_tma_plan(p, v, m->n, m->num_sms, 6 - rpt, &m->tplan, &tab)) {
+            // lines a compute thread's tile: the autotuner's pick for matrices
+            // of this shape, else 1
+            const int ty = m->fast_variant == 11 ? tuned_stage_shape(m, 0, 1).second : 1;
+            if (make_tma_plan(p, v, m->n, m->num_sms, ty, &m->tplan, &tab) ||
+                make_tma_plan(p, v, m->n, m->num_sms, 3 - ty, &m->tplan, &tab)) {
                 uint32_t* dt;
                 if ((st = dev_copy(m, tab.data(), tab.size(), &dt))) return st;
                 m->tplan.expected = dt;
@@ -890,10 +891,10 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
                     cands.push_back(Cand{10, {}, zp, {}});
             }
             if (A->tplan_ok && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0)
-                for (int rpt : {2, 4}) {
+                for (int ty : {1, 2}) {
                     TmaPlan tp;
                     std::vector<uint32_t> tab;
-                    if (make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, rpt, &tp, &tab)) {
+                    if (make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, ty, &tp, &tab)) {
                         tp.expected = A->tplan.expected;   // the same table for every shape
                         cands.push_back(Cand{11, {}, {}, tp});
                     }
@@ -995,7 +996,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         else if (pick.variant == 10)
             g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.zc;
         else if (pick.variant == 11)
-            g_tune[tune_key(A)] = pick.tplan.rpt;
+            g_tune[tune_key(A)] = pick.tplan.ty;
         else if (staged_pick)
             g_tune[tune_key(A)] = (pick.plan.rows / pick.plan.rows_per_thread) * 16 + pick.plan.rows_per_thread;
     }
@@ -1049,7 +1050,8 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
         return SPMV_OK;
     }
     if (variant == 11) {
-        // tile_rows: rows a thread, 2 or 4 (0: keep the current plan's)
+        // tile_rows: lines of a compute thread's tile, 1 or 2 (0: keep the
+        // current plan's)
         if (!A->tplan_ok)
             return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel for this matrix (the full 27-point box of an "
                                            "nx*ny*nz grid with uniform neighbour weights, nx a multiple of 4 up "
@@ -1057,9 +1059,9 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
         if (tile_rows != 0) {
             TmaPlan tp;
             std::vector<uint32_t> tab;
-            if (tile_rows != 2 && tile_rows != 4) return fail(SPMV_EINVAL, "variant 11 takes 2 or 4 rows a thread");
+            if (tile_rows != 1 && tile_rows != 2) return fail(SPMV_EINVAL, "variant 11 takes tiles of 1 or 2 lines");
             if (!make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, tile_rows, &tp, &tab))
-                return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel with that many rows a thread here");
+                return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel with that tile here");
             tp.expected = A->tplan.expected;
             A->tplan = tp;
         }

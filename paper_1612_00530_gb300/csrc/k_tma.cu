@@ -4,7 +4,7 @@
 //
 // One persistent CTA an SM walks an equal share of the (column block, plane)
 // sequence.  A column block is L whole grid lines of a plane (C = L*nx rows,
-// RPT consecutive rows a compute thread).  A producer warp keeps the copies
+// a tile of TY lines by four columns a compute thread).  A producer warp keeps the copies
 // going: lane 0 loads, for every plane z of the block, the x window W(z) --
 // the box of nx+4 elements by L+2 lines at (ix = -2, iy = first line - 1, z),
 // one TMA tensor copy that fills everything outside the grid with zeros
@@ -18,9 +18,9 @@
 //    (the dominant codes at the in-grid slots, the absent code elsewhere,
 //    the matching pattern number) and hand the record stage back;
 //  - convert the newest window once into 53-bit fixed point (two int32
-//    limbs) in a ring of four shared-memory slots, stored as RPT
-//    sub-arrays by element index mod RPT so that a thread's RPT+2
-//    consecutive elements of a run are conflict-free 8-byte loads at
+//    limbs) in a ring of four shared-memory slots, stored as four
+//    sub-arrays by element index mod 4 so that the six consecutive elements
+//    of a window line a tile reads are conflict-free 8-byte loads at
 //    constant offsets, and hand the raw stage back;
 //  - sum every row of the plane two windows back over all 27 window slots
 //    with the dominant record's weights (an out-of-grid neighbour reads a
@@ -140,32 +140,50 @@ __device__ __forceinline__ bool compute_sync_or(int n, bool v) {
     return r != 0;
 }
 
-// The (block, plane) share of CTA `cta` out of `ctas`: runs of planes
-// z0 .. z1-1 of one column block, visited block-major.
+// A CTA's share of the (block, plane) sequence, visited block-major, as
+// runs of planes z0 .. z1-1 of one column block.  A run costs its planes
+// plus about kRunCost steps of start-up, so each block counts kRunCost
+// more units than it has planes (the start-up of the run that begins it)
+// and the CTAs take equal ranges of those units: a CTA whose range crosses
+// a block boundary gets fewer planes.
+constexpr int kRunCost = 2;
 struct Share {
-    int64_t u, uend;
+    int64_t u, uend;      // units of this CTA still to visit: [u, uend)
     int nzr, z_lo;
     __device__ bool next(int& b, int& z0, int& z1) {
-        if (u >= uend) return false;
-        b = int(u / nzr);
-        z0 = z_lo + int(u - int64_t(b) * nzr);
-        z1 = z_lo + int(min(uend - int64_t(b) * nzr, int64_t(nzr)));
-        u = int64_t(b) * nzr + (z1 - z_lo);
-        return true;
+        const int per = nzr + kRunCost;
+        while (u < uend) {
+            b = int(u / per);
+            const int o0 = int(u - int64_t(b) * per);
+            const int o1 = int(min(uend - int64_t(b) * per, int64_t(per)));
+            u = int64_t(b) * per + o1;
+            // unit offsets 0 .. kRunCost-1 of a block stand for its start-up
+            const int p0 = max(o0 - kRunCost, 0), p1 = max(o1 - kRunCost, 0);
+            if (p1 > p0) {
+                z0 = z_lo + p0;
+                z1 = z_lo + p1;
+                return true;
+            }
+        }
+        return false;
     }
 };
 
-// RPT consecutive rows a compute thread (2 or 4); a ring slot holds RPT
-// sub-arrays, sub-array s the window elements e with e mod RPT = s at index
-// e / RPT.  Threads 0 .. C/RPT-1 compute; the last warp is the producer.
-template <int RPT>
-__global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
+// A compute thread sums a tile of TY grid lines by four columns (K = 4 TY
+// rows).  A ring slot holds four sub-arrays, sub-array s the window elements
+// e with e mod 4 = s at index e / 4: the six elements of a window line a
+// tile reads (its four columns and one each side) are six conflict-free
+// 8-byte loads at constant offsets.  Threads 0 .. C/K-1 compute; the last
+// warp is the producer.
+template <int TY>
+__global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
     pattern_fast_tma_kernel(const __grid_constant__ CUtensorMap xmap, const PatternView a, const TmaPlan tp,
                             const double* __restrict__ x, double* __restrict__ y) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr int SUB = kSlotElems / RPT;
+    constexpr int K = 4 * TY;                          // rows a compute thread
+    constexpr int SUB = kSlotElems / 4;
     constexpr uint32_t SUBB = uint32_t(SUB) * 8u;     // bytes of a sub-array
-    constexpr uint32_t SLOTB = uint32_t(RPT) * SUBB;   // bytes of a ring slot
+    constexpr uint32_t SLOTB = 4u * SUBB;              // bytes of a ring slot
     const int tid = threadIdx.x, lane = tid & 31;
     const int NC = tp.threads, C = tp.C, nx = tp.nx;   // compute threads, rows a block
     const int fw = C >> 5;                             // match words a plane
@@ -200,7 +218,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
     __syncthreads();
 
     const int nzr = tp.z_hi - tp.z_lo;
-    const int64_t units = int64_t(tp.nblk) * nzr;
+    const int64_t units = int64_t(tp.nblk) * (nzr + kRunCost);
     Share share{units * blockIdx.x / gridDim.x, units * (blockIdx.x + 1) / gridDim.x, nzr, tp.z_lo};
 
     if (tid >= NC) {
@@ -250,19 +268,20 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
     }
 
     // ---- compute threads
-    // summing: rows RPT*tid .. RPT*tid+RPT-1 of the block (line cline,
-    // columns cix.., all in one line since RPT divides nx)
-    const int cline = (RPT * tid) / nx, cix = RPT * tid - cline * nx;
-    // byte offset in a ring slot of the sub-array index of each run's first
-    // element ((cline + d) * pitch + cix + 1 = RPT q + 1 for the line d - 1
-    // above/at/below the rows)
-    uint32_t qoff[3];
+    // summing: the tile of block lines TY*ctl .. TY*ctl+TY-1 and columns
+    // cix .. cix+3 (four-column groups of a line: nx / 4)
+    const int xgs = nx >> 2;
+    const int ctl = tid / xgs, cix = 4 * (tid - ctl * xgs);
+    // byte offset in a ring slot of the sub-array index of the first element
+    // the tile reads in window line TY*ctl + l, l = 0 .. TY+1 (window line 0
+    // is the line above the block): (TY*ctl + l) * pitch + cix + 1 = 4 q + 1
+    uint32_t qoff[TY + 2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) qoff[d] = uint32_t(((cline + d) * tp.pitch + cix) / RPT) * 8u;
+    for (int l = 0; l < TY + 2; ++l) qoff[l] = uint32_t(((TY * ctl + l) * tp.pitch + cix) >> 2) * 8u;
     // checking: rows tid + k*NC of the block, one a lane, coalesced
-    int ckx[RPT], ckl[RPT];
+    int ckx[K], ckl[K];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
+    for (int k = 0; k < K; ++k) {
         const int rho = tid + k * NC;
         ckl[k] = rho / nx;
         const int ixk = rho - ckl[k] * nx;
@@ -278,19 +297,19 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
     int b, z0, z1;
     while (!aborted && share.next(b, z0, z1)) {
         const int64_t blk0 = int64_t(b) * C;    // the block's first row inside a plane
-        int cxy[RPT];
+        int cxy[K];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
+        for (int k = 0; k < K; ++k) {
             const int iy = b * tp.L + ckl[k];
             cxy[k] = ckx[k] | ((iy > 0 ? 1 : 0) | (iy < tp.ny - 1 ? 2 : 0)) << 2;
         }
         int cz_cached = -1;
-        uint32_t ex[RPT][7];
+        uint32_t ex[K][7];
         uint32_t E_true = 0u;            // largest biased exponent seen in this run of planes
         uint32_t E_ring = 64u;           // scale of the converted windows: max(E_true, 64)
 
         auto store_limbs = [&](unsigned char* slot, int e, int2 v) {
-            *reinterpret_cast<int2*>(slot + uint32_t(e % RPT) * SUBB + uint32_t(e / RPT) * 8u) = v;
+            *reinterpret_cast<int2*>(slot + uint32_t(e & 3) * SUBB + uint32_t(e >> 2) * 8u) = v;
         };
         auto convert = [&](const unsigned char* rw, unsigned char* slot, uint32_t E) -> uint32_t {
             uint32_t mx = 0;
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
                 const uint4 v = *reinterpret_cast<const uint4*>(rw + 16 * pi);
                 mx = max(mx, max(v.y & 0x7FFFFFFFu, v.w & 0x7FFFFFFFu));
                 const int e = 2 * pi;   // elements e (an even sub-array) and e + 1 (the next one)
-                unsigned char* d0 = slot + uint32_t(e % RPT) * SUBB + uint32_t(e / RPT) * 8u;
+                unsigned char* d0 = slot + uint32_t(e & 3) * SUBB + uint32_t(e >> 2) * 8u;
                 *reinterpret_cast<int2*>(d0) = fixed_limbs(v.x, v.y, E);
                 *reinterpret_cast<int2*>(d0 + SUBB) = fixed_limbs(v.z, v.w, E);
             }
@@ -318,7 +337,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
         };
         auto rescale = [&](unsigned char* slot, uint32_t d) {
             for (int e = tid; e < tp.win_elems; e += NC) {
-                int2* pv = reinterpret_cast<int2*>(slot + uint32_t(e % RPT) * SUBB + uint32_t(e / RPT) * 8u);
+                int2* pv = reinterpret_cast<int2*>(slot + uint32_t(e & 3) * SUBB + uint32_t(e >> 2) * 8u);
                 const int2 v = *pv;
                 const int64_t X = int64_t(v.y) * (int64_t(1) << 26) + v.x;
                 const uint64_t mag = X < 0 ? uint64_t(0) - uint64_t(X) : uint64_t(X);
@@ -347,7 +366,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
                 const int cz = (p > 0 ? 1 : 0) | (p < tp.nz - 1 ? 2 : 0);
                 if (cz != cz_cached) {
 #pragma unroll
-                    for (int k = 0; k < RPT; ++k)
+                    for (int k = 0; k < K; ++k)
 #pragma unroll
                         for (int i = 0; i < 7; ++i) ex[k][i] = sexp[(cxy[k] | (cz << 4)) * 8 + i];
                     cz_cached = cz;
@@ -355,7 +374,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
                 const unsigned char* rs = rec + st * 28u * uint32_t(C);
                 uint32_t nbad = 0;
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) {
+                for (int k = 0; k < K; ++k) {
                     const int rho = tid + k * NC;
                     const uint4 v16 = *reinterpret_cast<const uint4*>(rs + 16 * rho);
                     const uint2 v8 = *reinterpret_cast<const uint2*>(rs + 16 * C + 8 * rho);
@@ -397,68 +416,80 @@ __global__ void __launch_bounds__(kMaxBlockRows / RPT + 32, 1)
             const bool have_q = q >= z0 && q < z1;
             const bool fast_q = E_true >= 64u && E_true < 2047u;
             if (have_q) {
-                const int64_t row0 = int64_t(q) * tp.S + blk0 + RPT * tid;
+                const int64_t trow0 = int64_t(q) * tp.S + blk0 + int64_t(TY * ctl) * nx + cix;   // tile's first row
                 if (fast_q) {
                     const unsigned char* slots[3] = {ring + uint32_t((j - 3) & 3) * SLOTB,   // W(q-1)
                                                      ring + uint32_t((j - 2) & 3) * SLOTB,   // W(q)
                                                      ring + uint32_t((j - 1) & 3) * SLOTB};  // W(q+1)
-                    // high limbs in two sums of at most 14 terms (|xh| < 2^27),
-                    // low limbs in one of 26 (|xl| < 2^26): no int32 overflow
-                    int32_t A[RPT], B[RPT], SL[RPT], CH[RPT], CL[RPT];
+                    // per row: high limbs in two sums of at most 14 terms
+                    // (|xh| < 2^27), low limbs in one of 26 (|xl| < 2^26): no
+                    // int32 overflow; the centre apart
+                    int32_t A[TY][4], B[TY][4], SL[TY][4], CH[TY][4], CL[TY][4];
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) A[r] = B[r] = SL[r] = 0;
+                    for (int ry = 0; ry < TY; ++ry)
+#pragma unroll
+                        for (int rx = 0; rx < 4; ++rx) A[ry][rx] = B[ry][rx] = SL[ry][rx] = 0;
 #pragma unroll
                     for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const unsigned char* base = slots[dz] + qoff[dy];
-                            // element c of the run: sub-array (1 + c) mod RPT, index q + (1 + c) / RPT
-                            int2 e[RPT + 2];
+                        for (int l = 0; l < TY + 2; ++l) {
+                            const unsigned char* base = slots[dz] + qoff[l];
+                            // element c of the window line: sub-array (1 + c) mod 4, index q + (1 + c) / 4
+                            int2 e[6];
 #pragma unroll
-                            for (int c = 0; c < RPT + 2; ++c)
-                                e[c] = *reinterpret_cast<const int2*>(base + uint32_t((1 + c) % RPT) * SUBB +
-                                                                      uint32_t((1 + c) / RPT) * 8u);
+                            for (int c = 0; c < 6; ++c)
+                                e[c] = *reinterpret_cast<const int2*>(base + uint32_t((1 + c) & 3) * SUBB +
+                                                                      uint32_t((1 + c) >> 2) * 8u);
 #pragma unroll
-                            for (int r = 0; r < RPT; ++r) {
-                                if (dz == 1 && dy == 1) {
-                                    CH[r] = e[r + 1].y;
-                                    CL[r] = e[r + 1].x;
-                                    B[r] += e[r].y + e[r + 2].y;
-                                    SL[r] += e[r].x + e[r + 2].x;
-                                } else if (dz == 0 || (dz == 1 && dy == 0)) {
-                                    A[r] += e[r].y + e[r + 1].y + e[r + 2].y;
-                                    SL[r] += e[r].x + e[r + 1].x + e[r + 2].x;
-                                } else {
-                                    B[r] += e[r].y + e[r + 1].y + e[r + 2].y;
-                                    SL[r] += e[r].x + e[r + 1].x + e[r + 2].x;
+                            for (int ry = 0; ry < TY; ++ry) {
+                                const int dy = l - 1 - ry;   // the line's offset from tile line ry
+                                if (dy < -1 || dy > 1) continue;
+#pragma unroll
+                                for (int rx = 0; rx < 4; ++rx) {
+                                    if (dz == 1 && dy == 0) {
+                                        CH[ry][rx] = e[rx + 1].y;
+                                        CL[ry][rx] = e[rx + 1].x;
+                                        B[ry][rx] += e[rx].y + e[rx + 2].y;
+                                        SL[ry][rx] += e[rx].x + e[rx + 2].x;
+                                    } else if (dz == 0 || (dz == 1 && dy == -1)) {
+                                        A[ry][rx] += e[rx].y + e[rx + 1].y + e[rx + 2].y;
+                                        SL[ry][rx] += e[rx].x + e[rx + 1].x + e[rx + 2].x;
+                                    } else {
+                                        B[ry][rx] += e[rx].y + e[rx + 1].y + e[rx + 2].y;
+                                        SL[ry][rx] += e[rx].x + e[rx + 1].x + e[rx + 2].x;
+                                    }
                                 }
                             }
                         }
                     const int S = int(E_ring) - 1075 + a.mult_exp;
-                    double o[RPT];
+                    const uint32_t* flq = sflags + ((it - 1) % 3) * fw;   // the check of plane q, one step ago
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) {
-                        const int64_t ah =
-                            int64_t(a.dom_mo) * A[r] + int64_t(a.dom_mo) * B[r] + int64_t(a.dom_mc) * CH[r];
-                        const int64_t al = int64_t(a.dom_mo) * SL[r] + int64_t(a.dom_mc) * CL[r];
-                        o[r] = fixed_to_double(ah * (int64_t(1) << 26) + al, S);
-                    }
-                    // this thread's rows' match bits (the check of plane q, one step ago)
-                    const uint32_t mbits =
-                        (sflags[((it - 1) % 3) * fw + (RPT * tid >> 5)] >> ((RPT * tid) & 31)) & ((1u << RPT) - 1u);
-                    if (mbits == (1u << RPT) - 1u) {
-                        double2* yv = reinterpret_cast<double2*>(y + row0);
+                    for (int ry = 0; ry < TY; ++ry) {
+                        double o[4];
 #pragma unroll
-                        for (int r = 0; r < RPT; r += 2) yv[r / 2] = make_double2(o[r], o[r + 1]);
-                    } else {
+                        for (int rx = 0; rx < 4; ++rx) {
+                            const int64_t ah = int64_t(a.dom_mo) * A[ry][rx] + int64_t(a.dom_mo) * B[ry][rx] +
+                                               int64_t(a.dom_mc) * CH[ry][rx];
+                            const int64_t al = int64_t(a.dom_mo) * SL[ry][rx] + int64_t(a.dom_mc) * CL[ry][rx];
+                            o[rx] = fixed_to_double(ah * (int64_t(1) << 26) + al, S);
+                        }
+                        // store the rows whose record was the expected one
+                        const int rho = (TY * ctl + ry) * nx + cix;
+                        const uint32_t mbits = (flq[rho >> 5] >> (rho & 31)) & 15u;
+                        double* yr = y + trow0 + int64_t(ry) * nx;
+                        if (mbits == 15u) {
+                            reinterpret_cast<double2*>(yr)[0] = make_double2(o[0], o[1]);
+                            reinterpret_cast<double2*>(yr)[1] = make_double2(o[2], o[3]);
+                        } else {
 #pragma unroll
-                        for (int r = 0; r < RPT; ++r)
-                            if ((mbits >> r) & 1u) y[row0 + r] = o[r];
+                            for (int rx = 0; rx < 4; ++rx)
+                                if ((mbits >> rx) & 1u) yr[rx] = o[rx];
+                        }
                     }
                 } else {
                     // zero/subnormal-only or non-finite x in play: the COLUMN order
-                    for (int r = 0; r < RPT; ++r) {
-                        const int64_t row = row0 + r;
+                    for (int r = 0; r < K; ++r) {
+                        const int64_t row = trow0 + int64_t(r >> 2) * nx + (r & 3);
                         uint32_t w7[kMaxRecordWords];
                         load_record<7>(a, row, w7);
                         const uint32_t pat = byte_of(w7, 27);
@@ -559,9 +590,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int rpt, TmaPlan* out,
+bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
                    std::vector<uint32_t>* expected) {
-    if (rpt != 2 && rpt != 4) return false;
+    if (ty != 1 && ty != 2) return false;
     if (!p.fast_ok || v.nu != 27 || v.words != 7 || v.run_len != 3 || !v.dom_ok || !v.dom_uni) return false;
     const std::vector<int32_t>& U = p.uoff;
     if (U.size() != 27) return false;
@@ -574,11 +605,11 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
     if (S % nx != 0 || n % S != 0) return false;
     const int64_t ny = S / nx, nz = n / S;
     if (nx % 4 != 0 || nx + 4 > 256 || nz < 1) return false;
-    // the most lines a block (whole warps of rpt rows a thread) whose window
-    // fits a ring slot
+    // the most lines a block (whole warps of ty-by-4 tiles) whose window fits
+    // a ring slot
     int L = 0;
-    for (int64_t l = 1; l <= ny && l * nx <= kMaxBlockRows; ++l)
-        if (ny % l == 0 && (l * nx) % (32 * rpt) == 0 && (l + 2) * (nx + 4) <= kSlotElems) L = int(l);
+    for (int64_t l = ty; l <= ny && l * nx <= kMaxBlockRows; l += ty)
+        if (ny % l == 0 && (l * nx) % (128 * ty) == 0 && (l + 2) * (nx + 4) <= kSlotElems) L = int(l);
     if (L == 0) return false;
     TmaPlan t{};
     t.nx = int32_t(nx);
@@ -586,8 +617,8 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
     t.nz = int32_t(nz);
     t.L = L;
     t.C = int32_t(L * nx);
-    t.rpt = rpt;
-    t.threads = t.C / rpt;
+    t.ty = ty;
+    t.threads = t.C / (4 * ty);
     t.pitch = t.nx + 4;
     t.win_elems = (L + 2) * t.pitch;
     t.nblk = int32_t(ny / L);
@@ -653,7 +684,7 @@ cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, con
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    auto kernel = tp.rpt == 2 ? pattern_fast_tma_kernel<2> : pattern_fast_tma_kernel<4>;
+    auto kernel = tp.ty == 2 ? pattern_fast_tma_kernel<2> : pattern_fast_tma_kernel<1>;
     {
         static std::mutex mu;
         static bool set[64][2] = {};
@@ -662,11 +693,11 @@ cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, con
         if (e != cudaSuccess) return e;
         std::lock_guard<std::mutex> g(mu);
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!set[dev][tp.rpt == 2]) {
+        if (!set[dev][tp.ty == 2]) {
             e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return e;
-            set[dev][tp.rpt == 2] = true;
+            set[dev][tp.ty == 2] = true;
         }
     }
     kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y);

@@ -241,8 +241,8 @@ bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int 
 // matrix whose union is the full 27-point box {dz*S + dy*nx + dx} of an
 // nx*ny*nz grid (n = nx*ny*nz, S = nx*ny) and whose dominant record has
 // uniform neighbour weights.  A column block is L whole grid lines
-// (C = L*nx rows of a plane, rpt consecutive rows a compute thread, and a
-// producer warp that keeps the copies going); persistent CTAs (one an SM)
+// (C = L*nx rows of a plane, a tile of ty lines by four columns a compute
+// thread, and a producer warp that keeps the copies going); persistent CTAs (one an SM)
 // walk equal shares of the (block, plane) sequence, block-major.  The x window of a block in
 // plane z is the box [nx+4 elements, L+2 lines] at (ix = -2, iy = b*L - 1,
 // z), loaded by TMA with zero fill outside the grid.  Each row's record is
@@ -253,7 +253,8 @@ bool make_stage_plan(const std::vector<int32_t>& uoff, int rows_per_thread, int 
 // slot from its own record and global x.
 struct TmaPlan {
     int32_t nx, ny, nz;
-    int32_t L, C, rpt, threads;     // lines a block, rows a block (L*nx), rows a thread (2 or 4), C/rpt threads
+    int32_t L, C, ty, threads;      // lines a block, rows a block (L*nx), lines a compute thread's tile (1 or 2,
+                                    // four columns wide), C/(4*ty) compute threads
     int32_t pitch;                  // nx + 4: elements of a window line
     int32_t win_elems;              // (L + 2) * pitch
     int32_t nblk;                   // column blocks a plane (ny / L)
@@ -272,7 +273,7 @@ struct TmaPlan {
 };
 // Builds the plan and the expected-record table (64 classes x 8 words);
 // false when the matrix or its grid has no compiled shape for variant 11.
-bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int rpt, TmaPlan* out,
+bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
                    std::vector<uint32_t>* expected);
 // Launches variant 11; falls back to cudaErrorNotSupported when x or y is
 // not 16-byte aligned (the TMA box and the bulk store need it).

@@ -218,7 +218,7 @@ def test_config2_192cubed_sampled():
     assert P.spmv_device_error(C) == 0
 
 
-BENCH_SHAPES = [(11, 2, 0), (11, 4, 0), (10, 2048, 256), (10, 1536, 256)]
+BENCH_SHAPES = [(11, 1, 0), (11, 2, 0), (10, 2048, 256), (10, 1536, 256)]
 
 
 @pytest.fixture(scope="module")
@@ -380,7 +380,7 @@ def test_host_buffers_pipelined_in_row_chunks():
     x = torch.from_numpy(x_np).cuda()
     hx = torch.from_numpy(x_np).pin_memory()
     for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (8, 1024, 256), (9, 1024, 256),
-                     (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
+                     (10, 1536, 256), (10, 2048, 256), (11, 1, 0), (11, 2, 0)]:
         P.spmv_set_tile(C, v, t, bt)
         yd = torch.empty_like(x)
         P.spmv_apply(C, x, yd)
@@ -496,9 +496,9 @@ def test_fast_variants_on_hpcg_grids():
                    (64, 48, 40): [(6, 512, 256), (6, 1024, 256), (6, 1024, 512),
                                   (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
                                   (8, 512, 256), (8, 1024, 256), (9, 512, 256), (9, 1024, 256), (9, 1024, 512),
-                                  (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]}
+                                  (10, 1536, 256), (10, 2048, 256), (11, 1, 0), (11, 2, 0)]}
         for v, t, bt in [(6, 512, 256), (6, 1024, 256), (6, 1024, 512), (7, 512, 256), (7, 1024, 256), (7, 1024, 512),
-                         (8, 512, 256), (9, 1024, 256), (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
+                         (8, 512, 256), (9, 1024, 256), (10, 1536, 256), (10, 2048, 256), (11, 1, 0), (11, 2, 0)]:
             if (v, t, bt) not in rstaged.get(g, []):
                 with pytest.raises(P.SpmvError):
                     P.spmv_set_tile(C, v, t, bt)
@@ -563,7 +563,7 @@ def test_fast_zmarch_several_planes_per_cta():
     n = 64 * 64 * 160
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
     x = spmv_inputs.uniform_vector(n, seed=24)
-    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
+    for v, t, bt in [(7, 512, 256), (7, 1024, 256), (10, 1536, 256), (10, 2048, 256), (11, 1, 0), (11, 2, 0)]:
         P.spmv_set_tile(C, v, t, bt)
         check_persistent(C, g, n, x)
 
@@ -583,7 +583,7 @@ def test_fast_uniform_stencil_with_odd_rows():
     scale = abs_row_sums(rowptr, col, val, x)
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
     for v, t, bt in [(1, 1024, 256), (1, 2048, 512), (6, 512, 256), (6, 1024, 256), (7, 512, 256), (7, 1024, 512),
-                     (8, 512, 256), (9, 512, 256), (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0)]:
+                     (8, 512, 256), (9, 512, 256), (10, 1536, 256), (10, 2048, 256), (11, 1, 0), (11, 2, 0)]:
         P.spmv_set_tile(C, v, t, bt)
         check_fast(run(C, x), y_ref, scale)
     assert P.spmv_device_error(C) == 0
@@ -676,9 +676,9 @@ def test_fast_order_is_one_rounding_of_the_exact_fixed_point_sum(vscale, xscale)
              ((24, 24, 4), [(6, 512, 256), (8, 512, 256), (9, 512, 256), (1, 512, 256), (2, 0, 512)]),
              # plane stride 2048: z-marching tiles
              ((32, 64, 3), [(7, 512, 256), (7, 1024, 256), (7, 1024, 512), (10, 1536, 256), (10, 2048, 256),
-                            (11, 2, 0), (11, 4, 0)]),
+                            (11, 1, 0), (11, 2, 0)]),
              # TMA kernel: 1536-row blocks of 24 lines, several planes a CTA
-             ((64, 48, 11), [(11, 2, 0), (11, 4, 0)])]
+             ((64, 48, 11), [(11, 1, 0), (11, 2, 0)])]
     for g, shapes in cases:
         rowptr, col, val = oracle.hpcg_csr(*g)
         n = len(rowptr) - 1
@@ -738,7 +738,7 @@ def test_fast_variant_persistent_many_tiles():
     x = spmv_inputs.uniform_vector(n, seed=13)
     for variant, t, bt in [(5, 0, 512), (4, 0, 512), (6, 1024, 256), (6, 512, 256), (6, 1024, 512),
                            (7, 512, 256), (7, 1024, 256), (7, 1024, 512), (8, 1024, 256), (8, 512, 256),
-                           (10, 1536, 256), (10, 2048, 256), (11, 2, 0), (11, 4, 0),
+                           (10, 1536, 256), (10, 2048, 256), (11, 1, 0), (11, 2, 0),
                            (9, 512, 256), (9, 1024, 512)]:
         P.spmv_set_tile(C, variant, t, bt)
         check_persistent(C, g, n, x)
@@ -903,11 +903,11 @@ def test_tma_kernel_shapes_and_refusals():
     for g, rows in [((192, 192, 3), 1536), ((160, 160, 3), 1280), ((64, 48, 3), 1536), ((32, 64, 3), 1024),
                     ((96, 96, 3), 1536), ((16, 16, 16), 256)]:
         C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
-        for rpt in (2, 4):
-            P.spmv_set_tile(C, 11, rpt, 0)
+        for ty in (1, 2):
+            P.spmv_set_tile(C, 11, ty, 0)
             info = P.spmv_info(C)
             assert (info["fast_variant"], info["fast_tile_rows"], info["fast_block_threads"]) == \
-                (11, rows, rows // rpt), (g, rpt)
+                (11, rows, rows // (4 * ty)), (g, ty)
         with pytest.raises(P.SpmvError):
             P.spmv_set_tile(C, 11, 3, 0)
     # nx not a multiple of 4; no block of whole lines that divides ny; nx
@@ -932,7 +932,7 @@ def test_tma_kernel_misaligned_vectors_and_scale_changes():
     rowptr, col, val = oracle.hpcg_csr(*g)
     n = len(rowptr) - 1
     C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
-    P.spmv_set_tile(C, 11, 4, 0)
+    P.spmv_set_tile(C, 11, 2, 0)
     x = spmv_inputs.uniform_vector(n, seed=51)
     y_ref = oracle.spmv(rowptr, col, val, x)
     scale = abs_row_sums(rowptr, col, val, x)
