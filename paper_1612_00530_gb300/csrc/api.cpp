@@ -1155,4 +1155,20 @@ const char* spmv_version(void) { return "spmvc 0.1 (sm_103a)"; }
 namespace spmvc {
 int api_ensure_device(spmv_mat_s* m) { return ensure_device(m); }
 bool api_valid(spmv_mat_t m) { return valid(m); }
+
+// y = A x where the caller also has the partial maxima of x's high words
+// (xmax_n words, sign cleared): the TMA kernel then scales by the whole
+// vector's exponent (no rescaling of windows); other kernels ignore them.
+int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xmax_part, int xmax_n,
+                   cudaStream_t s) {
+    int st = ensure_device(A);
+    if (st) return st;
+    if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty() && A->fast_variant == 11 &&
+        A->tplan_ok && A->n > 0 && x != y) {
+        const cudaError_t e = launch_pattern_fast_tma(A->pat_view, A->tplan, x, y, s, xmax_part, xmax_n);
+        if (e == cudaSuccess) return SPMV_OK;
+        if (e != cudaErrorNotSupported) return cuda_fail(e, "spmv launch");
+    }
+    return spmv_apply(A, x, y, s);
+}
 }  // namespace spmvc

@@ -19,6 +19,8 @@
 namespace spmvc {
 int api_ensure_device(spmv_mat_s* m);
 bool api_valid(spmv_mat_t m);
+int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xmax_part, int xmax_n,
+                   cudaStream_t s);
 
 namespace {
 
@@ -26,7 +28,8 @@ constexpr int kRedBlocks = 1216;   // 8 blocks per SM; partial sums reduced by o
 constexpr int kRedThreads = 256;
 
 struct CgState {
-    double rr;          // current r.r (FP64 CG) or inner r.r (IR)
+    double rr;          // inner r.r (IR)
+    double rr2[2];      // FP64 CG: r.r before the step of that parity
     double rr0;         // inner: initial r.r
     double bnorm;
     double tol;
@@ -82,18 +85,19 @@ __global__ void __launch_bounds__(kRedThreads) dot_kernel(const double* __restri
 }
 
 // alpha = rr / (p.q); x += alpha p; r -= alpha q; partial sums of r.r
+// (par: the step's parity, which of st->rr2 holds its r.r)
 __global__ void __launch_bounds__(kRedThreads) update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
                                                                 const double* __restrict__ p,
                                                                 const double* __restrict__ q, int64_t n,
                                                                 const double* __restrict__ partial_pq,
                                                                 double* __restrict__ partial_rr,
-                                                                const CgState* __restrict__ st) {
+                                                                const CgState* __restrict__ st, int par) {
     if (st->done) return;
     __shared__ double sm[32];
     __shared__ double s_alpha;
     if (threadIdx.x < 32) {
         const double pq = sum_partials(partial_pq);
-        if (threadIdx.x == 0) s_alpha = st->rr / pq;
+        if (threadIdx.x == 0) s_alpha = st->rr2[par] / pq;
     }
     __syncthreads();
     const double alpha = s_alpha;
@@ -138,15 +142,31 @@ __global__ void __launch_bounds__(kRedThreads) update_xr_kernel(double* __restri
     if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
 }
 
-// beta = rr_new / rr; p = r + beta p
+// beta = rr_new / rr; p = r + beta p.  Block 0 also closes the step: the
+// new r.r into the other parity's slot, the step count, the history and
+// the convergence flag.  A block that starts after the flag is set skips
+// the update of p, which no later step reads then.
 __global__ void __launch_bounds__(kRedThreads) update_p_kernel(double* __restrict__ p, const double* __restrict__ r,
                                                                int64_t n, const double* __restrict__ partial_rr,
-                                                               const CgState* __restrict__ st) {
+                                                               CgState* __restrict__ st, double* __restrict__ hist,
+                                                               int par, uint32_t* __restrict__ pmax) {
     if (st->done) return;
     __shared__ double s_beta;
+    __shared__ uint32_t s_mx[32];
+    uint32_t mx = 0u;
     if (threadIdx.x < 32) {
         const double rr_new = sum_partials(partial_rr);
-        if (threadIdx.x == 0) s_beta = rr_new / st->rr;
+        if (threadIdx.x == 0) {
+            s_beta = rr_new / st->rr2[par];
+            if (blockIdx.x == 0) {
+                st->rr2[par ^ 1] = rr_new;
+                const int32_t it = st->it + 1;
+                st->it = it;
+                const double rel = sqrt(rr_new) / st->bnorm;
+                hist[it] = rel;
+                if (rel <= st->tol || it >= st->max_it) st->done = 1;
+            }
+        }
     }
     __syncthreads();
     const double beta = s_beta;
@@ -161,25 +181,28 @@ __global__ void __launch_bounds__(kRedThreads) update_p_kernel(double* __restric
             pv.x = fma(beta, pv.x, rv.x);
             pv.y = fma(beta, pv.y, rv.y);
             p2[i] = pv;
+            mx = max(mx, max(uint32_t(__double2hiint(pv.x)) & 0x7FFFFFFFu, uint32_t(__double2hiint(pv.y)) & 0x7FFFFFFFu));
         }
-        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = fma(beta, p[n - 1], r[n - 1]);
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            const double pl = fma(beta, p[n - 1], r[n - 1]);
+            p[n - 1] = pl;
+            mx = max(mx, uint32_t(__double2hiint(pl)) & 0x7FFFFFFFu);
+        }
     } else {
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride)
-            p[i] = fma(beta, p[i], r[i]);
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
+            const double pv = fma(beta, p[i], r[i]);
+            p[i] = pv;
+            mx = max(mx, uint32_t(__double2hiint(pv)) & 0x7FFFFFFFu);
+        }
     }
-}
-
-// rr = rr_new, history, convergence flag (one warp)
-__global__ void finalize_kernel(const double* __restrict__ partial_rr, CgState* __restrict__ st,
-                                double* __restrict__ hist) {
-    if (st->done) return;
-    const double rr_new = sum_partials(partial_rr);
-    if (threadIdx.x == 0) {
-        st->rr = rr_new;
-        st->it += 1;
-        const double rel = sqrt(rr_new) / st->bnorm;
-        hist[st->it] = rel;
-        if (rel <= st->tol || st->it >= st->max_it) st->done = 1;
+    // the block's largest high word of |p| (the next product's scale)
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < (blockDim.x >> 5) ? s_mx[threadIdx.x] : 0u;
+        v = __reduce_max_sync(0xFFFFFFFFu, v);
+        if (threadIdx.x == 0) pmax[blockIdx.x] = v;
     }
 }
 
@@ -198,9 +221,25 @@ __global__ void __launch_bounds__(kRedThreads) residual_kernel(const double* __r
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void copy_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t n) {
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-        dst[i] = src[i];
+// dst = src; pmax (optional): per block, the largest high word of |src|
+__global__ void __launch_bounds__(kRedThreads) copy_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                                           int64_t n, uint32_t* __restrict__ pmax) {
+    __shared__ uint32_t s_mx[32];
+    uint32_t mx = 0u;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double v = src[i];
+        dst[i] = v;
+        mx = max(mx, uint32_t(__double2hiint(v)) & 0x7FFFFFFFu);
+    }
+    if (!pmax) return;
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < (blockDim.x >> 5) ? s_mx[threadIdx.x] : 0u;
+        v = __reduce_max_sync(0xFFFFFFFFu, v);
+        if (threadIdx.x == 0) pmax[blockIdx.x] = v;
+    }
 }
 
 // ---------------------------------------------------- binary32 inner CG ---
@@ -720,7 +759,9 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     CgState* d_st = ws.get<CgState>(1);
     const int hist_cap = o.max_iter + 2;
     double* d_hist = ws.get<double>(hist_cap);
-    if (!r || !q || !p || !part_a || !part_b || !d_scalar || !d_st || !d_hist) return fail(SPMV_ENOMEM, "CG workspace");
+    uint32_t* pmax = ws.get<uint32_t>(kRedBlocks);
+    if (!r || !q || !p || !part_a || !part_b || !d_scalar || !d_st || !d_hist || !pmax)
+        return fail(SPMV_ENOMEM, "CG workspace");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -753,23 +794,28 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     if (o.mode == SPMV_CG_FP64) {
         CG_ST(true_residual());
         const double rr0 = read_scalar(d_scalar, s);
-        CgState h{rr0, rr0, bnorm, o.tol, 0, o.max_iter, 0, 0};
+        CgState h{rr0, {rr0, 0.0}, rr0, bnorm, o.tol, 0, o.max_iter, 0, 0};
         h.done = (std::sqrt(rr0) / bnorm <= o.tol) ? 1 : 0;
         CG_CUDA(cudaMemcpyAsync(d_st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
         const double h0 = std::sqrt(rr0) / bnorm;
         CG_CUDA(cudaMemcpyAsync(d_hist, &h0, sizeof(double), cudaMemcpyHostToDevice, s));
-        copy_kernel<<<G, T, 0, s>>>(p, r, n);
+        copy_kernel<<<G, T, 0, s>>>(p, r, n, pmax);
+        // steps alternate which slot of rr2 they read: the body is called
+        // once a step in order (captured or not), and an even chunk keeps a
+        // replayed graph's parities those of the global step count
+        int step = 0;
         auto body = [&]() -> int {
-            CG_ST(spmv_apply(A, p, q, s));
+            const int par = step++ & 1;
+            CG_ST(api_apply_xmax(A, p, q, pmax, int(G), s));
             dot_kernel<<<G, T, 0, s>>>(p, q, n, part_a, d_st);
-            update_xr_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_a, part_b, d_st);
-            update_p_kernel<<<G, T, 0, s>>>(p, r, n, part_b, d_st);
-            finalize_kernel<<<1, 32, 0, s>>>(part_b, d_st, d_hist);
+            update_xr_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_a, part_b, d_st, par);
+            update_p_kernel<<<G, T, 0, s>>>(p, r, n, part_b, d_st, d_hist, par, pmax);
             CG_CUDA(cudaGetLastError());
             return SPMV_OK;
         };
-        const int replays = (o.max_iter + o.check_every - 1) / o.check_every + 1;
-        CG_ST(run_until_done(s, o.use_graph != 0, o.check_every, d_st, replays, body));
+        const int chunk = (o.check_every + 1) & ~1;
+        const int replays = (o.max_iter + chunk - 1) / chunk + 1;
+        CG_ST(run_until_done(s, o.use_graph != 0, chunk, d_st, replays, body));
         CG_CUDA(cudaMemcpyAsync(&h, d_st, sizeof(h), cudaMemcpyDeviceToHost, s));
         CG_CUDA(cudaStreamSynchronize(s));
         history.resize(h.it + 1);

@@ -178,7 +178,8 @@ struct Share {
 template <int TY>
 __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
     pattern_fast_tma_kernel(const __grid_constant__ CUtensorMap xmap, const PatternView a, const TmaPlan tp,
-                            const double* __restrict__ x, double* __restrict__ y) {
+                            const double* __restrict__ x, double* __restrict__ y,
+                            const uint32_t* __restrict__ xmax_part, int xmax_n) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int K = 4 * TY;                          // rows a compute thread
     constexpr int SUB = kSlotElems / 4;
@@ -204,6 +205,14 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
 
     for (int i = tid; i < 64 * 8; i += blockDim.x) sexp[i] = __ldg(tp.expected + i);
     if (tid < 12) swmax[tid] = 0u;
+    // a caller that knows max |x| (partial maxima of the high words) fixes
+    // the scale for every run: no window ever raises it
+    uint32_t E_given = 0u;
+    if (xmax_part) {
+        uint32_t m = 0u;
+        for (int i = lane; i < xmax_n; i += 32) m = max(m, __ldg(xmax_part + i));
+        E_given = __reduce_max_sync(0xFFFFFFFFu, m) >> 20;
+    }
     if (tid == 0) {
         for (int i = 0; i < kRawStages; ++i) {
             mbar_init(raw_full + i, 1);
@@ -305,8 +314,8 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
         }
         int cz_cached = -1;
         uint32_t ex[K][7];
-        uint32_t E_true = 0u;            // largest biased exponent seen in this run of planes
-        uint32_t E_ring = 64u;           // scale of the converted windows: max(E_true, 64)
+        uint32_t E_true = E_given;       // largest biased exponent seen in this run of planes
+        uint32_t E_ring = max(E_given, 64u);   // scale of the converted windows: max(E_true, 64)
 
         auto store_limbs = [&](unsigned char* slot, int e, int2 v) {
             *reinterpret_cast<int2*>(slot + uint32_t(e & 3) * SUBB + uint32_t(e >> 2) * 8u) = v;
@@ -667,7 +676,7 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
 }
 
 cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, const double* x, double* y,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const uint32_t* xmax_part, int xmax_n) {
     if (a.n == 0 || tp.z_hi <= tp.z_lo) return cudaSuccess;
     if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) != 0) return cudaErrorNotSupported;
     if (tp.z_lo < 0 || tp.z_hi > tp.nz) return cudaErrorInvalidValue;
@@ -700,7 +709,7 @@ cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, con
             set[dev][tp.ty == 2] = true;
         }
     }
-    kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y);
+    kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y, xmax_part, xmax_n);
     return cudaGetLastError();
 }
 

@@ -275,10 +275,13 @@ struct TmaPlan {
 // false when the matrix or its grid has no compiled shape for variant 11.
 bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
                    std::vector<uint32_t>* expected);
-// Launches variant 11; falls back to cudaErrorNotSupported when x or y is
-// not 16-byte aligned (the TMA box and the bulk store need it).
+// Launches variant 11; returns cudaErrorNotSupported (nothing launched)
+// when x or y is not 16-byte aligned (the TMA box and the vector stores
+// need it).  xmax_part (optional): xmax_n words whose maximum is the largest
+// high word of |x_j| (sign cleared); the product then scales every run by
+// that exponent (the whole vector's) instead of the largest one it has met.
 cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, const double* x, double* y,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const uint32_t* xmax_part = nullptr, int xmax_n = 0);
 bool stage_supported(int nu);  // union sizes with a compiled staged kernel
 bool rstage_supported(const StagePlan& sp);  // plans the register-staged kernel takes
 

@@ -107,3 +107,27 @@ def test_ir_fp32_with_longer_inner_solves():
     res = P.cg_solve(C, b, x, tol=1e-10, mode="ir_fp32", inner_max_iter=400, inner_tol=1e-6)
     assert res["status"] == P.SPMV_OK and res["rel_residual"] <= 1e-10
     assert np.max(np.abs(x.cpu().numpy() - 1.0)) < 1e-8
+
+
+
+def test_cg_fp64_with_tma_kernel():
+    """FP64 CG whose FAST product is the TMA kernel: the history follows the
+    oracle's, is the same with and without graphs, and x reaches the
+    all-ones solution."""
+    g = (32, 64, 6)
+    csr, C, b, b_np = setup(g, "fast")
+    P.spmv_set_tile(C, 11, 1, 0)
+    x1 = torch.zeros_like(b)
+    r1 = P.cg_solve(C, b, x1, tol=1e-10, mode="fp64", check_every=8)
+    assert r1["status"] == P.SPMV_OK and r1["rel_residual"] <= 1.5e-10
+    x_ref, it_ref, hist_ref = oracle.cg(*csr, b_np, tol=1e-10, maxit=2000)
+    hist = np.array(r1["history"])
+    assert abs(r1["iterations"] - it_ref) <= 1
+    m = min(30, len(hist), len(hist_ref))
+    assert np.max(np.abs(hist[:m] / hist_ref[:m] - 1)) < 1e-8
+    assert np.max(np.abs(x1.cpu().numpy() - 1.0)) < 1e-8
+    x2 = torch.zeros_like(b)
+    r2 = P.cg_solve(C, b, x2, tol=1e-10, mode="fp64", check_every=8, use_graph=False)
+    assert r1["history"] == r2["history"]
+    assert torch.equal(x1, x2)
+    assert P.spmv_device_error(C) == 0
