@@ -9,70 +9,150 @@
 #include <cmath>
 #include <cstring>
 #include <map>
-#include <unordered_map>
 
+#include "host_par.h"
 #include "spmvc_internal.h"
 
 namespace spmvc {
 
 namespace {
 
-uint64_t bits_of(double v) {
-    uint64_t b;
-    std::memcpy(&b, &v, 8);
-    return b;
+double value_of(uint64_t bits) {
+    double v;
+    std::memcpy(&v, &bits, 8);
+    return v;
+}
+
+// Ascending values, -0.0 before +0.0.
+bool value_less(double a, double b) {
+    if (a != b) return a < b;
+    return std::signbit(a) > std::signbit(b);
 }
 
 // Value table of Sec. V: the distinct values in ascending order.  Values are
 // told apart by their bit patterns so that -0.0 and +0.0 both survive a
-// round trip; NaN is refused.
-int value_table(const std::vector<double>& val, std::vector<double>* dict,
-                std::unordered_map<uint64_t, int64_t>* counts) {
-    counts->clear();
-    for (double v : val) {
-        if (std::isnan(v)) return fail(SPMV_EUNSUPPORTED, "NaN matrix values cannot be tabled");
-        (*counts)[bits_of(v)]++;
-    }
+// round trip; NaN is refused, and so is a table above `limit` entries
+// (limit 0: no limit).  *counts receives every value's count.
+int value_table(const std::vector<double>& val, size_t limit, std::vector<double>* dict, BitsTable* counts,
+                const char* over_msg) {
+    bool over = false, nan = false;
+    count_values(val, limit, counts, &over, &nan);
+    if (nan) return fail(SPMV_EUNSUPPORTED, "NaN matrix values cannot be tabled");
+    if (over) return fail(SPMV_EUNSUPPORTED, over_msg);
     dict->clear();
-    for (const auto& kv : *counts) {
-        double v;
-        std::memcpy(&v, &kv.first, 8);
-        dict->push_back(v);
-    }
-    std::sort(dict->begin(), dict->end(), [](double a, double b) {
-        if (a != b) return a < b;
-        return std::signbit(a) > std::signbit(b);  // -0.0 before +0.0
-    });
+    counts->for_each([&](uint64_t k, int64_t) { dict->push_back(value_of(k)); });
+    std::sort(dict->begin(), dict->end(), value_less);
     return SPMV_OK;
 }
 
+// dict[v] -> v, looked up by bit pattern (-1 when absent)
+BitsTable code_table(const std::vector<double>& dict) {
+    BitsTable t;
+    for (size_t v = 0; v < dict.size(); ++v) t.at(value_bits(dict[v])) = int64_t(v);
+    return t;
+}
+
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Numbers the distinct keys of rows 0..n-1 in order of first appearance
+// (the row order, as one sequential pass would), chunks of rows in
+// parallel and their local tables merged in chunk order.  key_of(r, key)
+// fills row r's key and returns false to abort.  ids[r] receives row r's
+// number.  Returns 0, 1 when there are more than `limit` keys, 2 when
+// key_of aborted.
+template <class Key, class KeyOf>
+int register_first_seen(int64_t n, size_t limit, KeyOf&& key_of, std::vector<uint8_t>* ids, std::vector<Key>* keys) {
+    constexpr int64_t kGrain = 1 << 16;
+    const int parts = parallel_parts(n, kGrain);
+    std::vector<std::vector<Key>> local(parts);
+    std::vector<int> bad(parts, 0);
+    std::vector<int32_t> lid(static_cast<size_t>(n));
+    parallel_ranges(n, kGrain, [&](int64_t a, int64_t b, int t) {
+        std::map<Key, int32_t> reg;
+        Key k;
+        int32_t last = -1;
+        for (int64_t r = a; r < b; ++r) {
+            if (!key_of(r, k)) { bad[t] = 2; return; }
+            int32_t id;
+            if (last >= 0 && local[t][last] == k) {
+                id = last;
+            } else {
+                auto it = reg.find(k);
+                if (it == reg.end()) {
+                    if (local[t].size() == limit) { bad[t] = 1; return; }
+                    id = static_cast<int32_t>(local[t].size());
+                    reg.emplace(k, id);
+                    local[t].push_back(k);
+                } else {
+                    id = it->second;
+                }
+            }
+            lid[r] = id;
+            last = id;
+        }
+    });
+    for (int t = 0; t < parts; ++t)
+        if (bad[t]) return bad[t];
+    std::map<Key, int32_t> glob;
+    std::vector<std::vector<uint8_t>> remap(parts);
+    keys->clear();
+    for (int t = 0; t < parts; ++t)
+        for (const Key& k : local[t]) {
+            auto it = glob.find(k);
+            if (it == glob.end()) {
+                if (keys->size() == limit) return 1;
+                it = glob.emplace(k, static_cast<int32_t>(keys->size())).first;
+                keys->push_back(k);
+            }
+            remap[t].push_back(static_cast<uint8_t>(it->second));
+        }
+    ids->resize(static_cast<size_t>(n));
+    parallel_ranges(n, kGrain, [&](int64_t a, int64_t b, int t) {
+        for (int64_t r = a; r < b; ++r) (*ids)[r] = remap[t][lid[r]];
+    });
+    return 0;
+}
 
 }  // namespace
 
 // ------------------------------------------------------------------ ELL ---
 int pack_ell(const Csr& a, EllFormat* out) {
     const int64_t n = a.n;
-    out->nslices = (n + kSliceRows - 1) / kSliceRows;
-    out->slice_off.assign(out->nslices + 1, 0);
-    out->slice_w.assign(out->nslices, 0);
-    for (int64_t s = 0; s < out->nslices; ++s) {
-        int64_t w = 0;
-        for (int64_t r = s * kSliceRows; r < std::min(n, (s + 1) * kSliceRows); ++r)
-            w = std::max<int64_t>(w, a.rowptr[r + 1] - a.rowptr[r]);
-        out->slice_w[s] = static_cast<int32_t>(w);
-        out->slice_off[s + 1] = out->slice_off[s] + w * kSliceRows;
-    }
-    out->val.assign(out->slice_off.back(), 0.0);
-    out->col.assign(out->slice_off.back(), -1);
-    for (int64_t r = 0; r < n; ++r) {
-        const int64_t s = r / kSliceRows, l = r % kSliceRows;
-        int64_t t = 0;
-        for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k, ++t) {
-            out->val[out->slice_off[s] + t * kSliceRows + l] = a.val[k];
-            out->col[out->slice_off[s] + t * kSliceRows + l] = a.col[k];
+    const int64_t ns = (n + kSliceRows - 1) / kSliceRows;
+    out->nslices = ns;
+    out->slice_off.assign(ns + 1, 0);
+    out->slice_w.assign(ns, 0);
+    parallel_ranges(ns, 4096, [&](int64_t s0, int64_t s1, int) {
+        for (int64_t s = s0; s < s1; ++s) {
+            int64_t w = 0;
+            for (int64_t r = s * kSliceRows; r < std::min(n, (s + 1) * kSliceRows); ++r)
+                w = std::max<int64_t>(w, a.rowptr[r + 1] - a.rowptr[r]);
+            out->slice_w[s] = static_cast<int32_t>(w);
         }
-    }
+    });
+    for (int64_t s = 0; s < ns; ++s) out->slice_off[s + 1] = out->slice_off[s] + int64_t(out->slice_w[s]) * kSliceRows;
+    out->val.resize(out->slice_off.back());
+    out->col.resize(out->slice_off.back());
+    // every slot written once: a row's entries, then padding (value 0,
+    // column -1) up to the slice width
+    parallel_ranges(ns, 4096, [&](int64_t s0, int64_t s1, int) {
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t w = out->slice_w[s], base = out->slice_off[s];
+            for (int64_t l = 0; l < kSliceRows; ++l) {
+                const int64_t r = s * kSliceRows + l;
+                int64_t t = 0;
+                if (r < n)
+                    for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k, ++t) {
+                        out->val[base + t * kSliceRows + l] = a.val[k];
+                        out->col[base + t * kSliceRows + l] = a.col[k];
+                    }
+                for (; t < w; ++t) {
+                    out->val[base + t * kSliceRows + l] = 0.0;
+                    out->col[base + t * kSliceRows + l] = -1;
+                }
+            }
+        }
+    });
     return SPMV_OK;
 }
 
@@ -104,15 +184,21 @@ void derive_fast_order(int64_t n, PatternFormat* p) {
         p->mult.push_back(static_cast<int32_t>(m));
     }
     const int nu = static_cast<int>(p->uoff.size());
+    std::vector<int64_t> part_worst(parallel_parts(n, 1 << 16), 0);
+    parallel_ranges(n, 1 << 16, [&](int64_t a, int64_t b, int t) {
+        int64_t w = 0;
+        for (int64_t r = a; r < b; ++r) {
+            const uint8_t* rb = reinterpret_cast<const uint8_t*>(&p->rec[static_cast<size_t>(r) * p->words]);
+            const uint32_t mask = p->pmask[rb[nu]];
+            int64_t s = 0;
+            for (int u = 0; u < nu; ++u)
+                if ((mask >> u) & 1u) s += std::abs(p->mult[rb[u]]);
+            w = std::max(w, s);
+        }
+        part_worst[t] = w;
+    });
     int64_t worst = 0;
-    for (int64_t r = 0; r < n; ++r) {
-        const uint8_t* b = reinterpret_cast<const uint8_t*>(&p->rec[static_cast<size_t>(r) * p->words]);
-        const uint32_t mask = p->pmask[b[nu]];
-        int64_t s = 0;
-        for (int u = 0; u < nu; ++u)
-            if ((mask >> u) & 1u) s += std::abs(p->mult[b[u]]);
-        worst = std::max(worst, s);
-    }
+    for (int64_t w : part_worst) worst = std::max(worst, w);
     p->max_row_abs = worst;
     p->mult_exp = e_min;
     p->fast_ok = worst < 1024;
@@ -147,42 +233,22 @@ bool build_row_types(int64_t n, PatternFormat* p) {
 // -------------------------------------------------------------- pattern ---
 int compress_pattern(const Csr& a, int max_dict, PatternFormat* out) {
     const int64_t n = a.n;
-    std::unordered_map<uint64_t, int64_t> counts;
-    int st = value_table(a.val, &out->dict, &counts);
+    BitsTable counts;
+    int st = value_table(a.val, static_cast<size_t>(max_dict), &out->dict, &counts, "value table larger than max_dict");
     if (st) return st;
-    if (static_cast<int>(out->dict.size()) > max_dict)
-        return fail(SPMV_EUNSUPPORTED, "value table larger than max_dict");
-    std::unordered_map<uint64_t, int> code_of;
-    for (size_t v = 0; v < out->dict.size(); ++v) code_of[bits_of(out->dict[v])] = static_cast<int>(v);
+    const BitsTable code = code_table(out->dict);
 
     // Register each row's displacement list (columns relative to the
     // diagonal) in the pattern table (Sec. V).
-    std::map<std::vector<int32_t>, int> registry;
     std::vector<std::vector<int32_t>> patterns;
-    std::vector<uint8_t> row_pat(n);
-    std::vector<int32_t> disp;
-    int last = -1;
-    for (int64_t r = 0; r < n; ++r) {
+    std::vector<uint8_t> row_pat;
+    auto disp_of = [&](int64_t r, std::vector<int32_t>& disp) {
         disp.clear();
         for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k) disp.push_back(static_cast<int32_t>(a.col[k] - r));
-        int id;
-        if (last >= 0 && patterns[last] == disp) {
-            id = last;
-        } else {
-            auto it = registry.find(disp);
-            if (it == registry.end()) {
-                if (static_cast<int>(patterns.size()) == kMaxPatterns)
-                    return fail(SPMV_EUNSUPPORTED, "more than 32 displacement patterns");
-                id = static_cast<int>(patterns.size());
-                registry.emplace(disp, id);
-                patterns.push_back(disp);
-            } else {
-                id = it->second;
-            }
-        }
-        row_pat[r] = static_cast<uint8_t>(id);
-        last = id;
-    }
+        return true;
+    };
+    if (register_first_seen(n, kMaxPatterns, disp_of, &row_pat, &patterns))
+        return fail(SPMV_EUNSUPPORTED, "more than 32 displacement patterns");
     // union of displacements and per-pattern slot masks
     std::vector<int32_t> uni;
     for (const auto& p : patterns) uni.insert(uni.end(), p.begin(), p.end());
@@ -201,18 +267,20 @@ int compress_pattern(const Csr& a, int max_dict, PatternFormat* out) {
             slot_of[p].push_back(u);
         }
     out->words = (nu + 1 + 3) / 4;
-    out->rec.assign(static_cast<size_t>(n) * out->words, 0u);
+    out->rec.resize(static_cast<size_t>(n) * out->words);
     const uint8_t absent = static_cast<uint8_t>(out->dict.size());
-    std::vector<uint8_t> bytes(4 * out->words);
-    for (int64_t r = 0; r < n; ++r) {
-        std::fill(bytes.begin(), bytes.end(), 0);
-        std::fill(bytes.begin(), bytes.begin() + nu, absent);
-        const int p = row_pat[r];
-        int64_t k = a.rowptr[r];
-        for (int u : slot_of[p]) bytes[u] = static_cast<uint8_t>(code_of[bits_of(a.val[k++])]);
-        bytes[nu] = static_cast<uint8_t>(p);
-        std::memcpy(&out->rec[static_cast<size_t>(r) * out->words], bytes.data(), bytes.size());
-    }
+    parallel_ranges(n, 1 << 16, [&](int64_t r0, int64_t r1, int) {
+        std::vector<uint8_t> bytes(4 * out->words);
+        for (int64_t r = r0; r < r1; ++r) {
+            std::fill(bytes.begin(), bytes.end(), 0);
+            std::fill(bytes.begin(), bytes.begin() + nu, absent);
+            const int p = row_pat[r];
+            int64_t k = a.rowptr[r];
+            for (int u : slot_of[p]) bytes[u] = static_cast<uint8_t>(code.get(value_bits(a.val[k++]), 0));
+            bytes[nu] = static_cast<uint8_t>(p);
+            std::memcpy(&out->rec[static_cast<size_t>(r) * out->words], bytes.data(), bytes.size());
+        }
+    });
 
     derive_fast_order(n, out);
     return SPMV_OK;
@@ -225,38 +293,35 @@ int compress_pattern(const Csr& a, int max_dict, PatternFormat* out) {
 // value group (Fig. 2's terminal indices, stored exclusive).
 int compress_dit(const Csr& a, DitFormat* out) {
     const int64_t n = a.n;
-    std::unordered_map<uint64_t, int64_t> counts;
-    int st = value_table(a.val, &out->dict, &counts);
+    BitsTable counts;
+    int st = value_table(a.val, 255, &out->dict, &counts, "Data+Index Table: more than 255 distinct values");
     if (st) return st;
     const int nv = static_cast<int>(out->dict.size());
-    if (nv > 255) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: more than 255 distinct values");
-    std::unordered_map<uint64_t, int> code_of;
-    for (int v = 0; v < nv; ++v) code_of[bits_of(out->dict[v])] = v;
-    std::map<std::vector<int32_t>, int> types;
+    const BitsTable code = code_table(out->dict);
+    out->ends.resize(static_cast<size_t>(n) * nv);
+    // a row's displacement list, its entries grouped by value code (value
+    // groups ascending, columns ascending inside a group), and the end of
+    // each group
+    auto disp_of = [&](int64_t r, std::vector<int32_t>& disp) {
+        const int64_t k0 = a.rowptr[r], len = a.rowptr[r + 1] - k0;
+        if (len > 255) return false;
+        uint8_t c[255];
+        int32_t pos[257];
+        std::fill(pos, pos + nv + 1, 0);
+        for (int64_t i = 0; i < len; ++i) {
+            c[i] = static_cast<uint8_t>(code.get(value_bits(a.val[k0 + i]), 0));
+            ++pos[c[i] + 1];
+        }
+        for (int v = 0; v < nv; ++v) pos[v + 1] += pos[v];
+        disp.resize(static_cast<size_t>(len));
+        for (int64_t i = 0; i < len; ++i) disp[pos[c[i]]++] = static_cast<int32_t>(a.col[k0 + i] - r);
+        for (int v = 0; v < nv; ++v) out->ends[static_cast<size_t>(v) * n + r] = static_cast<uint8_t>(pos[v]);
+        return true;
+    };
     std::vector<std::vector<int32_t>> lists;
-    out->type.assign(static_cast<size_t>(n), 0);
-    out->ends.assign(static_cast<size_t>(n) * nv, 0);
-    std::vector<std::vector<int32_t>> groups(nv);
-    std::vector<int32_t> disp;
-    for (int64_t r = 0; r < n; ++r) {
-        const int64_t len = a.rowptr[r + 1] - a.rowptr[r];
-        if (len > 255) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: a row holds more than 255 entries");
-        for (auto& g : groups) g.clear();
-        for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k)
-            groups[code_of[bits_of(a.val[k])]].push_back(static_cast<int32_t>(a.col[k] - r));
-        disp.clear();
-        for (int v = 0; v < nv; ++v) {
-            disp.insert(disp.end(), groups[v].begin(), groups[v].end());
-            out->ends[static_cast<size_t>(v) * n + r] = static_cast<uint8_t>(disp.size());
-        }
-        auto it = types.find(disp);
-        if (it == types.end()) {
-            if (types.size() == 256) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: more than 256 row types");
-            it = types.emplace(disp, static_cast<int>(lists.size())).first;
-            lists.push_back(disp);
-        }
-        out->type[r] = static_cast<uint8_t>(it->second);
-    }
+    st = register_first_seen(n, 256, disp_of, &out->type, &lists);
+    if (st == 2) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: a row holds more than 255 entries");
+    if (st == 1) return fail(SPMV_EUNSUPPORTED, "Data+Index Table: more than 256 row types");
     out->maxlen = 0;
     for (const auto& l : lists) out->maxlen = std::max<int32_t>(out->maxlen, static_cast<int32_t>(l.size()));
     out->disp.assign(lists.size() * static_cast<size_t>(std::max(out->maxlen, 1)), 0);
@@ -272,83 +337,88 @@ int compress_dit(const Csr& a, DitFormat* out) {
 // The delta format's value table: the most frequent values with at least
 // min_count uses, at most max_dict of them, in ascending order.
 void delta_dictionary(const std::vector<double>& val, int max_dict, int min_count, std::vector<double>* dict) {
-    std::unordered_map<uint64_t, int64_t> counts;
-    std::vector<double> all;
-    if (value_table(val, &all, &counts)) {
-        // NaN values: no table at all, every slice raw
-        all.clear();
-        counts.clear();
-    }
+    BitsTable counts;
+    bool over = false, nan = false;
+    count_values(val, 0, &counts, &over, &nan);
     std::vector<std::pair<int64_t, double>> freq;
-    for (double v : all) {
-        const int64_t c = counts[bits_of(v)];
-        if (c >= min_count) freq.emplace_back(-c, v);
-    }
+    // NaN values: no table at all, every slice raw
+    if (!nan)
+        counts.for_each([&](uint64_t k, int64_t c) {
+            if (c >= min_count) freq.emplace_back(-c, value_of(k));
+        });
     std::sort(freq.begin(), freq.end(), [](const auto& x, const auto& y) {
         if (x.first != y.first) return x.first < y.first;
-        return x.second < y.second;
+        return value_less(x.second, y.second);
     });
     if (static_cast<int>(freq.size()) > max_dict) freq.resize(max_dict);
     dict->clear();
     for (const auto& f : freq) dict->push_back(f.second);
-    std::sort(dict->begin(), dict->end(), [](double x, double y) {
-        if (x != y) return x < y;
-        return std::signbit(x) > std::signbit(y);
-    });
+    std::sort(dict->begin(), dict->end(), value_less);
 }
 
 int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) {
     const int64_t n = a.n;
     delta_dictionary(a.val, max_dict, min_count, &out->dict);
-    std::unordered_map<uint64_t, int> code_of;
-    for (size_t v = 0; v < out->dict.size(); ++v) code_of[bits_of(out->dict[v])] = static_cast<int>(v);
+    const BitsTable code = code_table(out->dict);
 
-    out->nslices = (n + kSliceRows - 1) / kSliceRows;
-    out->hdr.assign(out->nslices, DeltaSlice{0, 0, 0});
-    uint64_t off = 0;
-    for (int64_t s = 0; s < out->nslices; ++s) {
-        const int64_t r0 = s * kSliceRows, r1 = std::min(n, r0 + kSliceRows);
-        int64_t w = 0;
-        uint32_t flags = 0;
-        for (int64_t r = r0; r < r1; ++r) {
-            w = std::max<int64_t>(w, a.rowptr[r + 1] - a.rowptr[r]);
-            for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k) {
-                const int64_t dlt = static_cast<int64_t>(a.col[k]) - r;
-                if (dlt < -32768 || dlt > 32767) flags |= kSliceColRaw;
-                if (std::isnan(a.val[k]) || code_of.find(bits_of(a.val[k])) == code_of.end()) flags |= kSliceValRaw;
+    const int64_t ns = (n + kSliceRows - 1) / kSliceRows;
+    out->nslices = ns;
+    out->hdr.assign(ns, DeltaSlice{0, 0, 0});
+    std::vector<uint64_t> bytes(static_cast<size_t>(ns));
+    std::atomic<bool> too_wide{false};
+    parallel_ranges(ns, 2048, [&](int64_t s0, int64_t s1, int) {
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t r0 = s * kSliceRows, r1 = std::min(n, r0 + kSliceRows);
+            int64_t w = 0;
+            uint32_t flags = 0;
+            for (int64_t r = r0; r < r1; ++r) {
+                w = std::max<int64_t>(w, a.rowptr[r + 1] - a.rowptr[r]);
+                for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k) {
+                    const int64_t dlt = static_cast<int64_t>(a.col[k]) - r;
+                    if (dlt < -32768 || dlt > 32767) flags |= kSliceColRaw;
+                    if (std::isnan(a.val[k]) || code.get(value_bits(a.val[k]), -1) < 0) flags |= kSliceValRaw;
+                }
             }
+            if (w > 255) too_wide = true;
+            const int64_t cb = (flags & kSliceColRaw) ? 4 : 2, vb = (flags & kSliceValRaw) ? 8 : 1;
+            out->hdr[s] = DeltaSlice{0, static_cast<uint32_t>(std::min<int64_t>(w, 255)), flags};
+            bytes[s] = round_up(32 + w * kSliceRows * cb, 16) + round_up(w * kSliceRows * vb, 16);
         }
-        if (w > 255) return fail(SPMV_EUNSUPPORTED, "delta format holds at most 255 entries per row");
-        const int64_t cb = (flags & kSliceColRaw) ? 4 : 2, vb = (flags & kSliceValRaw) ? 8 : 1;
-        out->hdr[s] = DeltaSlice{off, static_cast<uint32_t>(w), flags};
-        off += round_up(32 + w * kSliceRows * cb, 16) + round_up(w * kSliceRows * vb, 16);
+    });
+    if (too_wide) return fail(SPMV_EUNSUPPORTED, "delta format holds at most 255 entries per row");
+    uint64_t off = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        out->hdr[s].off = off;
+        off += bytes[s];
     }
     out->payload.assign(off, 0);
-    for (int64_t s = 0; s < out->nslices; ++s) {
-        const DeltaSlice h = out->hdr[s];
-        const int64_t r0 = s * kSliceRows, r1 = std::min(n, r0 + kSliceRows);
-        uint8_t* base = out->payload.data() + h.off;
-        const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
-        uint8_t* cols = base + 32;
-        uint8_t* vals = base + round_up(32 + int64_t(h.w) * kSliceRows * (craw ? 4 : 2), 16);
-        for (int64_t r = r0; r < r1; ++r) {
-            const int64_t l = r - r0;
-            base[l] = static_cast<uint8_t>(a.rowptr[r + 1] - a.rowptr[r]);
-            int64_t t = 0;
-            for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k, ++t) {
-                const int64_t slot = t * kSliceRows + l;
-                if (craw) {
-                    const int32_t c = a.col[k];
-                    std::memcpy(cols + 4 * slot, &c, 4);
-                } else {
-                    const int16_t d16 = static_cast<int16_t>(a.col[k] - r);
-                    std::memcpy(cols + 2 * slot, &d16, 2);
+    parallel_ranges(ns, 2048, [&](int64_t s0, int64_t s1, int) {
+        for (int64_t s = s0; s < s1; ++s) {
+            const DeltaSlice h = out->hdr[s];
+            const int64_t r0 = s * kSliceRows, r1 = std::min(n, r0 + kSliceRows);
+            uint8_t* base = out->payload.data() + h.off;
+            const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
+            uint8_t* cols = base + 32;
+            uint8_t* vals = base + round_up(32 + int64_t(h.w) * kSliceRows * (craw ? 4 : 2), 16);
+            for (int64_t r = r0; r < r1; ++r) {
+                const int64_t l = r - r0;
+                base[l] = static_cast<uint8_t>(a.rowptr[r + 1] - a.rowptr[r]);
+                int64_t t = 0;
+                for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k, ++t) {
+                    const int64_t slot = t * kSliceRows + l;
+                    if (craw) {
+                        const int32_t c = a.col[k];
+                        std::memcpy(cols + 4 * slot, &c, 4);
+                    } else {
+                        const int16_t d16 = static_cast<int16_t>(a.col[k] - r);
+                        std::memcpy(cols + 2 * slot, &d16, 2);
+                    }
+                    if (vraw) std::memcpy(vals + 8 * slot, &a.val[k], 8);
+                    else vals[slot] = static_cast<uint8_t>(code.get(value_bits(a.val[k]), 0));
                 }
-                if (vraw) std::memcpy(vals + 8 * slot, &a.val[k], 8);
-                else vals[slot] = static_cast<uint8_t>(code_of[bits_of(a.val[k])]);
             }
         }
-    }
+    });
     return SPMV_OK;
 }
 

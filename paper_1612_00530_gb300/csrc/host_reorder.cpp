@@ -7,19 +7,39 @@
 // permutation is applied as B = P A P^T; products gather x and scatter y.
 #include <algorithm>
 #include <cstring>
-#include <unordered_set>
 #include <vector>
 
+#include "host_par.h"
 #include "spmvc_internal.h"
 
 namespace spmvc {
 
 namespace {
 
-uint64_t bits_of(double v) {
-    uint64_t b;
-    std::memcpy(&b, &v, 8);
-    return b;
+// Row i of P A P^T (perm[i] = old row) or of P^T B P (the inverse map):
+// row `src` of m with every column c mapped to colmap[c], columns sorted.
+void permute_rows(const Csr& m, const std::vector<int32_t>& rowsrc, const std::vector<int32_t>& colmap, Csr* out) {
+    const int64_t n = m.n;
+    out->n = n;
+    out->rowptr.assign(static_cast<size_t>(n) + 1, 0);
+    for (int64_t i = 0; i < n; ++i) out->rowptr[i + 1] = out->rowptr[i] + (m.rowptr[rowsrc[i] + 1] - m.rowptr[rowsrc[i]]);
+    out->col.resize(m.col.size());
+    out->val.resize(m.val.size());
+    parallel_ranges(n, 1 << 15, [&](int64_t a, int64_t b, int) {
+        std::vector<std::pair<int32_t, double>> row;
+        for (int64_t i = a; i < b; ++i) {
+            const int32_t o = rowsrc[i];
+            row.clear();
+            for (int64_t k = m.rowptr[o]; k < m.rowptr[o + 1]; ++k) row.emplace_back(colmap[m.col[k]], m.val[k]);
+            std::sort(row.begin(), row.end(), [](const auto& p, const auto& q) { return p.first < q.first; });
+            int64_t pos = out->rowptr[i];
+            for (const auto& e : row) {
+                out->col[pos] = e.first;
+                out->val[pos] = e.second;
+                ++pos;
+            }
+        }
+    });
 }
 
 // Breadth-first levels from `start` over unvisited nodes; returns the nodes
@@ -57,12 +77,14 @@ int reorder_rcm(const Csr& a, const std::vector<double>& dict, std::vector<int32
     std::vector<int32_t> deg(static_cast<size_t>(n));
     for (int64_t i = 0; i < n; ++i) deg[i] = static_cast<int32_t>(a.rowptr[i + 1] - a.rowptr[i]);
     // rows holding a value outside the table
-    std::unordered_set<uint64_t> in_table;
-    for (double v : dict) in_table.insert(bits_of(v));
+    BitsTable in_table;
+    for (double v : dict) in_table.at(value_bits(v)) = 1;
     std::vector<uint8_t> dirty(static_cast<size_t>(n), 0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k)
-            if (!in_table.count(bits_of(a.val[k]))) { dirty[i] = 1; break; }
+    parallel_ranges(n, 1 << 15, [&](int64_t r0, int64_t r1, int) {
+        for (int64_t i = r0; i < r1; ++i)
+            for (int64_t k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k)
+                if (!in_table.get(value_bits(a.val[k]), 0)) { dirty[i] = 1; break; }
+    });
     // nodes by ascending degree: each component starts from its first one,
     // moved to a pseudo-peripheral node (last level, smallest degree) by two
     // extra sweeps
@@ -115,52 +137,16 @@ int reorder_rcm(const Csr& a, const std::vector<double>& dict, std::vector<int32
 }
 
 void permute_csr(const Csr& a, const std::vector<int32_t>& perm, Csr* out) {
-    const int64_t n = a.n;
-    std::vector<int32_t> inv(static_cast<size_t>(n));
-    for (int64_t i = 0; i < n; ++i) inv[perm[i]] = static_cast<int32_t>(i);
-    out->n = n;
-    out->rowptr.assign(static_cast<size_t>(n) + 1, 0);
-    out->col.resize(a.col.size());
-    out->val.resize(a.val.size());
-    std::vector<std::pair<int32_t, double>> row;
-    int64_t pos = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        const int32_t o = perm[i];
-        row.clear();
-        for (int64_t k = a.rowptr[o]; k < a.rowptr[o + 1]; ++k) row.emplace_back(inv[a.col[k]], a.val[k]);
-        std::sort(row.begin(), row.end(), [](const auto& p, const auto& q) { return p.first < q.first; });
-        for (const auto& e : row) {
-            out->col[pos] = e.first;
-            out->val[pos] = e.second;
-            ++pos;
-        }
-        out->rowptr[i + 1] = pos;
-    }
+    std::vector<int32_t> inv(perm.size());
+    for (size_t i = 0; i < perm.size(); ++i) inv[perm[i]] = static_cast<int32_t>(i);
+    permute_rows(a, perm, inv, out);
 }
 
+// A = P^T B P: row o of A is row inv[o] of B with columns mapped back
 void unpermute_csr(const Csr& b, const std::vector<int32_t>& perm, Csr* out) {
-    const int64_t n = b.n;
-    std::vector<int32_t> inv(static_cast<size_t>(n));
-    for (int64_t i = 0; i < n; ++i) inv[perm[i]] = static_cast<int32_t>(i);
-    // A = P^T B P: row o of A is row inv[o] of B with columns mapped back
-    out->n = n;
-    out->rowptr.assign(static_cast<size_t>(n) + 1, 0);
-    out->col.resize(b.col.size());
-    out->val.resize(b.val.size());
-    std::vector<std::pair<int32_t, double>> row;
-    int64_t pos = 0;
-    for (int64_t o = 0; o < n; ++o) {
-        const int32_t i = inv[o];
-        row.clear();
-        for (int64_t k = b.rowptr[i]; k < b.rowptr[i + 1]; ++k) row.emplace_back(perm[b.col[k]], b.val[k]);
-        std::sort(row.begin(), row.end(), [](const auto& p, const auto& q) { return p.first < q.first; });
-        for (const auto& e : row) {
-            out->col[pos] = e.first;
-            out->val[pos] = e.second;
-            ++pos;
-        }
-        out->rowptr[o + 1] = pos;
-    }
+    std::vector<int32_t> inv(perm.size());
+    for (size_t i = 0; i < perm.size(); ++i) inv[perm[i]] = static_cast<int32_t>(i);
+    permute_rows(b, inv, perm, out);
 }
 
 }  // namespace spmvc
