@@ -36,11 +36,17 @@ METRIC = "SpMV GFLOP/s + % HBM roofline, compressed vs plain ELL, 192^3 HPCG, 1 
 WORKLOAD = "hpcg_192^3_x_seed1_compressed_pattern_uint8codes_5bit_patterns_vs_ell"
 
 
+KERNEL_SOURCES = ("k_spmv.cu", "k_tma.cu", "fast_fixed.cuh")
+
+
 def kernel_source_hash() -> str:
+    """sha256 (first 16 hex digits) of the FAST kernels' sources, in order."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1612_00530_gb300", "csrc", "k_spmv.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1612_00530_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled(kernel: str, tag: str = "traffic", key: str = "bytes"):
@@ -229,174 +235,156 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_suite(args):
-    """One JSON line per further workload (irregular 128^3, CG vs IR-CG on
-    192^3, SpMM k = 1..32 on 160^3, the ragged batch).  Not the headline."""
-    import torch
-
-    import oracle
-    import paper_1612_00530_gb300 as P
-    import spmv_inputs
-    from paper_1612_00530_gb300 import build as lib_build
-
-    lib_build.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    peaks = measured_peaks()
-
+def make_timer(torch, stream=None):
+    """ms per call of fn, CUDA events on `stream` (the current stream by
+    default) after `warm` untimed calls."""
     def time_ms(fn, steps, warm=3):
+        st = stream or torch.cuda.current_stream()
         for _ in range(warm):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+        e0.record(st)
         for _ in range(steps):
             fn()
-        e1.record()
+        e1.record(st)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
+    return time_ms
 
-    def emit(d):
-        print(json.dumps(d), flush=True)
 
-    # --- irregular 128^3: delta format (bit-exact) vs ELL
+def bench_irregular(P, torch, dev, time_ms, peaks, iters=100):
+    """Irregular 128^3 (seed 2): ELL vs the delta format, unordered and with
+    the locality reordering inside spmv_compress (both bit-exact)."""
+    import spmv_inputs
     A = P.spmv_build("irregular", 128, 128, 128, seed=2)
     C = P.spmv_compress(A)
     ia, ic = P.spmv_info(A), P.spmv_info(C)
     n, nnz = ic["n"], ic["nnz"]
     x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=2)).to(dev)
     y = torch.empty_like(x)
-    t_ell = time_ms(lambda: P.spmv_apply(A, x, y), 200)
-    t_d = time_ms(lambda: P.spmv_apply(C, x, y), 200)
-    emit({"workload": "irregular_128^3_seed2", "rows": n, "nnz": nnz,
-          "ell": {"gflops": 2 * nnz / t_ell / 1e6, "ms": t_ell, "gbs": (ia["format_bytes"] + 16 * n) / t_ell / 1e6},
-          "delta": {"gflops": 2 * nnz / t_d / 1e6, "ms": t_d, "gbs": (ic["format_bytes"] + 16 * n) / t_d / 1e6,
-                    "format_bytes_per_nnz": ic["format_bytes"] / nnz, "dict_size": ic["dict_size"],
-                    "slices_value_raw_frac": ic["slices_value_raw"] / ic["n_slices"],
-                    "slices_col_raw_frac": ic["slices_col_raw"] / ic["n_slices"]},
-          "peak_gbs": peaks["hbm_gbs"], "order": "column (bit-exact)"})
-    # the same matrix with locality reordering inside spmv_compress
+    t_ell = time_ms(lambda: P.spmv_apply(A, x, y), iters)
+    t_d = time_ms(lambda: P.spmv_apply(C, x, y), iters)
     t0 = time.perf_counter()
     R = P.spmv_compress(A, reorder=True)
     t_reorder = time.perf_counter() - t0
     ir = P.spmv_info(R)
-    t_r = time_ms(lambda: P.spmv_apply(R, x, y), 200)
-    emit({"workload": "irregular_128^3_seed2_reordered", "rows": n, "nnz": nnz,
-          "reordered_delta": {"gflops": 2 * nnz / t_r / 1e6, "ms": t_r,
-                              "gbs": (ir["format_bytes"] + 16 * n + 40 * n) / t_r / 1e6,
-                              "format_bytes_per_nnz": ir["format_bytes"] / nnz, "dict_size": ir["dict_size"],
-                              "bandwidth": ir["bandwidth"], "bandwidth_unordered": ic["bandwidth"],
-                              "slices_value_raw_frac": ir["slices_value_raw"] / ir["n_slices"],
-                              "slices_col_raw_frac": ir["slices_col_raw"] / ir["n_slices"],
-                              "compress_seconds": t_reorder},
-          "speedup_vs_ell": t_ell / t_r, "speedup_vs_unordered_delta": t_d / t_r,
-          "note": "gbs counts the gather of x and scatter of y (40 B/row) around the product",
-          "order": "column order of the reordered matrix"})
-    del A, C, R, x, y
+    t_r = time_ms(lambda: P.spmv_apply(R, x, y), iters)
 
-    # --- Table II's three layouts on 192^3: plain ELL ("Original"), the
-    # pattern format and the Data+Index Table decoded as Listing 1
-    A = P.spmv_build("hpcg", 192, 192, 192)
+    def fmt(info, ms, extra_bytes):
+        return {"gflops": 2 * nnz / ms / 1e6, "ms": ms, "bytes_per_nnz": info["format_bytes"] / nnz,
+                "gbs": (info["format_bytes"] + extra_bytes) / ms / 1e6,
+                "slices_value_raw_frac": info["slices_value_raw"] / info["n_slices"],
+                "slices_col_raw_frac": info["slices_col_raw"] / info["n_slices"], "dict_size": info["dict_size"],
+                "bandwidth": info["bandwidth"]}
+    out = {"rows": n, "nnz": nnz, "ell": {"gflops": 2 * nnz / t_ell / 1e6, "ms": t_ell,
+                                           "bytes_per_nnz": ia["format_bytes"] / nnz},
+           "delta": fmt(ic, t_d, 16 * n),
+           "delta_reordered": dict(fmt(ir, t_r, 56 * n), compress_seconds=t_reorder),
+           "speedup_vs_ell": {"delta": t_ell / t_d, "delta_reordered": t_ell / t_r},
+           "peak_gbs": peaks["hbm_gbs"],
+           "note": "gbs counts format bytes + x,y (16 B/row); reordered also the gather of x and scatter of y "
+                   "(40 B/row more); column order, bit-exact"}
+    return out
+
+
+def bench_table2(P, torch, dev, A, x, time_ms, peaks, iters=100):
+    """Table II's layouts on 192^3: plain ELL ("Original"), the Data+Index
+    Table decoded in Listing 1's order (bit-exact), beside the headline
+    pattern format."""
     D = P.spmv_compress(A, format="dit")
-    ia, idt = P.spmv_info(A), P.spmv_info(D)
+    idt = P.spmv_info(D)
     n, nnz = idt["n"], idt["nnz"]
-    x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=1)).to(dev)
     y = torch.empty_like(x)
-    t_ell = time_ms(lambda: P.spmv_apply(A, x, y), 100)
-    t_dit = time_ms(lambda: P.spmv_apply(D, x, y), 100)
+    t_ell = time_ms(lambda: P.spmv_apply(A, x, y), iters)
+    t_dit = time_ms(lambda: P.spmv_apply(D, x, y), iters)
     dit_bytes = idt["format_bytes"] + 16 * n
-    emit({"workload": "hpcg_192^3_table2_layouts", "rows": n, "nnz": nnz,
-          "ell": {"gflops": 2 * nnz / t_ell / 1e6, "ms": t_ell},
-          "data_index_table": {"gflops": 2 * nnz / t_dit / 1e6, "ms": t_dit, "types": idt["n_patterns"],
-                               "bytes_per_row": idt["record_bytes"], "paper_bytes_per_row": 12,
-                               "gbs": dit_bytes / t_dit / 1e6, "frac_of_hbm": dit_bytes / t_dit / 1e6 / peaks["hbm_gbs"],
-                               "order": "Listing 1 (value groups ascending, fma per entry; bit-exact)"},
-          "speedup_vs_ell": t_ell / t_dit, "peak_gbs": peaks["hbm_gbs"]})
-    del D
+    return {"rows": n, "nnz": nnz,
+            "original_ell": {"gflops": 2 * nnz / t_ell / 1e6, "ms": t_ell, "bytes_per_row": 12 * nnz / n},
+            "data_index_table": {"gflops": 2 * nnz / t_dit / 1e6, "ms": t_dit, "types": idt["n_patterns"],
+                                 "bytes_per_row": idt["record_bytes"], "paper_bytes_per_row": 12,
+                                 "gbs": dit_bytes / t_dit / 1e6,
+                                 "frac_of_hbm": dit_bytes / t_dit / 1e6 / peaks["hbm_gbs"]},
+            "speedup_vs_ell": t_ell / t_dit, "order": "Listing 1 (value groups ascending; bit-exact)"}
 
-    # --- values registered in the pattern (Sec. V): one byte a row instead of
-    # the 28-byte record, same FAST kernel family, best tile shape
-    T = P.spmv_compress(A, format="pattern", order="fast")
-    best = None
-    for t, bt in ((1024, 256), (512, 256), (1024, 512)):
-        P.spmv_set_tile(T, 9, t, bt)
-        ms = time_ms(lambda: P.spmv_apply(T, x, y), 200)
-        if best is None or ms < best[0]:
-            best = (ms, t, bt)
-    it = P.spmv_info(T)
-    typed_bytes = n * 1 + 16 * n
-    emit({"workload": "hpcg_192^3_row_types", "rows": n, "nnz": nnz, "row_types": it["row_types"],
-          "gflops": 2 * nnz / best[0] / 1e6, "ms": best[0], "tile_rows": best[1], "threads": best[2],
-          "bytes_per_row": 1 + 16, "gbs": typed_bytes / best[0] / 1e6,
-          "frac_of_hbm": typed_bytes / best[0] / 1e6 / peaks["hbm_gbs"], "speedup_vs_ell": t_ell / best[0],
-          "order": "fast (<= 1e-14)"})
-    del T, x, y
 
-    # --- CG vs IR-CG on 192^3, b = A 1, x0 = 0, tol 1e-10
-    C = P.spmv_compress(A, format="pattern", order="fast")
+def bench_cg(P, torch, dev, A, C, batched=True, one_at_a_time=True):
+    """CG on 192^3 with b = A 1, x0 = 0, to a relative residual of 1e-10:
+    plain FP64 CG and FP64 iterative refinement around a binary32 inner
+    CG; optionally eight right-hand sides (b_j = A v_j, v_j ~ U[-1,1) seed
+    22) batched and one at a time."""
+    import spmv_inputs
     n = P.spmv_info(C)["n"]
     ones = torch.ones(n, dtype=torch.float64, device=dev)
     b = torch.empty_like(ones)
-    Ccol = P.spmv_compress(A, format="pattern", order="column")
-    P.spmv_apply(Ccol, ones, b)            # b = A 1 exactly (integer sums)
-    del Ccol
+    P.spmv_apply(A, ones, b)            # ELL, column order: integer sums, exact
     xx = torch.zeros_like(b)
-    P.spmv_autotune(C, ones, xx)
     res = {}
     for mode, extra in (("fp64", {}), ("ir_fp32", {"inner_max_iter": 200, "inner_tol": 1e-6})):
         xx.zero_()
         r = P.cg_solve(C, b, xx, tol=1e-10, mode=mode, max_iter=5000, **extra)
-        err = float((xx - 1.0).abs().max())
         res[mode] = {"seconds": r["seconds"], "iterations": r["iterations"], "outer": r["outer_iterations"],
-                     "rel_residual": r["rel_residual"], "max_abs_err_x_minus_1": err,
+                     "rel_residual": r["rel_residual"], "max_abs_err_x_minus_1": float((xx - 1.0).abs().max()),
                      "status": r["status"], "history_head": r["history"][:4], "history_tail": r["history"][-3:],
-                     **extra}
-    # eight right-hand sides in one batched solve (b_j = A v_j, v_j ~ U[-1,1) seed 22)
-    kb = 8
-    V = torch.from_numpy(spmv_inputs.uniform_matrix(n, kb, seed=22)).to(dev)
-    Bm = torch.empty_like(V)
-    Ccol2 = P.spmv_compress(A, format="pattern", order="column")
-    P.spmm_apply(Ccol2, V, Bm)
-    del Ccol2
-    Xm = torch.zeros_like(Bm)
-    r = P.cg_solve(C, Bm, Xm, tol=1e-10, max_iter=5000)
-    res["fp64_batched_8rhs"] = {"seconds": r["seconds"], "seconds_per_rhs": r["seconds"] / kb,
-                                "iterations": r["iterations"], "rel_residual": r["rel_residual"],
-                                "max_abs_err_x_minus_v": float((Xm - V).abs().max()), "status": r["status"]}
-    # the same eight right-hand sides solved one at a time
-    single_s, single_it = 0.0, []
-    for j in range(kb):
-        bj = Bm[:, j].contiguous()
-        xj = torch.zeros_like(bj)
-        rj = P.cg_solve(C, bj, xj, tol=1e-10, max_iter=5000)
-        single_s += rj["seconds"]
-        single_it.append(rj["iterations"])
-    res["fp64_same_8rhs_one_at_a_time"] = {"seconds": single_s, "seconds_per_rhs": single_s / kb,
-                                           "iterations": single_it}
-    emit({"workload": "cg_192^3_b_eq_A1_tol1e-10", "rows": n, "spmv_order": "fast", **res,
-          "ir_speedup": res["fp64"]["seconds"] / res["ir_fp32"]["seconds"],
-          "batched_speedup_per_rhs": single_s / r["seconds"]})
-    del A, C, b, xx, ones, V, Bm, Xm
+                     "history_len": len(r["history"]), **extra}
+    res["ir_speedup"] = res["fp64"]["seconds"] / res["ir_fp32"]["seconds"]
+    if batched:
+        kb = 8
+        V = torch.from_numpy(spmv_inputs.uniform_matrix(n, kb, seed=22)).to(dev)
+        Bm = torch.empty_like(V)
+        for j in range(kb):              # b_j = A v_j by the exact ELL product, column by column
+            vj = V[:, j].contiguous()
+            bj = torch.empty_like(vj)
+            P.spmv_apply(A, vj, bj)
+            Bm[:, j] = bj
+        Xm = torch.zeros_like(Bm)
+        r = P.cg_solve(C, Bm, Xm, tol=1e-10, max_iter=5000)
+        res["fp64_batched_8rhs"] = {"seconds": r["seconds"], "seconds_per_rhs": r["seconds"] / kb,
+                                    "iterations": r["iterations"], "rel_residual": r["rel_residual"],
+                                    "max_abs_err_x_minus_v": float((Xm - V).abs().max()), "status": r["status"]}
+        if one_at_a_time:
+            single_s, single_it = 0.0, []
+            for j in range(kb):
+                bj = Bm[:, j].contiguous()
+                xj = torch.zeros_like(bj)
+                rj = P.cg_solve(C, bj, xj, tol=1e-10, max_iter=5000)
+                single_s += rj["seconds"]
+                single_it.append(rj["iterations"])
+            res["fp64_same_8rhs_one_at_a_time"] = {"seconds": single_s, "seconds_per_rhs": single_s / kb,
+                                                   "iterations": single_it}
+            res["batched_speedup_per_rhs"] = single_s / r["seconds"]
+    return res
 
-    # --- SpMM on 160^3, k = 1, 4, 8, 16, 32 (X seed 3)
-    A = P.spmv_build("hpcg", 160, 160, 160)
+
+def bench_spmm(P, torch, dev, time_ms, ks=(1, 8, 32), iters=10, column=False, edge=160):
+    """SpMM Y = A X on the HPCG matrix of edge^3, X ~ U[-1,1) (seed 3),
+    FAST order (and COLUMN order when asked)."""
+    import spmv_inputs
+    A = P.spmv_build("hpcg", edge, edge, edge)
     Cf = P.spmv_compress(A, format="pattern", order="fast")
-    Cc = P.spmv_compress(A, format="pattern", order="column")
+    Cc = P.spmv_compress(A, format="pattern", order="column") if column else None
     n, nnz = P.spmv_info(Cf)["n"], P.spmv_info(Cf)["nnz"]
-    out = {}
-    for k in (1, 4, 8, 16, 32):
+    del A
+    out = {"rows": n, "nnz": nnz}
+    for k in ks:
         X = torch.from_numpy(spmv_inputs.uniform_matrix(n, k, seed=3)).to(dev)
         Y = torch.empty_like(X)
-        tf = time_ms(lambda: P.spmm_apply(Cf, X, Y), 20)
-        tc = time_ms(lambda: P.spmm_apply(Cc, X, Y), 5, warm=1)
-        out[f"k{k}"] = {"fast_gflops": 2 * nnz * k / tf / 1e6, "fast_ms": tf,
-                        "column_gflops": 2 * nnz * k / tc / 1e6, "column_ms": tc,
-                        "fast_gbs_alg": (nnz + n * 5 / 8 + 16 * n * k) / tf / 1e6}
+        tf = time_ms(lambda: P.spmm_apply(Cf, X, Y), iters)
+        alg = nnz + n * 5 / 8 + 16 * n * k
+        d = {"fast_gflops": 2 * nnz * k / tf / 1e6, "fast_ms": tf, "fast_gbs_alg": alg / tf / 1e6,
+             "alg_bytes_per_row": alg / n}
+        if Cc is not None:
+            tc = time_ms(lambda: P.spmm_apply(Cc, X, Y), max(2, iters // 4), warm=1)
+            d.update(column_gflops=2 * nnz * k / tc / 1e6, column_ms=tc)
+        out[f"k{k}"] = d
         del X, Y
-    emit({"workload": "spmm_160^3_X_seed3", "rows": n, "nnz": nnz, **out})
-    del A, Cf, Cc
+    return out
 
-    # --- ragged batch: 24 cubes, edges U{16..96} (seed 4), one graph launch
+
+def bench_ragged(P, torch, dev, time_ms, iters=30):
+    """24 HPCG cubes, edges U{16..96} (seed 4), one captured-graph launch
+    for the whole batch vs one launch per matrix."""
+    import spmv_inputs
     edges = spmv_inputs.grid_edges(24, seed=4)
     mats, xs, ys = [], [], []
     tot_nnz = 0
@@ -407,12 +395,67 @@ def run_suite(args):
         xs.append(torch.from_numpy(spmv_inputs.uniform_vector(e ** 3, seed=100 + bidx)).to(dev))
         ys.append(torch.empty_like(xs[-1]))
     plan = P.spmv_batch_create(mats, xs, ys)
-    tb = time_ms(lambda: P.spmv_batch_launch(plan), 50)
-    ts = time_ms(lambda: [P.spmv_apply(M, xv, yv) for M, xv, yv in zip(mats, xs, ys)], 20)
-    emit({"workload": "ragged_24_cubes_seed4", "edges": edges, "nnz": tot_nnz,
-          "batched_graph": {"ms": tb, "gflops": 2 * tot_nnz / tb / 1e6},
-          "one_launch_per_matrix": {"ms": ts, "gflops": 2 * tot_nnz / ts / 1e6},
-          "order": "column (bit-exact)"})
+    tb = time_ms(lambda: P.spmv_batch_launch(plan), iters)
+    ts = time_ms(lambda: [P.spmv_apply(M, xv, yv) for M, xv, yv in zip(mats, xs, ys)], max(3, iters // 3))
+    return {"edges": edges, "nnz": tot_nnz,
+            "batched_graph": {"ms": tb, "gflops": 2 * tot_nnz / tb / 1e6},
+            "one_launch_per_matrix": {"ms": ts, "gflops": 2 * tot_nnz / ts / 1e6},
+            "order": "column (bit-exact)"}
+
+
+def bench_row_types(P, torch, dev, A, x, time_ms, peaks, t_ell, iters=200):
+    """Values registered in the pattern (Sec. V): one byte a row."""
+    T = P.spmv_compress(A, format="pattern", order="fast")
+    n, nnz = P.spmv_info(T)["n"], P.spmv_info(T)["nnz"]
+    y = torch.empty_like(x)
+    best = None
+    for t, bt in ((1024, 256), (512, 256), (1024, 512)):
+        P.spmv_set_tile(T, 9, t, bt)
+        ms = time_ms(lambda: P.spmv_apply(T, x, y), iters)
+        if best is None or ms < best[0]:
+            best = (ms, t, bt)
+    it = P.spmv_info(T)
+    typed_bytes = n * 1 + 16 * n
+    return {"rows": n, "nnz": nnz, "row_types": it["row_types"], "gflops": 2 * nnz / best[0] / 1e6,
+            "ms": best[0], "tile_rows": best[1], "threads": best[2], "bytes_per_row": 1 + 16,
+            "gbs": typed_bytes / best[0] / 1e6, "frac_of_hbm": typed_bytes / best[0] / 1e6 / peaks["hbm_gbs"],
+            "speedup_vs_ell": t_ell / best[0], "order": "fast (<= 1e-14)"}
+
+
+def run_suite(args):
+    """The further workloads at full length, one JSON line each (irregular
+    128^3, Table II layouts and row types on 192^3, CG vs IR-CG and
+    batched CG on 192^3, SpMM k = 1..32 on 160^3, the ragged batch).  Not
+    the headline."""
+    import torch
+
+    import paper_1612_00530_gb300 as P
+    import spmv_inputs
+    from paper_1612_00530_gb300 import build as lib_build
+
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = measured_peaks()
+    time_ms = make_timer(torch)
+
+    def emit(name, d):
+        print(json.dumps({"workload": name, **d}), flush=True)
+
+    emit("irregular_128^3_seed2", bench_irregular(P, torch, dev, time_ms, peaks, iters=200))
+    A = P.spmv_build("hpcg", 192, 192, 192)
+    n = P.spmv_info(A)["n"]
+    x = torch.from_numpy(spmv_inputs.uniform_vector(n, seed=1)).to(dev)
+    t2 = bench_table2(P, torch, dev, A, x, time_ms, peaks)
+    emit("hpcg_192^3_table2_layouts", t2)
+    emit("hpcg_192^3_row_types", bench_row_types(P, torch, dev, A, x, time_ms, peaks, t2["original_ell"]["ms"]))
+    C = P.spmv_compress(A, format="pattern", order="fast")
+    y = torch.empty_like(x)
+    P.spmv_autotune(C, x, y)
+    emit("cg_192^3_b_eq_A1_tol1e-10", bench_cg(P, torch, dev, A, C))
+    del A, C, x, y
+    emit("spmm_160^3_X_seed3", bench_spmm(P, torch, dev, time_ms, ks=(1, 4, 8, 16, 32), iters=20, column=True))
+    emit("ragged_24_cubes_seed4", bench_ragged(P, torch, dev, time_ms, iters=50))
 
 
 def main():
@@ -423,6 +466,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", action="store_true", help="measure the further workloads instead of the headline")
+    ap.add_argument("--kernel", default=None, metavar="VARIANT:TILE",
+                    help="set the FAST kernel instead of running the autotuner (e.g. 11:1, the choice the "
+                         "autotuner makes in plain runs; under a profiler its timings are distorted)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave the further workloads' short measurements out of the headline line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world, rank, local = dist_setup()
@@ -456,7 +504,11 @@ def main():
     x = torch.from_numpy(x_np).to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    P.spmv_autotune(C, x, y)
+    if args.kernel:
+        kv, kt = (int(v) for v in args.kernel.split(":"))
+        P.spmv_set_tile(C, kv, kt, 0)
+    else:
+        P.spmv_autotune(C, x, y)
     info_c = P.spmv_info(C)
     variant = info_c["fast_variant"]
     tile, threads = info_c["fast_tile_rows"], info_c["fast_block_threads"]
@@ -591,6 +643,17 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "paper_context_gflops": {"pezy_sc_ell": 11.6, "pezy_sc_data_index_table": 32.4},
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        # the further workloads, short runs on this GPU (rank 0 of one)
+        t_ex = time.perf_counter()
+        time_ms = make_timer(torch, stream)
+        line["cg_192"] = bench_cg(P, torch, dev, A, C, batched=True, one_at_a_time=True)
+        line["table2_192"] = bench_table2(P, torch, dev, A, x, time_ms, peaks, iters=50)
+        del A, C
+        line["irregular_128"] = bench_irregular(P, torch, dev, time_ms, peaks, iters=50)
+        line["spmm_160"] = bench_spmm(P, torch, dev, time_ms, ks=(1, 8, 32), iters=10)
+        line["ragged_24"] = bench_ragged(P, torch, dev, time_ms, iters=20)
+        line["extras_seconds"] = time.perf_counter() - t_ex
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(y_check=y_fast)
     if rank == 0:

@@ -12,6 +12,9 @@ Parity status of each function (what pins it is in tests/test_oracle_pins.py):
   spmv / spmv_f32 / spmm              : pinned (integer-x exactness vs dense
       matmul, eigenpairs, brute force)
   value_table / data_table_row        : pinned (Fig. 2 worked example)
+  data_table_spmv                     : pinned (exact rational model of its
+      fma chain in value-group order on non-integer x, with planted slips;
+      integer-x equality with the CSR product; Fig. 2 row)
   data_index_table / listing1_spmv    : pinned (pattern census, integer-x
       equality with the CSR product, byte counts of Sec. V)
   kron_apply                          : pinned (dense Kronecker product)
@@ -55,6 +58,7 @@ def _load():
             "orc_spmm_csr": (None, [_i64, _i32, _p, _p, _p, _p, _p]),
             "orc_value_table": (_i64, [_i64, _p, _p]),
             "orc_data_table_row": (None, [_i32, _p, _p, _i32, _p, _p, _p, _p]),
+            "orc_data_table_spmv": (None, [_i64, _p, _p, _p, _i32, _p, _p, _p]),
             "orc_data_index_table": (_i64, [_i64, _p, _p, _p, _i32, _p, _i32, _i64, _p, _p, _p, _p]),
             "orc_listing1_spmv": (None, [_i64, _p, _p, _i32, _p, _i32, _p, _p, _p]),
             "orc_hpcg_kron_apply": (None, [_i32, _i32, _i32, _p, _p, _p]),
@@ -184,6 +188,17 @@ def data_table_row(col, val, V):
     Te = np.zeros(len(V), np.int32)
     _load().orc_data_table_row(len(col), _ptr(col), _ptr(val), len(V), _ptr(V), _ptr(S), _ptr(Ti), _ptr(Te))
     return S, Ti, Te
+
+
+def data_table_spmv(rowptr, col, val, V, x) -> np.ndarray:
+    """y = A x from each row's (S_i, T_i) over the value table V (Sec. V,
+    "Data Table"): value groups ascending, one fma per entry."""
+    rowptr, col, val = _c(rowptr, np.int64), _c(col, np.int32), _c(val, np.float64)
+    V, x = _c(V, np.float64), _c(x, np.float64)
+    n = len(rowptr) - 1
+    y = np.zeros(n, np.float64)
+    _load().orc_data_table_spmv(n, _ptr(rowptr), _ptr(col), _ptr(val), len(V), _ptr(V), _ptr(x), _ptr(y))
+    return y
 
 
 def data_index_table(rowptr, col, val, V, maxlen: int = 27, maxtypes: int = 4096):

@@ -364,6 +364,39 @@ void orc_data_table_row(int len, const int32_t *col, const double *val, int nV, 
     }
 }
 
+/* Sec. V, first scheme ("Data Table" of Table II): each row kept as its
+ * value-sorted column list S_i and terminal indices T_i over the value
+ * table V.  y_i walks the value groups in ascending order and, inside a
+ * group, S_i in order; each entry adds V[v] * x[S_i[idx]] with one fma. */
+void orc_data_table_spmv(int64_t n, const int64_t *rowptr, const int32_t *col, const double *val,
+                         int nV, const double *V, const double *x, double *y)
+{
+    int maxlen = 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] - rowptr[i] > maxlen)
+            maxlen = (int)(rowptr[i + 1] - rowptr[i]);
+    int32_t *S = malloc(sizeof(int32_t) * maxlen);
+    int32_t *Ti = malloc(sizeof(int32_t) * (nV > 0 ? nV : 1));
+    int32_t *Te = malloc(sizeof(int32_t) * (nV > 0 ? nV : 1));
+    if (!S || !Ti || !Te) {
+        free(S); free(Ti); free(Te);
+        return;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int len = (int)(rowptr[i + 1] - rowptr[i]);
+        orc_data_table_row(len, col + rowptr[i], val + rowptr[i], nV, V, S, Ti, Te);
+        double s = 0.0;
+        int idx = 0;
+        for (int v = 0; v < nV; ++v)
+            for (; idx < Te[v]; ++idx)
+                s = fma(V[v], x[S[idx]], s);
+        y[i] = s;
+    }
+    free(S);
+    free(Ti);
+    free(Te);
+}
+
 /* Sec. V, second scheme: within each row the value-sorted column list S_i
  * is made relative to the diagonal (S_i - i) and the displacement list is
  * registered in a table of patterns; the row keeps only its pattern number

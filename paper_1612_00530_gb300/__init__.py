@@ -350,8 +350,9 @@ def spmv_set_variant(A: SpmvMatrix, variant: int, tile_rows: int = 0) -> None:
 def spmv_set_tile(A: SpmvMatrix, variant: int, tile_rows: int, block_threads: int) -> None:
     """spmv_set_variant with the staged kernel's block size (512, or 256 on
     the full 27-slot union); variant 10, the z-block kernel, takes 256 with
-    tile_rows = 512 x planes (1536 or 2048); variant 11 ignores both (its
-    block is whole grid lines, four rows a thread)."""
+    tile_rows = 512 x planes (1536 or 2048); variant 11 takes tile_rows 1 or 2
+    (grid lines a thread's 4-column tile spans; 0 keeps the current one) and
+    ignores block_threads (its block is whole grid lines)."""
     _check(library().spmv_set_tile(A, variant, tile_rows, block_threads))
 
 

@@ -287,6 +287,68 @@ def test_fig2_worked_example():
     assert np.array_equal(T_end, T_incl + 1)
 
 
+def exact_data_table_spmv(rowptr, col, val, x):
+    """Each row: entries ordered by value (ascending), ties by ascending
+    column; s = 0; s = RN64(a * x_j + s) per entry, every step evaluated
+    exactly in rationals and rounded once to binary64 (Python's float of a
+    Fraction rounds correctly), which is what an fma chain computes."""
+    from fractions import Fraction
+    xs = [Fraction(float(v)) for v in x.tolist()]
+    out = np.empty(len(rowptr) - 1, np.float64)
+    for i in range(len(rowptr) - 1):
+        ks = sorted(range(rowptr[i], rowptr[i + 1]), key=lambda k: (val[k], col[k]))
+        s = Fraction(0)
+        for k in ks:
+            s = Fraction(float(Fraction(float(val[k])) * xs[col[k]] + s))
+        out[i] = float(s)
+    return out
+
+
+@pytest.mark.parametrize("which", ["hpcg", "irregular"])
+def test_data_table_spmv_is_the_value_group_fma_chain(which):
+    """Non-integer x: the Data Table product equals the exact model of an
+    fma chain in value-group order bit for bit; two plausible slips (the
+    column-order chain, separate multiply and add) both differ from it."""
+    if which == "hpcg":
+        rowptr, col, val = oracle.hpcg_csr(5, 4, 6)
+    else:
+        # no unique-valued rows: the table holds the 16 levels and the diagonals
+        rowptr, col, val, _ = oracle.irregular_csr(6, 5, 4, seed=2, special_frac=0.0, diag_rule=1)
+    n = len(rowptr) - 1
+    x = spmv_inputs.uniform_vector(n, seed=13)
+    V = oracle.value_table(val)
+    want = exact_data_table_spmv(rowptr, col, val, x)
+    got = oracle.data_table_spmv(rowptr, col, val, V, x)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    slip_col = oracle.spmv(rowptr, col, val, x)                 # ascending columns
+    assert not np.array_equal(slip_col, want)
+    slip_sep = np.empty(n)
+    for i in range(n):
+        s = 0.0
+        for k in sorted(range(rowptr[i], rowptr[i + 1]), key=lambda k: (val[k], col[k])):
+            s = float(np.float64(val[k]) * np.float64(x[col[k]])) + s
+        slip_sep[i] = s
+    assert not np.array_equal(slip_sep, want)
+
+
+def test_data_table_spmv_integer_x_and_fig2_row():
+    # integer x: every partial sum is exact, so any order gives the CSR product
+    rowptr, col, val = oracle.hpcg_csr(6, 7, 5)
+    n = len(rowptr) - 1
+    x = np.random.default_rng(4).integers(-50, 50, n).astype(np.float64)
+    V = oracle.value_table(val)
+    assert np.array_equal(oracle.data_table_spmv(rowptr, col, val, V, x), oracle.spmv(rowptr, col, val, x))
+    ones = np.ones(n)
+    assert np.array_equal(oracle.data_table_spmv(rowptr, col, val, V, ones), 27.0 - np.diff(rowptr))
+    # the Fig. 2 row as a one-row matrix over 66 columns, x_j = j
+    g = read_golden("fig2_worked_example.txt")
+    fcol = np.array(g["columns"], dtype=np.int32)
+    fval = np.array(g["values"], dtype=np.float64)
+    xj = np.arange(66, dtype=np.float64)
+    y = oracle.data_table_spmv(np.array([0, len(fcol)]), fcol, fval, oracle.value_table(fval), xj)
+    assert y[0] == -(45 + 49 + 51 + 65) + 26 * 50
+
+
 def test_value_table_of_hpcg():
     _, _, val = oracle.hpcg_csr(7, 7, 7)
     assert np.array_equal(oracle.value_table(val), np.array([-1.0, 26.0]))
