@@ -289,23 +289,31 @@ def bench_irregular(P, torch, dev, time_ms, peaks, iters=100):
 
 
 def bench_table2(P, torch, dev, A, x, time_ms, peaks, iters=100):
-    """Table II's layouts on 192^3: plain ELL ("Original"), the Data+Index
-    Table decoded in Listing 1's order (bit-exact), beside the headline
-    pattern format."""
+    """Table II's three layouts on 192^3: plain ELL ("Original"), the Data
+    Table (value-sorted columns S_i + terminal indices T_i) and the
+    Data+Index Table, both decoded in Listing 1's order (bit-exact)."""
     D = P.spmv_compress(A, format="dit")
-    idt = P.spmv_info(D)
+    T = P.spmv_compress(A, format="data_table")
+    idt, itb = P.spmv_info(D), P.spmv_info(T)
     n, nnz = idt["n"], idt["nnz"]
     y = torch.empty_like(x)
     t_ell = time_ms(lambda: P.spmv_apply(A, x, y), iters)
+    t_dt = time_ms(lambda: P.spmv_apply(T, x, y), iters)
     t_dit = time_ms(lambda: P.spmv_apply(D, x, y), iters)
-    dit_bytes = idt["format_bytes"] + 16 * n
+
+    def row(ms, fbytes, **kw):
+        b = fbytes + 16 * n
+        return {"gflops": 2 * nnz / ms / 1e6, "ms": ms, "bytes_per_row": fbytes / n, "gbs": b / ms / 1e6,
+                "frac_of_hbm": b / ms / 1e6 / peaks["hbm_gbs"], **kw}
     return {"rows": n, "nnz": nnz,
-            "original_ell": {"gflops": 2 * nnz / t_ell / 1e6, "ms": t_ell, "bytes_per_row": 12 * nnz / n},
-            "data_index_table": {"gflops": 2 * nnz / t_dit / 1e6, "ms": t_dit, "types": idt["n_patterns"],
-                                 "bytes_per_row": idt["record_bytes"], "paper_bytes_per_row": 12,
-                                 "gbs": dit_bytes / t_dit / 1e6,
-                                 "frac_of_hbm": dit_bytes / t_dit / 1e6 / peaks["hbm_gbs"]},
-            "speedup_vs_ell": t_ell / t_dit, "order": "Listing 1 (value groups ascending; bit-exact)"}
+            "original_ell": row(t_ell, 12 * nnz, paper_bytes_per_row=324),
+            "data_table": row(t_dt, itb["format_bytes"], paper_bytes_per_row=116),
+            "data_index_table": row(t_dit, idt["format_bytes"], types=idt["n_patterns"], paper_bytes_per_row=12),
+            "speedup_vs_ell": {"data_table": t_ell / t_dt, "data_index_table": t_ell / t_dit},
+            "paper_gflops_pezy_sc": {"original_ell": 11.6, "data_table": 15.9, "data_index_table": 32.4},
+            "order": "Listing 1 (value groups ascending, one fma per entry; bit-exact)",
+            "fp64_pipe_bound_ms": nnz / (FP64_FMA_PER_SM_CLK * torch.cuda.get_device_properties(dev).multi_processor_count
+                                         * 2.07e9) * 1e3}
 
 
 def bench_cg(P, torch, dev, A, C, batched=True, one_at_a_time=True):

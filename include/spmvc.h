@@ -67,12 +67,22 @@ typedef void *spmv_stream_t;
 #define SPMV_FMT_DIT 4         /* Sec. V "Data+Index Table": per row a type (a
                                   registered value-grouped displacement list)
                                   and its value-group ends; Listing 1 decode */
+#define SPMV_FMT_DATA_TABLE 5  /* Sec. V "Data Table" (Fig. 2): per row its
+                                  columns sorted by value, S_i (int32, columns
+                                  ascending inside a value; 32-row slices,
+                                  slot-major), and the exclusive end of each
+                                  value group, T_i + 1 (uint8, value-major);
+                                  4 B a nonzero + 1 B a value a row, where the
+                                  paper counts (27 + 2) * 4 = 116 B a row.
+                                  Decoded like Listing 1: value groups
+                                  ascending, one fma per entry.  At most 255
+                                  distinct values and 255 entries a row. */
 
 #define SPMV_ORDER_COLUMN 0    /* y_i = fma chain over ascending columns from 0:
                                   bit-identical to the plain CSR product (the
-                                  Data+Index Table format: Listing 1's chain,
-                                  value groups ascending, columns ascending
-                                  inside a group) */
+                                  Data+Index Table and Data Table formats:
+                                  Listing 1's chain, value groups ascending,
+                                  columns ascending inside a group) */
 #define SPMV_ORDER_FAST 1      /* pattern format only: exact fixed-point sums,
                                   one rounding per row (error bound below) */
 
@@ -128,7 +138,9 @@ int spmv_build_csr(int64_t n, const int64_t *rowptr, const int32_t *col,
 /* ---- compression (Sec. V) -------------------------------------------- */
 typedef struct {
     int32_t format;        /* SPMV_FMT_AUTO, SPMV_FMT_PATTERN, SPMV_FMT_DELTA or
-                              SPMV_FMT_DIT (never chosen by AUTO) */
+                              SPMV_FMT_DIT or SPMV_FMT_DATA_TABLE (neither
+                              chosen by AUTO; no stream form, no binary32
+                              product, no SpMM, COLUMN order only) */
     int32_t order;         /* SPMV_ORDER_COLUMN or SPMV_ORDER_FAST */
     int32_t max_dict;      /* largest value table, 1..254 (default 254 when 0) */
     int32_t min_count;     /* delta format: a value enters the table only if it

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libspmvc.so")
 
 SPMV_OK, SPMV_EINVAL, SPMV_ENOMEM, SPMV_ECUDA, SPMV_ECORRUPT = 0, 1, 2, 3, 4
 SPMV_EUNSUPPORTED, SPMV_ENOTCONVERGED, SPMV_ETIMEOUT, SPMV_EDEVICE = 5, 6, 7, 8
-FORMATS = {"auto": 0, "ell": 1, "pattern": 2, "delta": 3, "dit": 4}
+FORMATS = {"auto": 0, "ell": 1, "pattern": 2, "delta": 3, "dit": 4, "data_table": 5}
 FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
 ORDERS = {"column": 0, "fast": 1}
 CG_MODES = {"fp64": 0, "ir_fp32": 1}

@@ -18,6 +18,7 @@ int decompress_ell(int64_t n, const EllFormat& e, Csr* out);
 int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out);
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out);
 int decompress_dit(int64_t n, const DitFormat& d, Csr* out);
+int decompress_data_table(int64_t n, const DataTableFormat& d, Csr* out);
 uint64_t checksum_of(const spmv_mat_s& m);
 int export_stream(const spmv_mat_s& m, void* buf, size_t* len);
 int import_stream(const void* buf, size_t len, spmv_mat_s* m);
@@ -323,6 +324,27 @@ int ensure_device(spmv_mat_s* m) {
             m->fast_variant = 1;
         if ((m->fast_variant == 1 || m->fast_variant == 3) && !m->stage_ok) m->fast_variant = m->d_xfixed ? 2 : 0;
         if (m->fast_variant == 0 && m->stage_ok) m->fast_variant = 1;
+    } else if (m->fmt == SPMV_FMT_DATA_TABLE) {
+        const DataTableFormat& d = m->dt;
+        DataTableView& v = m->dt_view;
+        v.n = m->n;
+        v.nslices = d.nslices;
+        v.nv = static_cast<int32_t>(d.dict.size());
+        int64_t* so;
+        uint8_t *sw, *en;
+        int32_t* S;
+        double* dd;
+        if ((st = dev_copy(m, d.slice_off.data(), d.slice_off.size(), &so))) return st;
+        if ((st = dev_copy(m, d.slice_w.data(), d.slice_w.size(), &sw))) return st;
+        if ((st = dev_copy(m, d.S.data(), d.S.size(), &S))) return st;
+        if ((st = dev_copy(m, d.ends.data(), d.ends.size(), &en))) return st;
+        if ((st = dev_copy(m, d.dict.data(), d.dict.size(), &dd))) return st;
+        v.slice_off = so;
+        v.slice_w = sw;
+        v.S = S;
+        v.ends = en;
+        v.dict = dd;
+        v.err = m->d_err;
     } else if (m->fmt == SPMV_FMT_DIT) {
         const DitFormat& d = m->dit;
         DitView& v = m->dit_view;
@@ -408,6 +430,7 @@ int stored_csr(spmv_mat_s* a, Csr* c) {
     if (a->fmt == SPMV_FMT_ELL) return decompress_ell(a->n, a->ell, c);
     if (a->fmt == SPMV_FMT_PATTERN) return decompress_pattern(a->n, a->pat, c);
     if (a->fmt == SPMV_FMT_DIT) return decompress_dit(a->n, a->dit, c);
+    if (a->fmt == SPMV_FMT_DATA_TABLE) return decompress_data_table(a->n, a->dt, c);
     return decompress_delta(a->n, a->dlt, c);
 }
 
@@ -453,6 +476,7 @@ int apply_stored(spmv_mat_s* A, const double* x, double* y, cudaStream_t s) {
             : A->fast_variant == 1 ? launch_pattern_fast_staged(A->pat_view, A->stage, x, y, s)
                                    : launch_pattern_fast_f64(A->pat_view, x, y, A->d_scratch_words, s);
     else if (A->fmt == SPMV_FMT_DIT) e = launch_dit_f64(A->dit_view, x, y, s);
+    else if (A->fmt == SPMV_FMT_DATA_TABLE) e = launch_data_table_f64(A->dt_view, x, y, s);
     else e = launch_delta_f64(A->dlt_view, x, y, s);
     if (e != cudaSuccess) return cuda_fail(e, "spmv launch");
     return SPMV_OK;
@@ -499,8 +523,8 @@ int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
     if (o.min_count <= 0) o.min_count = 64;
     if (o.max_dict > 254) return fail(SPMV_EINVAL, "max_dict above 254");
     if (o.format != SPMV_FMT_AUTO && o.format != SPMV_FMT_PATTERN && o.format != SPMV_FMT_DELTA &&
-        o.format != SPMV_FMT_DIT)
-        return fail(SPMV_EINVAL, "compress format must be AUTO, PATTERN, DELTA or DIT");
+        o.format != SPMV_FMT_DIT && o.format != SPMV_FMT_DATA_TABLE)
+        return fail(SPMV_EINVAL, "compress format must be AUTO, PATTERN, DELTA, DIT or DATA_TABLE");
     Csr c;
     int st = to_csr(A, &c);
     if (st) return st;
@@ -523,6 +547,10 @@ int spmv_compress(spmv_mat_t A, const spmv_opts* opts, spmv_mat_t* out) {
         st = compress_dit(c, &m->dit);
         if (st) { delete m; return st; }
         m->fmt = SPMV_FMT_DIT;
+    } else if (o.format == SPMV_FMT_DATA_TABLE) {
+        st = compress_data_table(c, &m->dt);
+        if (st) { delete m; return st; }
+        m->fmt = SPMV_FMT_DATA_TABLE;
     } else if (o.format == SPMV_FMT_AUTO || o.format == SPMV_FMT_PATTERN) {
         st = compress_pattern(c, o.max_dict, &m->pat);
         if (st == SPMV_OK) m->fmt = SPMV_FMT_PATTERN;
@@ -589,6 +617,14 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         out->format_bytes = A->n * 4 * A->pat.words;
         out->padding_bytes = out->format_bytes - A->nnz - A->n;
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->pat.dict.size() * 12);
+    } else if (A->fmt == SPMV_FMT_DATA_TABLE) {
+        out->dict_size = static_cast<int32_t>(A->dt.dict.size());
+        out->n_slices = A->dt.nslices;
+        out->format_bytes = static_cast<int64_t>(A->dt.S.size() * 4 + A->dt.ends.size());
+        out->record_bytes = A->n ? static_cast<int32_t>((out->format_bytes + A->n - 1) / A->n) : 0;
+        out->padding_bytes = static_cast<int64_t>(A->dt.S.size() - A->nnz) * 4;
+        out->device_bytes = out->format_bytes +
+                            static_cast<int64_t>(A->dt.slice_off.size() * 8 + A->dt.slice_w.size() + A->dt.dict.size() * 8);
     } else if (A->fmt == SPMV_FMT_DIT) {
         out->dict_size = static_cast<int32_t>(A->dit.dict.size());
         out->n_patterns = static_cast<int32_t>(A->dit.tlen.size());
@@ -787,6 +823,7 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
 int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no binary32 product for the Data+Index Table format");
+    if (A->fmt == SPMV_FMT_DATA_TABLE) return fail(SPMV_EUNSUPPORTED, "no binary32 product for the Data Table format");
     if (!A->perm.empty()) return fail(SPMV_EUNSUPPORTED, "no binary32 product for a reordered handle");
     if (A->n > 0 && (!x || !y)) return fail(SPMV_EINVAL, "null vector");
     int st = ensure_device(A);
@@ -815,6 +852,7 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y,
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (k < 1 || k > 64 || ldx < k || ldy < k) return fail(SPMV_EINVAL, "need 1 <= k <= 64, ldx >= k, ldy >= k");
     if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no SpMM for the Data+Index Table format");
+    if (A->fmt == SPMV_FMT_DATA_TABLE) return fail(SPMV_EUNSUPPORTED, "no SpMM for the Data Table format");
     if (!A->perm.empty()) return fail(SPMV_EUNSUPPORTED, "no SpMM for a reordered handle");
     if (A->n > 0 && (!X || !Y)) return fail(SPMV_EINVAL, "null block");
     int st = ensure_device(A);

@@ -14,6 +14,7 @@ int decompress_ell(int64_t n, const EllFormat& e, Csr* out);
 int decompress_pattern(int64_t n, const PatternFormat& p, Csr* out);
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out);
 int decompress_dit(int64_t n, const DitFormat& d, Csr* out);
+int decompress_data_table(int64_t n, const DataTableFormat& d, Csr* out);
 uint64_t checksum_of(const spmv_mat_s& m);
 int export_stream(const spmv_mat_s& m, void* buf, size_t* len);
 int import_stream(const void* buf, size_t len, spmv_mat_s* m);
@@ -148,6 +149,46 @@ int decompress_dit(int64_t n, const DitFormat& d, Csr* out) {
     return finish_csr(out);
 }
 
+// Data Table -> CSR: walk each row's value groups over S_i, then put the
+// entries back in column order.  Every index is checked.
+int decompress_data_table(int64_t n, const DataTableFormat& d, Csr* out) {
+    const int nv = static_cast<int>(d.dict.size());
+    const int64_t ns = (n + kSliceRows - 1) / kSliceRows;
+    if (d.nslices != ns || static_cast<int64_t>(d.slice_w.size()) != ns ||
+        static_cast<int64_t>(d.slice_off.size()) != ns + 1 || static_cast<int64_t>(d.ends.size()) != n * nv ||
+        d.slice_off[0] != 0)
+        return corrupt("Data Table sizes");
+    for (int64_t s = 0; s < ns; ++s)
+        if (d.slice_off[s + 1] - d.slice_off[s] != int64_t(d.slice_w[s]) * kSliceRows) return corrupt("Data Table slices");
+    if (d.slice_off[ns] != static_cast<int64_t>(d.S.size())) return corrupt("Data Table column list size");
+    out->n = n;
+    out->rowptr.assign(static_cast<size_t>(n) + 1, 0);
+    out->col.clear();
+    out->val.clear();
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t s = r / kSliceRows, l = r % kSliceRows;
+        row.clear();
+        int idx = 0;
+        for (int v = 0; v < nv; ++v) {
+            const int end = d.ends[static_cast<size_t>(v) * n + r];
+            if (end < idx || end > d.slice_w[s]) return corrupt("value group end");
+            for (; idx < end; ++idx) {
+                const int64_t c = d.S[d.slice_off[s] + int64_t(idx) * kSliceRows + l];
+                if (c < 0 || c >= n) return corrupt("column outside the matrix");
+                row.emplace_back(static_cast<int32_t>(c), d.dict[v]);
+            }
+        }
+        std::sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (const auto& e : row) {
+            out->col.push_back(e.first);
+            out->val.push_back(e.second);
+        }
+        out->rowptr[r + 1] = static_cast<int64_t>(out->col.size());
+    }
+    return finish_csr(out);
+}
+
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out) {
     if (d.nslices != (n + kSliceRows - 1) / kSliceRows || (int64_t)d.hdr.size() != d.nslices || d.dict.size() > 255)
         return corrupt("delta slice table size");
@@ -215,6 +256,12 @@ uint64_t checksum_of(const spmv_mat_s& m) {
         f.vec(m.pat.pmask);
         f.pod(m.pat.words);
         f.vec(m.pat.rec);
+    } else if (m.fmt == SPMV_FMT_DATA_TABLE) {
+        f.vec(m.dt.dict);
+        f.vec(m.dt.slice_off);
+        f.vec(m.dt.slice_w);
+        f.vec(m.dt.S);
+        f.vec(m.dt.ends);
     } else if (m.fmt == SPMV_FMT_DIT) {
         f.vec(m.dit.dict);
         f.pod(m.dit.maxlen);
@@ -272,6 +319,7 @@ const char kTag[8] = {'S', 'P', 'M', 'V', 'C', 0, 'v', '1'};
 
 int export_stream(const spmv_mat_s& m, void* buf, size_t* len) {
     if (m.fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "the Data+Index Table format has no stream form");
+    if (m.fmt == SPMV_FMT_DATA_TABLE) return fail(SPMV_EUNSUPPORTED, "the Data Table format has no stream form");
     Writer w{static_cast<uint8_t*>(buf), 0, buf ? *len : 0, buf == nullptr};
     w.put(kTag, 8);
     w.pod(m.fmt);

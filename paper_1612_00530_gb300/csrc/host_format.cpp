@@ -333,6 +333,62 @@ int compress_dit(const Csr& a, DitFormat* out) {
     return SPMV_OK;
 }
 
+// ------------------------------------------------------------ Data Table ---
+// Sec. V, first scheme: per row the columns in value order (S_i) and the end
+// of every value group, rows packed in 32-row slices for coalesced reads.
+int compress_data_table(const Csr& a, DataTableFormat* out) {
+    const int64_t n = a.n;
+    BitsTable counts;
+    int st = value_table(a.val, 255, &out->dict, &counts, "Data Table: more than 255 distinct values");
+    if (st) return st;
+    const int nv = static_cast<int>(out->dict.size());
+    const BitsTable code = code_table(out->dict);
+    const int64_t ns = (n + kSliceRows - 1) / kSliceRows;
+    out->nslices = ns;
+    out->slice_w.assign(ns, 0);
+    out->slice_off.assign(ns + 1, 0);
+    std::atomic<bool> too_long{false};
+    parallel_ranges(ns, 4096, [&](int64_t s0, int64_t s1, int) {
+        for (int64_t s = s0; s < s1; ++s) {
+            int64_t w = 0;
+            for (int64_t r = s * kSliceRows; r < std::min(n, (s + 1) * kSliceRows); ++r)
+                w = std::max<int64_t>(w, a.rowptr[r + 1] - a.rowptr[r]);
+            if (w > 255) too_long = true;
+            out->slice_w[s] = static_cast<uint8_t>(std::min<int64_t>(w, 255));
+        }
+    });
+    if (too_long) return fail(SPMV_EUNSUPPORTED, "Data Table: a row holds more than 255 entries");
+    for (int64_t s = 0; s < ns; ++s) out->slice_off[s + 1] = out->slice_off[s] + int64_t(out->slice_w[s]) * kSliceRows;
+    out->S.resize(out->slice_off.back());
+    out->ends.resize(static_cast<size_t>(n) * nv);
+    parallel_ranges(ns, 4096, [&](int64_t s0, int64_t s1, int) {
+        for (int64_t s = s0; s < s1; ++s) {
+            const int64_t w = out->slice_w[s], base = out->slice_off[s];
+            for (int64_t l = 0; l < kSliceRows; ++l) {
+                const int64_t r = s * kSliceRows + l;
+                int64_t len = 0;
+                if (r < n) {
+                    // a stable counting sort of the row's entries by value code
+                    const int64_t k0 = a.rowptr[r];
+                    len = a.rowptr[r + 1] - k0;
+                    uint8_t c[255];
+                    int32_t pos[257];
+                    std::fill(pos, pos + nv + 1, 0);
+                    for (int64_t i = 0; i < len; ++i) {
+                        c[i] = static_cast<uint8_t>(code.get(value_bits(a.val[k0 + i]), 0));
+                        ++pos[c[i] + 1];
+                    }
+                    for (int v = 0; v < nv; ++v) pos[v + 1] += pos[v];
+                    for (int64_t i = 0; i < len; ++i) out->S[base + int64_t(pos[c[i]]++) * kSliceRows + l] = a.col[k0 + i];
+                    for (int v = 0; v < nv; ++v) out->ends[static_cast<size_t>(v) * n + r] = static_cast<uint8_t>(pos[v]);
+                }
+                for (int64_t t = len; t < w; ++t) out->S[base + t * kSliceRows + l] = -1;
+            }
+        }
+    });
+    return SPMV_OK;
+}
+
 // ---------------------------------------------------------------- delta ---
 // The delta format's value table: the most frequent values with at least
 // min_count uses, at most max_dict of them, in ascending order.

@@ -2054,6 +2054,51 @@ __global__ void __launch_bounds__(kBlock) dit_kernel(DitView a, const double* __
     y[r] = acc;
 }
 
+// ------------------------------------------------------- Data Table ------
+// Sec. V's first scheme on the GPU, one thread per row, a warp per 32-row
+// slice: slot t of the slice's rows is one coalesced 128-byte read of S.  The
+// value groups are walked in ascending order with one fma per entry, so the
+// result is bit-identical to the oracle's Data Table chain.  A column outside
+// [0, n) or a group end past the slice width can only come from a corrupt
+// table: it sets the matrix's error word and the entry is skipped.
+__global__ void __launch_bounds__(kBlock) data_table_kernel(DataTableView a, const double* __restrict__ x,
+                                                           double* __restrict__ y) {
+    __shared__ double sdict[256];
+    for (int i = threadIdx.x; i < a.nv; i += blockDim.x) sdict[i] = __ldg(a.dict + i);
+    __syncthreads();
+    const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (r >= a.n) return;
+    const int64_t sl = r >> 5;
+    const int w = __ldg(a.slice_w + sl);
+    const int32_t* S = a.S + __ldg(a.slice_off + sl) + (r & 31);
+    int idx = 0;
+    double acc = 0.0;
+    for (int v = 0; v < a.nv; ++v) {
+        const double av = sdict[v];
+        int end = __ldg(a.ends + int64_t(v) * a.n + r);
+        if (end > w) {
+            atomicOr(a.err, 1);
+            end = w;
+        }
+        for (; idx < end; ++idx) {
+            const int32_t j = __ldg(S + idx * 32);
+            if (uint32_t(j) >= uint64_t(a.n)) {
+                atomicOr(a.err, 1);
+                continue;
+            }
+            acc = fma(av, __ldg(x + j), acc);
+        }
+    }
+    y[r] = acc;
+}
+
+cudaError_t launch_data_table_f64(const DataTableView& a, const double* x, double* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (a.nv > 256) return cudaErrorInvalidValue;
+    data_table_kernel<<<grid_of(a.n), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.nv > 256) return cudaErrorInvalidValue;

@@ -119,6 +119,22 @@ struct DitFormat {
 };
 int compress_dit(const Csr& a, DitFormat* out);
 
+// The "Data Table" of Sec. V (Fig. 2): the value table V; for every row its
+// columns sorted by value, S_i (ties in ascending column order), and the
+// exclusive end of each value group in S_i (T_i + 1; T_i is the last
+// position of the group).  Rows in 32-row slices, S as int32 slot-major
+// [w][32] per slice (w its longest row, padding -1), ends uint8 value-major
+// [nv][n]; rows of at most 255 entries, at most 255 values.
+struct DataTableFormat {
+    std::vector<double> dict;
+    int64_t nslices = 0;
+    std::vector<int64_t> slice_off;   // nslices + 1, in S entries
+    std::vector<uint8_t> slice_w;     // slots a row of the slice
+    std::vector<int32_t> S;
+    std::vector<uint8_t> ends;        // nv x n
+};
+int compress_data_table(const Csr& a, DataTableFormat* out);
+
 // --------------------------------------------------------- device views --
 struct EllView {
     int64_t n, nslices;
@@ -169,6 +185,17 @@ struct DitView {
     const uint8_t* type;
     const uint8_t* ends;            // nv x n
     const int32_t* disp;            // ntypes x maxlen
+    const double* dict;
+    int32_t* err;
+};
+
+struct DataTableView {
+    int64_t n, nslices;
+    int32_t nv;
+    const int64_t* slice_off;
+    const uint8_t* slice_w;
+    const int32_t* S;
+    const uint8_t* ends;            // nv x n
     const double* dict;
     int32_t* err;
 };
@@ -313,6 +340,7 @@ cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double*
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_data_table_f64(const DataTableView& a, const double* x, double* y, cudaStream_t s);
 // k_check.cu: *out = max |x_j| as bits (atomicMax; *out zeroed by the
 // caller); *bad += count of i with |y_i - yref_i| > abs_tol + rel_tol |yref_i|
 // (non-finite entries must match)
@@ -370,6 +398,7 @@ struct spmv_mat_s {
     spmvc::PatternFormat pat;
     spmvc::DeltaFormat dlt;
     spmvc::DitFormat dit;
+    spmvc::DataTableFormat dt;
     uint64_t checksum = 0;
 
     // device side (allocated on first use)
@@ -379,6 +408,7 @@ struct spmv_mat_s {
     spmvc::PatternView pat_view{};
     spmvc::DeltaView dlt_view{};
     spmvc::DitView dit_view{};
+    spmvc::DataTableView dt_view{};
     int32_t* d_err = nullptr;
     spmvc::StagePlan stage{};          // FAST order: shared-memory staging plan
     bool stage_ok = false;

@@ -824,6 +824,84 @@ def test_data_index_table_cg():
     assert float((x - 1).abs().max()) < 1e-8
 
 
+def data_table_reference(rowptr, col, val, x):
+    return oracle.data_table_spmv(rowptr, col, val, oracle.value_table(val), x)
+
+
+@pytest.mark.parametrize("g", [(1, 1, 1), (2, 3, 5), (4, 4, 4), (17, 17, 17), (33, 9, 5), (40, 36, 12)])
+def test_data_table_bit_exact(g):
+    """Sec. V's Data Table decoded in value-group order (fma per entry):
+    bit-identical to the oracle's Data Table chain, within 1e-14 of the CSR
+    product, exact for integer x; ragged last slices included."""
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    D = P.spmv_compress(P.spmv_build("hpcg", *g), format="data_table")
+    x = spmv_inputs.uniform_vector(n, seed=34)
+    y = run(D, x)
+    assert np.array_equal(y.view(np.uint64), data_table_reference(rowptr, col, val, x).view(np.uint64))
+    check_fast(y, oracle.spmv(rowptr, col, val, x), abs_row_sums(rowptr, col, val, x))
+    xi = spmv_inputs.integer_vector(n, seed=35)
+    assert np.array_equal(run(D, xi), oracle.spmv(rowptr, col, val, xi))
+    assert P.spmv_device_error(D) == 0
+
+
+def test_data_table_several_values_irregular_reordered_and_cg():
+    """Four values (weighted stencil) and seventeen (irregular, permuted
+    numbering, then reordered): bit-identical to the oracle's chain; host
+    buffers; FP64 CG through the handle; no binary32 product or SpMM."""
+    g = (32, 64, 6)
+    rowptr, col, val = weighted_27_point_csr(g)
+    n = len(rowptr) - 1
+    D = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="data_table")
+    x = spmv_inputs.uniform_vector(n, seed=36)
+    y = run(D, x)
+    assert np.array_equal(y.view(np.uint64), data_table_reference(rowptr, col, val, x).view(np.uint64))
+    yh = np.zeros(n)
+    P.spmv_apply_host(D, np.ascontiguousarray(x), yh)
+    assert np.array_equal(yh, y)
+    for call in (lambda: P.spmv_apply_f32(D, torch.zeros(n, dtype=torch.float32, device="cuda"),
+                                          torch.zeros(n, dtype=torch.float32, device="cuda")),
+                 lambda: P.spmm_apply(D, torch.zeros(n, 2, dtype=torch.float64, device="cuda"),
+                                      torch.zeros(n, 2, dtype=torch.float64, device="cuda"))):
+        with pytest.raises(P.SpmvError):
+            call()
+    gi = (24, 20, 18)
+    rowptr, col, val, _ = oracle.irregular_csr(*gi, seed=2, special_frac=0.0)
+    n = len(rowptr) - 1
+    A = P.spmv_build("irregular", *gi, seed=2, special_frac=0.0)
+    D = P.spmv_compress(A, format="data_table")
+    x = spmv_inputs.uniform_vector(n, seed=37)
+    assert np.array_equal(run(D, x).view(np.uint64), data_table_reference(rowptr, col, val, x).view(np.uint64))
+    R = P.spmv_compress(A, format="data_table", reorder=True)
+    perm = P.spmv_permutation(R)
+    rp, c2, v2 = permuted_csr(rowptr, col, val, perm)
+    yb = np.empty(n)
+    yb[perm] = data_table_reference(rp, c2, v2, x[perm])
+    assert np.array_equal(run(R, x).view(np.uint64), yb.view(np.uint64))
+    assert P.spmv_device_error(D) == 0 and P.spmv_device_error(R) == 0
+    ones = torch.ones(n, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(ones)
+    P.spmv_apply(A, ones, b)
+    xs = torch.zeros_like(ones)
+    r = P.cg_solve(D, b, xs, tol=1e-10, max_iter=2000, mode="fp64")
+    assert r["status"] == 0 and float((xs - 1).abs().max()) < 1e-7
+
+
+def test_data_table_192cubed_every_row(hpcg192):
+    """The Table II comparison's workload: the Data Table product at 192^3
+    (x seed 1) bit-identical to the oracle's chain on every row."""
+    x_np, y_ref, scale = hpcg192
+    nx = 192
+    rowptr, col, val = oracle.hpcg_csr(nx, nx, nx)
+    want = data_table_reference(rowptr, col, val, x_np)
+    del rowptr, col, val
+    D = P.spmv_compress(P.spmv_build("hpcg", nx, nx, nx), format="data_table")
+    y = run(D, x_np)
+    assert np.array_equal(y.view(np.uint64), want.view(np.uint64))
+    check_every_row(y, y_ref, scale)
+    assert P.spmv_device_error(D) == 0
+
+
 def permuted_csr(rowptr, col, val, perm):
     """P A P^T with perm[new] = old, columns ascending (numpy, test side)."""
     n = len(rowptr) - 1

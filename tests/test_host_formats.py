@@ -219,6 +219,62 @@ def test_data_index_table_signed_zeros_and_refusals():
         P.spmv_set_order(D, "fast")
 
 
+def data_table_bytes(rowptr, nv):
+    """S: 4 B for each slot of a 32-row slice, the slice as wide as its
+    longest row; ends: 1 B for each value and row."""
+    lens = np.diff(rowptr)
+    n = len(lens)
+    width = sum(int(lens[s:s + 32].max()) for s in range(0, n, 32)) if n else 0
+    return 4 * 32 * width + nv * n, 4 * (32 * width - int(lens.sum()))
+
+
+@pytest.mark.parametrize("g", [(1, 1, 1), (2, 3, 5), (17, 5, 3), (32, 32, 32)])
+def test_data_table_round_trip_and_sizes(g):
+    """Sec. V's Data Table (Fig. 2): bit-exact round trip, the value table of
+    the oracle, S_i at 4 B an entry in 32-row slices, 1 B a value a row."""
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    D = P.spmv_compress(P.spmv_build("hpcg", *g), format="data_table")
+    assert same_csr(P.spmv_decompress(D), (rowptr, col, val))
+    info = P.spmv_info(D)
+    V = oracle.value_table(val)
+    assert info["format_name"] == "data_table"
+    assert info["dict_size"] == len(V)
+    fb, pad = data_table_bytes(rowptr, len(V))
+    assert info["format_bytes"] == fb and info["padding_bytes"] == pad
+
+
+def test_data_table_irregular_signed_zeros_and_refusals():
+    # seventeen values (16 levels and the diagonal 26), permuted numbering
+    g = (9, 7, 11)
+    rowptr, col, val, _ = oracle.irregular_csr(*g, seed=13, special_frac=0.0)
+    A = P.spmv_build("irregular", *g, seed=13, special_frac=0.0)
+    D = P.spmv_compress(A, format="data_table")
+    assert same_csr(P.spmv_decompress(D), (rowptr, col, val))
+    assert P.spmv_info(D)["dict_size"] == len(oracle.value_table(val)) == 17
+    # with reordering the stored matrix is P A P^T; decompress gives A back
+    R = P.spmv_compress(A, format="data_table", reorder=True)
+    assert same_csr(P.spmv_decompress(R), (rowptr, col, val))
+    # -0.0 and +0.0 are two values
+    n = 300
+    band = [np.arange(max(0, i - 2), min(n, i + 3)) for i in range(n)]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in band])
+    c = np.concatenate(band).astype(np.int32)
+    v = np.where((c % 3) == 0, -0.0, np.where((c % 3) == 1, 0.0, 1.5))
+    got = P.spmv_decompress(P.spmv_compress(P.spmv_build_csr(rp, c, v), format="data_table"))
+    assert np.array_equal(got[0], rp) and np.array_equal(got[1], c)
+    assert np.array_equal(got[2].view(np.uint64), v.view(np.uint64))
+    # unique-valued rows: more than 255 distinct values
+    with pytest.raises(P.SpmvError) as e:
+        P.spmv_compress(P.spmv_build("irregular", 12, 12, 12, seed=2), format="data_table")
+    assert e.value.status == P.SPMV_EUNSUPPORTED
+    # no stream form, no FAST order
+    with pytest.raises(P.SpmvError):
+        P.spmv_export(D)
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_order(D, "fast")
+
+
 @pytest.mark.parametrize("g,seed", [((8, 8, 8), 2), ((16, 16, 16), 5)])
 def test_reorder_round_trip_and_locality(g, seed):
     """Locality reordering inside spmv_compress: a permutation, the exact
