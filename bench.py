@@ -36,14 +36,16 @@ METRIC = "SpMV GFLOP/s + % HBM roofline, compressed vs plain ELL, 192^3 HPCG, 1 
 WORKLOAD = "hpcg_192^3_x_seed1_compressed_pattern_uint8codes_5bit_patterns_vs_ell"
 
 
-KERNEL_SOURCES = ("k_spmv.cu", "k_tma.cu", "fast_fixed.cuh")
+KERNEL_SOURCES = {"tma": ("k_tma.cu", "fast_fixed.cuh", "tma_ptx.cuh"),
+                  "other": ("k_spmv.cu", "fast_fixed.cuh")}
 
 
-def kernel_source_hash() -> str:
-    """sha256 (first 16 hex digits) of the FAST kernels' sources, in order."""
+def kernel_source_hash(kernel: str = "") -> str:
+    """sha256 (first 16 hex digits) of the sources of a FAST kernel: the
+    TMA-fed kernel's files for ids starting with "tma", else k_spmv.cu's."""
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES["tma" if kernel.startswith("tma") else "other"]:
         with open(os.path.join(ROOT, "paper_1612_00530_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -63,7 +65,7 @@ def profiled(kernel: str, tag: str = "traffic", key: str = "bytes"):
                 parts = dict(p.split("=", 1) for p in line.split()[1:] if "=" in p)
                 if parts.get("kernel") == kernel:
                     fields = parts
-    if fields.get("source_sha256_16") != kernel_source_hash():
+    if fields.get("source_sha256_16") != kernel_source_hash(kernel):
         return None
     try:
         return float(fields[key])

@@ -62,8 +62,12 @@ typedef void *spmv_stream_t;
 #define SPMV_FMT_AUTO 0        /* compress: pattern format if it fits, else delta */
 #define SPMV_FMT_ELL 1         /* plain sliced ELL, FP64 value + int32 column */
 #define SPMV_FMT_PATTERN 2     /* uint8 value codes + stencil-pattern number per row */
-#define SPMV_FMT_DELTA 3       /* per 32-row slice: int16 delta or int32 column,
-                                  uint8 code or FP64 value */
+#define SPMV_FMT_DELTA 3       /* per 32-row slice: int16 delta, 24-bit delta
+                                  (int16 + int8 planes) or int32 column; uint8
+                                  code, uint8 code with per-entry escapes to
+                                  FP64 (a 32-bit mask a slot locates them), or
+                                  FP64 value -- the narrowest that holds the
+                                  slice */
 #define SPMV_FMT_DIT 4         /* Sec. V "Data+Index Table": per row a type (a
                                   registered value-grouped displacement list)
                                   and its value-group ends; Listing 1 decode */
@@ -219,7 +223,7 @@ typedef struct {
     int32_t row_types;          /* pattern format: distinct row records held as
                                    one-byte row types (variant 9), else 0 */
     int32_t reordered;          /* 1 if compressed with reorder = 1 */
-    int32_t reserved0;
+    int32_t slices_col24;       /* delta: slices storing 24-bit column deltas */
     int64_t bandwidth;          /* max |column - row| of the stored matrix */
 } spmv_info_t;
 
@@ -342,6 +346,26 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
  * Ignored for variants 0, 2, 4, 5.  SPMV_EINVAL for other block sizes,
  * SPMV_EUNSUPPORTED for shapes A has no kernel for. */
 int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads);
+
+/* The FAST-order SpMM kernel of a pattern-format handle.  kind 1, 2 or 3
+ * (1 is the default): for k >= 4 on a 27-point grid stencil with uniform
+ * neighbour weights, the TMA-fed z-marching kernel (blocks of L lines by W
+ * columns, 4 or 8 right-hand sides a pass, each row record read once a
+ * pass, every window converted once a column) with `kind` CTAs an SM, each
+ * taking blocks of at most 1536 / kind (row, column) outputs; X must then be
+ * 16-byte aligned with an even ldx, else the call takes kind 0.  kind 0: one
+ * thread a (row, column) pair.  All follow spmv_apply's FAST rule for every
+ * column, with the scale taken per column (the largest exponent a CTA has
+ * met in that column since its current run of planes began).  SPMV_EINVAL
+ * for another kind. */
+int spmv_set_spmm_kernel(spmv_mat_t A, int32_t kind);
+
+/* The binary32 product kernel of a pattern-format handle: kind 1 (the
+ * default) reads the one-byte row types (values registered in the pattern,
+ * Sec. V; built on the first binary32 call, when the matrix has at most 256
+ * distinct records), kind 0 the row records.  Both compute the same fmaf
+ * chain.  SPMV_EINVAL for another kind. */
+int spmv_set_f32_kernel(spmv_mat_t A, int32_t kind);
 
 /* Y = A X like spmm_apply, for callers that cannot allocate device memory
  * (a framework that routes every device allocation through its own pool, a

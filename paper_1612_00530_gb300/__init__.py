@@ -10,8 +10,8 @@ The functions keep the C names: spmv_build, spmv_build_csr, spmv_compress,
 spmv_set_order, spmv_info, spmv_decompress, spmv_export, spmv_import,
 spmv_apply, spmv_apply_host, spmv_apply_f32, spmm_apply, spmv_batch_create,
 spmv_batch_launch, spmv_batch_free, spmv_apply_batched, cg_solve,
-spmv_device_error, spmv_autotune, spmv_set_variant, spmv_set_tile, spmv_permutation,
-spmm_apply_noalloc, spmv_version.
+spmv_device_error, spmv_autotune, spmv_set_variant, spmv_set_tile,
+spmv_set_spmm_kernel, spmv_set_f32_kernel, spmv_permutation, spmm_apply_noalloc, spmv_version.
 """
 from __future__ import annotations
 
@@ -48,7 +48,7 @@ class spmv_info_t(ctypes.Structure):
                 ("fast_eligible", _i32), ("n_slices", _i64), ("slices_value_raw", _i64), ("slices_col_raw", _i64),
                 ("device_bytes", _i64), ("format_bytes", _i64), ("padding_bytes", _i64), ("checksum", _u64),
                 ("fast_tile_rows", _i32), ("fast_variant", _i32), ("fast_block_threads", _i32),
-                ("row_types", _i32), ("reordered", _i32), ("reserved0", _i32), ("bandwidth", _i64)]
+                ("row_types", _i32), ("reordered", _i32), ("slices_col24", _i32), ("bandwidth", _i64)]
 
 
 class spmv_cg_opts(ctypes.Structure):
@@ -102,6 +102,8 @@ def library() -> ctypes.CDLL:
             "spmv_autotune": [_p, _p, _p, _i32, ctypes.POINTER(_i32)],
             "spmv_set_variant": [_p, _i32, _i32],
             "spmv_set_tile": [_p, _i32, _i32, _i32],
+            "spmv_set_spmm_kernel": [_p, _i32],
+            "spmv_set_f32_kernel": [_p, _i32],
             "spmm_apply_noalloc": [_p, _i32, _p, _i64, _p, _i64, _p],
         }
         for name, args in sig.items():
@@ -236,6 +238,18 @@ def _dptr(t, dtype_name: str) -> int:
     return t.data_ptr()
 
 
+def _dptr_rows(t, dtype_name: str) -> int:
+    """A row-major block whose rows may be padded (stride(1) == 1, the
+    leading dimension stride(0) passed beside it)."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise ValueError(f"expected {dtype_name}, got {t.dtype}")
+    if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1) or t.stride(0) < t.shape[1]:
+        raise ValueError("expected a 2-D row-major block (unit column stride)")
+    return t.data_ptr()
+
+
 def spmv_apply(A: SpmvMatrix, x, y, stream=None) -> None:
     _check(library().spmv_apply(A, _dptr(x, "float64"), _dptr(y, "float64"), _stream(stream)))
 
@@ -253,16 +267,16 @@ def spmv_apply_f32(A: SpmvMatrix, x, y, stream=None) -> None:
 
 def spmm_apply(A: SpmvMatrix, X, Y, stream=None) -> None:
     k = X.shape[1]
-    _check(library().spmm_apply(A, k, _dptr(X, "float64"), X.stride(0), _dptr(Y, "float64"), Y.stride(0),
-                                _stream(stream)))
+    _check(library().spmm_apply(A, k, _dptr_rows(X, "float64"), X.stride(0), _dptr_rows(Y, "float64"),
+                                Y.stride(0), _stream(stream)))
 
 
 def spmm_apply_noalloc(A: SpmvMatrix, X, Y, stream=None) -> None:
     """Y = A X without any device allocation (pattern format, FAST order, A
     already on the device, at most 32 columns); see include/spmvc.h."""
     k = X.shape[1]
-    _check(library().spmm_apply_noalloc(A, k, _dptr(X, "float64"), X.stride(0), _dptr(Y, "float64"), Y.stride(0),
-                                        _stream(stream)))
+    _check(library().spmm_apply_noalloc(A, k, _dptr_rows(X, "float64"), X.stride(0), _dptr_rows(Y, "float64"),
+                                        Y.stride(0), _stream(stream)))
 
 
 class SpmvBatch:
@@ -345,6 +359,18 @@ def spmv_set_variant(A: SpmvMatrix, variant: int, tile_rows: int = 0) -> None:
     11 the TMA z-marching kernel (shapes and conditions in spmvc.h; 10
     needs spmv_set_tile)."""
     _check(library().spmv_set_variant(A, variant, tile_rows))
+
+
+def spmv_set_spmm_kernel(A: SpmvMatrix, kind: int) -> None:
+    """FAST SpMM kernel: 1, 2 or 3 the TMA-fed kernel with that many CTAs an
+    SM where it applies (1 by default), 0 one thread a (row, column) pair."""
+    _check(library().spmv_set_spmm_kernel(A, kind))
+
+
+def spmv_set_f32_kernel(A: SpmvMatrix, kind: int) -> None:
+    """Binary32 product kernel: 1 the one-byte row types (default), 0 the row
+    records."""
+    _check(library().spmv_set_f32_kernel(A, kind))
 
 
 def spmv_set_tile(A: SpmvMatrix, variant: int, tile_rows: int, block_threads: int) -> None:

@@ -315,6 +315,25 @@ int ensure_device(spmv_mat_s* m) {
                 m->tplan_ok = true;
             }
         }
+        // TMA SpMM plans, sharing the expected-record table
+        {
+            const uint32_t* table = m->tplan_ok ? m->tplan.expected : nullptr;
+            bool any = false;
+            for (int ki = 0; ki < 2; ++ki)
+                for (int c = 0; c < 3; ++c) {
+                    m->splan_ok[ki][c] = make_tma_spmm_plan(p, v, m->n, m->num_sms, ki ? 8 : 4, c + 1, &m->splan[ki][c]);
+                    any = any || m->splan_ok[ki][c];
+                }
+            if (any && !table) {
+                std::vector<uint32_t> tab;
+                expected_records(p, v, &tab);
+                uint32_t* dt;
+                if ((st = dev_copy(m, tab.data(), tab.size(), &dt))) return st;
+                table = dt;
+            }
+            for (int ki = 0; ki < 2; ++ki)
+                for (int c = 0; c < 3; ++c) m->splan[ki][c].expected = table;
+        }
         if (m->fast_variant == 11 && !m->tplan_ok) m->fast_variant = 1;
         if (m->fast_variant == 7 && !m->zplan_ok) m->fast_variant = 1;
         if (m->fast_variant == 10 && !m->zbplan_ok) m->fast_variant = 1;
@@ -483,6 +502,34 @@ int apply_stored(spmv_mat_s* A, const double* x, double* y, cudaStream_t s) {
 }
 
 
+// Values registered in the pattern: the row types, built and uploaded once
+// (false when the matrix has more than 256 distinct records or is not on
+// the device yet).
+bool ensure_row_types(spmv_mat_s* A) {
+    if (A->pat_view.rtype) return true;
+    if (A->fmt != SPMV_FMT_PATTERN || A->device < 0 || A->types_failed) return false;
+    if (!build_row_types(A->n, &A->pat)) {
+        A->types_failed = true;
+        return false;
+    }
+    uint8_t* rt;
+    uint32_t* tt;
+    if (dev_copy(A, A->pat.rtype.data(), A->pat.rtype.size(), &rt)) return false;
+    if (dev_copy(A, A->pat.rtypes.data(), A->pat.rtypes.size(), &tt)) return false;
+    A->pat_view.rtype = rt;
+    A->pat_view.rtypes = tt;
+    A->pat_view.ntypes = static_cast<int32_t>(A->pat.rtypes.size() / 8);
+    // the type whose record is the dominant one, if any
+    A->pat_view.dom_type = -1;
+    if (A->pat_view.dom_ok)
+        for (int32_t t = 0; t < A->pat_view.ntypes; ++t)
+            if (std::equal(A->pat.rtypes.begin() + t * 8, A->pat.rtypes.begin() + t * 8 + 7, A->pat_view.dom_w)) {
+                A->pat_view.dom_type = t;
+                break;
+            }
+    return true;
+}
+
 }  // namespace
 }  // namespace spmvc
 
@@ -638,15 +685,23 @@ int spmv_info(spmv_mat_t A, spmv_info_t* out) {
         for (const auto& h : A->dlt.hdr) {
             out->slices_value_raw += (h.flags & kSliceValRaw) ? 1 : 0;
             out->slices_col_raw += (h.flags & kSliceColRaw) ? 1 : 0;
+            out->slices_col24 += (h.flags & kSliceCol24) ? 1 : 0;
         }
         out->format_bytes = static_cast<int64_t>(A->dlt.payload.size() + A->dlt.hdr.size() * sizeof(DeltaSlice));
         int64_t useful = A->n;  // row lengths
         for (int64_t s = 0; s < A->dlt.nslices; ++s) {
             const auto& h = A->dlt.hdr[s];
             const int64_t r0 = s * kSliceRows, r1 = std::min<int64_t>(A->n, r0 + kSliceRows);
-            const int64_t per = ((h.flags & kSliceColRaw) ? 4 : 2) + ((h.flags & kSliceValRaw) ? 8 : 1);
+            const int64_t per = ((h.flags & kSliceColRaw) ? 4 : (h.flags & kSliceCol24) ? 3 : 2) +
+                                ((h.flags & kSliceValRaw) ? 8 : 1);
             const uint8_t* base = A->dlt.payload.data() + h.off;
             for (int64_t r = r0; r < r1; ++r) useful += per * base[r - r0];
+            if (h.flags & kSliceValLocal) {   // the slice's own value table
+                const DeltaParts pt = delta_parts(h.w, h.flags);
+                uint32_t nloc;
+                std::memcpy(&nloc, base + pt.local, 4);
+                useful += 8 * int64_t(nloc);
+            }
         }
         out->padding_bytes = out->format_bytes - useful - static_cast<int64_t>(A->dlt.hdr.size() * sizeof(DeltaSlice));
         out->device_bytes = out->format_bytes + static_cast<int64_t>(A->dlt.dict.size() * 12);
@@ -820,7 +875,8 @@ int spmv_apply_host(spmv_mat_t A, const double* x, double* y) {
     return SPMV_OK;
 }
 
-int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
+// binary32 product from the stored records (or ELL values)
+static int apply_f32_records(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (A->fmt == SPMV_FMT_DIT) return fail(SPMV_EUNSUPPORTED, "no binary32 product for the Data+Index Table format");
     if (A->fmt == SPMV_FMT_DATA_TABLE) return fail(SPMV_EUNSUPPORTED, "no binary32 product for the Data Table format");
@@ -847,6 +903,22 @@ int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream)
     return SPMV_OK;
 }
 
+int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->fmt == SPMV_FMT_PATTERN && A->perm.empty() && A->n > 0 && x && y) {
+        // one byte a row: the binary32 chain from the row types where the
+        // matrix has at most 256 distinct records
+        int st = ensure_device(A);
+        if (st) return st;
+        if (A->f32_types && ensure_row_types(A)) {
+            const cudaError_t e = launch_pattern_types_f32(A->pat_view, x, y, as_stream(stream));
+            if (e == cudaSuccess) return SPMV_OK;
+            if (e != cudaErrorNotSupported) return cuda_fail(e, "spmv_f32 launch");
+        }
+    }
+    return apply_f32_records(A, x, y, stream);
+}
+
 int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y, int64_t ldy,
                spmv_stream_t stream) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
@@ -859,6 +931,19 @@ int spmm_apply(spmv_mat_t A, int32_t k, const double* X, int64_t ldx, double* Y,
     if (st) return st;
     const cudaStream_t s = as_stream(stream);
     cudaError_t e;
+    if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->n > 0) {
+        // the TMA-fed kernel: 8 columns a pass from k = 8, else 4 from k = 4
+        const int c = A->spmm_kind - 1;
+        const TmaSpmmPlan* tp = c < 0 ? nullptr
+                                : k >= 8 && A->splan_ok[1][c] ? &A->splan[1][c]
+                                : k >= 4 && A->splan_ok[0][c] ? &A->splan[0][c]
+                                                              : nullptr;
+        if (tp) {
+            e = launch_pattern_spmm_tma(A->pat_view, *tp, k, X, ldx, Y, ldy, s);
+            if (e == cudaSuccess) return SPMV_OK;
+            if (e != cudaErrorNotSupported) return cuda_fail(e, "spmm launch");
+        }
+    }
     if (A->fmt == SPMV_FMT_ELL) e = launch_ell_spmm(A->ell_view, k, X, ldx, Y, ldy, s);
     else if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->d_xfixed &&
              A->pat_view.run_len == 3 && A->pat_view.nu == 27) {
@@ -1045,6 +1130,20 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
     return SPMV_OK;
 }
 
+int spmv_set_f32_kernel(spmv_mat_t A, int32_t kind) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (kind != 0 && kind != 1) return fail(SPMV_EINVAL, "binary32 kernel kind must be 0 or 1");
+    A->f32_types = kind == 1;
+    return SPMV_OK;
+}
+
+int spmv_set_spmm_kernel(spmv_mat_t A, int32_t kind) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (kind < 0 || kind > 3) return fail(SPMV_EINVAL, "SpMM kernel kind must be 0 to 3");
+    A->spmm_kind = kind;
+    return SPMV_OK;
+}
+
 int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
     if (A->fmt != SPMV_FMT_PATTERN || !A->pat.fast_ok) return fail(SPMV_EUNSUPPORTED, "no FAST kernels for this matrix");
@@ -1127,18 +1226,8 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
     if (rstaged && !rstage_supported(plan))
         return fail(SPMV_EUNSUPPORTED, "register-staged kernel: tile_rows/threads 1024/256, 512/256 or 1024/512 "
                                        "with windows of at most 2*pairs*threads elements");
-    if (variant == 9 && !A->pat_view.rtype) {
-        // values registered in the pattern: the row types, built and uploaded once
-        if (!build_row_types(A->n, &A->pat))
-            return fail(SPMV_EUNSUPPORTED, "more than 256 distinct row records: no row types");
-        uint8_t* rt;
-        uint32_t* tt;
-        if ((st = dev_copy(A, A->pat.rtype.data(), A->pat.rtype.size(), &rt))) return st;
-        if ((st = dev_copy(A, A->pat.rtypes.data(), A->pat.rtypes.size(), &tt))) return st;
-        A->pat_view.rtype = rt;
-        A->pat_view.rtypes = tt;
-        A->pat_view.ntypes = static_cast<int32_t>(A->pat.rtypes.size() / 8);
-    }
+    if (variant == 9 && !ensure_row_types(A))
+        return fail(SPMV_EUNSUPPORTED, "more than 256 distinct row records: no row types");
     A->stage = plan;
     A->stage_ok = true;
     A->fast_variant = variant;
@@ -1192,6 +1281,13 @@ const char* spmv_version(void) { return "spmvc 0.1 (sm_103a)"; }
 // Accessors used by the solver and batch translation units.
 namespace spmvc {
 int api_ensure_device(spmv_mat_s* m) { return ensure_device(m); }
+// Before timed binary32 work: the device copy and, for the pattern format,
+// the one-byte row types (built on the host once).
+int api_prepare_f32(spmv_mat_s* m) {
+    const int st = ensure_device(m);
+    if (st == SPMV_OK && m->fmt == SPMV_FMT_PATTERN && m->perm.empty() && m->f32_types) ensure_row_types(m);
+    return st;
+}
 bool api_valid(spmv_mat_t m) { return valid(m); }
 
 // y = A x where the caller also has the partial maxima of x's high words

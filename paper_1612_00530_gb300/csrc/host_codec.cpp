@@ -190,23 +190,29 @@ int decompress_data_table(int64_t n, const DataTableFormat& d, Csr* out) {
 }
 
 int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out) {
-    if (d.nslices != (n + kSliceRows - 1) / kSliceRows || (int64_t)d.hdr.size() != d.nslices || d.dict.size() > 255)
+    if (d.nslices != (n + kSliceRows - 1) / kSliceRows || (int64_t)d.hdr.size() != d.nslices || d.dict.size() > 254)
         return corrupt("delta slice table size");
     out->n = n;
     out->rowptr.assign(n + 1, 0);
     out->col.clear();
     out->val.clear();
+    const uint32_t nd = static_cast<uint32_t>(d.dict.size());
     for (int64_t s = 0; s < d.nslices; ++s) {
         const DeltaSlice h = d.hdr[s];
-        const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
-        if (h.flags & ~3u) return corrupt("slice flags");
+        const bool craw = h.flags & kSliceColRaw, c24 = h.flags & kSliceCol24;
+        const bool vraw = h.flags & kSliceValRaw, vloc = h.flags & kSliceValLocal;
+        if ((h.flags & ~15u) || (craw && c24) || (vraw && vloc)) return corrupt("slice flags");
         if (h.w > 255 || h.off % 16 != 0) return corrupt("slice header");
-        const uint64_t cbytes = (32 + uint64_t(h.w) * kSliceRows * (craw ? 4 : 2) + 15) / 16 * 16;
-        const uint64_t vbytes = (uint64_t(h.w) * kSliceRows * (vraw ? 8 : 1) + 15) / 16 * 16;
-        if (h.off + cbytes + vbytes > d.payload.size()) return corrupt("slice payload bounds");
+        const DeltaParts pt = delta_parts(h.w, h.flags);
+        if (h.off + pt.local > d.payload.size()) return corrupt("slice payload bounds");
         const uint8_t* base = d.payload.data() + h.off;
-        const uint8_t* cols = base + 32;
-        const uint8_t* vals = base + cbytes;
+        uint32_t nloc = 0;
+        if (vloc) {
+            if (h.off + pt.local + 16 > d.payload.size()) return corrupt("slice payload bounds");
+            std::memcpy(&nloc, base + pt.local, 4);
+            if (nloc > 256 - nd || h.off + pt.local + 16 + 8 * uint64_t(nloc) > d.payload.size())
+                return corrupt("slice value table");
+        }
         for (int64_t r = s * kSliceRows; r < std::min(n, (s + 1) * kSliceRows); ++r) {
             const int64_t l = r - s * kSliceRows;
             const uint32_t len = base[l];
@@ -216,20 +222,24 @@ int decompress_delta(int64_t n, const DeltaFormat& d, Csr* out) {
                 int64_t c;
                 if (craw) {
                     int32_t c32;
-                    std::memcpy(&c32, cols + 4 * slot, 4);
+                    std::memcpy(&c32, base + pt.cols + 4 * slot, 4);
                     c = c32;
                 } else {
-                    int16_t d16;
-                    std::memcpy(&d16, cols + 2 * slot, 2);
-                    c = r + d16;
+                    int16_t lo;
+                    std::memcpy(&lo, base + pt.cols + 2 * slot, 2);
+                    int64_t dlt = lo;
+                    if (c24) dlt = int64_t(int8_t(base[pt.hi + slot])) * 65536 + int64_t(uint16_t(lo));
+                    c = r + dlt;
                 }
                 if (c < 0 || c >= n) return corrupt("delta column out of range");
                 double v;
                 if (vraw) {
-                    std::memcpy(&v, vals + 8 * slot, 8);
+                    std::memcpy(&v, base + pt.vals + 8 * slot, 8);
                 } else {
-                    if (vals[slot] >= d.dict.size()) return corrupt("value code out of range");
-                    v = d.dict[vals[slot]];
+                    const uint32_t cv = base[pt.vals + slot];
+                    if (cv < nd) v = d.dict[cv];
+                    else if (vloc && cv - nd < nloc) std::memcpy(&v, base + pt.local + 16 + 8 * (cv - nd), 8);
+                    else return corrupt("value code out of range");
                 }
                 out->col.push_back(static_cast<int32_t>(c));
                 out->val.push_back(v);

@@ -6,6 +6,7 @@
 // decompression is bit-exact and doubles as the validation of imported
 // streams.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -210,20 +211,17 @@ bool build_row_types(int64_t n, PatternFormat* p) {
     p->rtype.clear();
     p->rtypes.clear();
     if (p->words != 7) return false;
-    std::map<std::vector<uint32_t>, int> types;
-    std::vector<uint8_t> rtype(static_cast<size_t>(n));
-    std::vector<uint32_t> table;
-    std::vector<uint32_t> key(7);
-    for (int64_t r = 0; r < n; ++r) {
+    std::vector<std::array<uint32_t, 7>> types;
+    std::vector<uint8_t> rtype;
+    auto rec_of = [&](int64_t r, std::array<uint32_t, 7>& key) {
         std::copy(&p->rec[static_cast<size_t>(r) * 7], &p->rec[static_cast<size_t>(r) * 7] + 7, key.begin());
-        auto it = types.find(key);
-        if (it == types.end()) {
-            if (types.size() == 256) return false;
-            it = types.emplace(key, static_cast<int>(types.size())).first;
-            table.insert(table.end(), key.begin(), key.end());
-            table.push_back(0u);                       // 8 words a type
-        }
-        rtype[r] = static_cast<uint8_t>(it->second);
+        return true;
+    };
+    if (register_first_seen(n, 256, rec_of, &rtype, &types)) return false;
+    std::vector<uint32_t> table;
+    for (const auto& t : types) {
+        table.insert(table.end(), t.begin(), t.end());
+        table.push_back(0u);                       // 8 words a type
     }
     p->rtype = std::move(rtype);
     p->rtypes = std::move(table);
@@ -414,31 +412,44 @@ void delta_dictionary(const std::vector<double>& val, int max_dict, int min_coun
 
 int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) {
     const int64_t n = a.n;
-    delta_dictionary(a.val, max_dict, min_count, &out->dict);
+    delta_dictionary(a.val, std::min(max_dict, 254), min_count, &out->dict);
     const BitsTable code = code_table(out->dict);
+    const int nd = static_cast<int>(out->dict.size());
 
     const int64_t ns = (n + kSliceRows - 1) / kSliceRows;
     out->nslices = ns;
     out->hdr.assign(ns, DeltaSlice{0, 0, 0});
     std::vector<uint64_t> bytes(static_cast<size_t>(ns));
     std::atomic<bool> too_wide{false};
+    // per slice: the narrowest column encoding that holds every delta, and
+    // global codes, global and local codes, or raw values, whichever fits
+    // and is smallest (a local table holds the slice's distinct values that
+    // the global table lacks, at most 256 - |global table| of them)
     parallel_ranges(ns, 2048, [&](int64_t s0, int64_t s1, int) {
+        BitsTable loc;
         for (int64_t s = s0; s < s1; ++s) {
             const int64_t r0 = s * kSliceRows, r1 = std::min(n, r0 + kSliceRows);
-            int64_t w = 0;
-            uint32_t flags = 0;
+            int64_t w = 0, maxd = 0;
+            loc.reset(8);
             for (int64_t r = r0; r < r1; ++r) {
                 w = std::max<int64_t>(w, a.rowptr[r + 1] - a.rowptr[r]);
                 for (int64_t k = a.rowptr[r]; k < a.rowptr[r + 1]; ++k) {
                     const int64_t dlt = static_cast<int64_t>(a.col[k]) - r;
-                    if (dlt < -32768 || dlt > 32767) flags |= kSliceColRaw;
-                    if (std::isnan(a.val[k]) || code.get(value_bits(a.val[k]), -1) < 0) flags |= kSliceValRaw;
+                    maxd = std::max<int64_t>(maxd, dlt < 0 ? -dlt - 1 : dlt);   // two's complement range
+                    if (code.get(value_bits(a.val[k]), -1) < 0) loc.at(value_bits(a.val[k])) = 0;
                 }
             }
             if (w > 255) too_wide = true;
-            const int64_t cb = (flags & kSliceColRaw) ? 4 : 2, vb = (flags & kSliceValRaw) ? 8 : 1;
-            out->hdr[s] = DeltaSlice{0, static_cast<uint32_t>(std::min<int64_t>(w, 255)), flags};
-            bytes[s] = round_up(32 + w * kSliceRows * cb, 16) + round_up(w * kSliceRows * vb, 16);
+            w = std::min<int64_t>(w, 255);
+            const int64_t nloc = int64_t(loc.size());
+            uint32_t flags = maxd <= 32767 ? 0u : maxd <= 8388607 ? kSliceCol24 : kSliceColRaw;
+            if (nloc > 0) {
+                const bool fits = nloc <= 256 - nd;
+                flags |= fits && 16 + 8 * nloc < w * kSliceRows * 7 ? kSliceValLocal : kSliceValRaw;
+            }
+            out->hdr[s] = DeltaSlice{0, static_cast<uint32_t>(w), flags};
+            const DeltaParts pt = delta_parts(uint32_t(w), flags);
+            bytes[s] = (flags & kSliceValLocal) ? delta_up16(pt.local + 16 + 8 * uint64_t(nloc)) : pt.local;
         }
     });
     if (too_wide) return fail(SPMV_EUNSUPPORTED, "delta format holds at most 255 entries per row");
@@ -449,13 +460,16 @@ int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) 
     }
     out->payload.assign(off, 0);
     parallel_ranges(ns, 2048, [&](int64_t s0, int64_t s1, int) {
+        BitsTable loc;
         for (int64_t s = s0; s < s1; ++s) {
             const DeltaSlice h = out->hdr[s];
+            const DeltaParts pt = delta_parts(h.w, h.flags);
             const int64_t r0 = s * kSliceRows, r1 = std::min(n, r0 + kSliceRows);
             uint8_t* base = out->payload.data() + h.off;
-            const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
-            uint8_t* cols = base + 32;
-            uint8_t* vals = base + round_up(32 + int64_t(h.w) * kSliceRows * (craw ? 4 : 2), 16);
+            const bool craw = h.flags & kSliceColRaw, c24 = h.flags & kSliceCol24;
+            const bool vraw = h.flags & kSliceValRaw, vloc = h.flags & kSliceValLocal;
+            loc.reset(8);
+            uint32_t nloc = 0;
             for (int64_t r = r0; r < r1; ++r) {
                 const int64_t l = r - r0;
                 base[l] = static_cast<uint8_t>(a.rowptr[r + 1] - a.rowptr[r]);
@@ -464,15 +478,30 @@ int compress_delta(const Csr& a, int max_dict, int min_count, DeltaFormat* out) 
                     const int64_t slot = t * kSliceRows + l;
                     if (craw) {
                         const int32_t c = a.col[k];
-                        std::memcpy(cols + 4 * slot, &c, 4);
+                        std::memcpy(base + pt.cols + 4 * slot, &c, 4);
                     } else {
-                        const int16_t d16 = static_cast<int16_t>(a.col[k] - r);
-                        std::memcpy(cols + 2 * slot, &d16, 2);
+                        const int32_t d = static_cast<int32_t>(a.col[k] - r);
+                        const int16_t lo = static_cast<int16_t>(static_cast<uint16_t>(uint32_t(d) & 0xFFFFu));
+                        std::memcpy(base + pt.cols + 2 * slot, &lo, 2);
+                        if (c24) base[pt.hi + slot] = static_cast<uint8_t>(static_cast<int8_t>(d >> 16));
                     }
-                    if (vraw) std::memcpy(vals + 8 * slot, &a.val[k], 8);
-                    else vals[slot] = static_cast<uint8_t>(code.get(value_bits(a.val[k]), 0));
+                    if (vraw) {
+                        std::memcpy(base + pt.vals + 8 * slot, &a.val[k], 8);
+                        continue;
+                    }
+                    int64_t cv = code.get(value_bits(a.val[k]), -1);
+                    if (cv < 0 && vloc) {   // the slice's own table, in order of first use
+                        int64_t& e = loc.at(value_bits(a.val[k]));
+                        if (e == 0) {
+                            e = ++nloc;
+                            std::memcpy(base + pt.local + 16 + 8 * (nloc - 1), &a.val[k], 8);
+                        }
+                        cv = int64_t(out->dict.size()) + e - 1;
+                    }
+                    base[pt.vals + slot] = static_cast<uint8_t>(cv);
                 }
             }
+            if (vloc) std::memcpy(base + pt.local, &nloc, 4);
         }
     });
     return SPMV_OK;

@@ -21,6 +21,7 @@ int api_ensure_device(spmv_mat_s* m);
 bool api_valid(spmv_mat_t m);
 int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xmax_part, int xmax_n,
                    cudaStream_t s);
+int api_prepare_f32(spmv_mat_s* m);
 
 namespace {
 
@@ -29,7 +30,7 @@ constexpr int kRedThreads = 256;
 
 struct CgState {
     double rr;          // inner r.r (IR)
-    double rr2[2];      // FP64 CG: r.r before the step of that parity
+    double rr2[2];      // r.r before the step of that parity (FP64 and binary32 loops)
     double rr0;         // inner: initial r.r
     double bnorm;
     double tol;
@@ -274,13 +275,13 @@ __global__ void __launch_bounds__(kRedThreads) update_dr32_kernel(float* __restr
                                                                   const float* __restrict__ p, const float* __restrict__ q,
                                                                   int64_t n, const double* __restrict__ partial_pq,
                                                                   double* __restrict__ partial_rr,
-                                                                  const CgState* __restrict__ st) {
+                                                                  const CgState* __restrict__ st, int par) {
     if (st->done) return;
     __shared__ double sm[32];
     __shared__ float s_alpha;
     if (threadIdx.x < 32) {
         const double pq = sum_partials(partial_pq);
-        if (threadIdx.x == 0) s_alpha = float(st->rr / pq);
+        if (threadIdx.x == 0) s_alpha = float(st->rr2[par] / pq);
     }
     __syncthreads();
     const float alpha = s_alpha;
@@ -318,14 +319,25 @@ __global__ void __launch_bounds__(kRedThreads) update_dr32_kernel(float* __restr
     if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
 }
 
+// beta; p = r + beta p.  Block 0 also closes the inner step (r.r into the
+// other parity's slot, the step count, the stopping test), as in the FP64
+// loop.
 __global__ void __launch_bounds__(kRedThreads) update_p32_kernel(float* __restrict__ p, const float* __restrict__ r,
                                                                  int64_t n, const double* __restrict__ partial_rr,
-                                                                 const CgState* __restrict__ st) {
+                                                                 CgState* __restrict__ st, int par) {
     if (st->done) return;
     __shared__ float s_beta;
     if (threadIdx.x < 32) {
         const double rr_new = sum_partials(partial_rr);
-        if (threadIdx.x == 0) s_beta = float(rr_new / st->rr);
+        if (threadIdx.x == 0) {
+            s_beta = float(rr_new / st->rr2[par]);
+            if (blockIdx.x == 0) {
+                st->rr2[par ^ 1] = rr_new;
+                const int32_t it = st->it + 1;
+                st->it = it;
+                if (sqrt(rr_new / st->rr0) <= st->tol || it >= st->max_it) st->done = 1;
+            }
+        }
     }
     __syncthreads();
     const float beta = s_beta;
@@ -342,16 +354,6 @@ __global__ void __launch_bounds__(kRedThreads) update_p32_kernel(float* __restri
     if (blockIdx.x == 0 && threadIdx.x < 4 && n4 * 4 + threadIdx.x < n) {
         const int64_t i = n4 * 4 + threadIdx.x;
         p[i] = fmaf(beta, p[i], r[i]);
-    }
-}
-
-__global__ void finalize32_kernel(const double* __restrict__ partial_rr, CgState* __restrict__ st) {
-    if (st->done) return;
-    const double rr_new = sum_partials(partial_rr);
-    if (threadIdx.x == 0) {
-        st->rr = rr_new;
-        st->it += 1;
-        if (sqrt(rr_new / st->rr0) <= st->tol || st->it >= st->max_it) st->done = 1;
     }
 }
 
@@ -378,6 +380,7 @@ __global__ void inner_init_state_kernel(const double* __restrict__ partial, CgSt
     const double rr = sum_partials(partial);
     if (threadIdx.x == 0) {
         st->rr = rr;
+        st->rr2[0] = rr;
         st->rr0 = rr;
         st->tol = inner_tol;
         st->it = 0;
@@ -765,6 +768,7 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    if (o.mode != SPMV_CG_FP64) CG_ST(api_prepare_f32(A));   // row types built before the clock starts
     CG_CUDA(cudaEventRecord(e0, s));
 
     const unsigned G = kRedBlocks, T = kRedThreads;
@@ -843,17 +847,19 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
             inner_start_kernel<<<G, T, 0, s>>>(r, 1.0 / rnorm, r32, p32, d32, n, part_a);
             inner_init_state_kernel<<<1, 32, 0, s>>>(part_a, d_st, o.inner_tol,
                                                      std::min(o.inner_max_iter, o.max_iter - total_inner));
+            int step = 0;   // parity of r.r's slot, as in the FP64 loop
             auto body = [&]() -> int {
+                const int par = step++ & 1;
                 CG_ST(spmv_apply_f32(A, p32, q32, s));
                 dot32_kernel<<<G, T, 0, s>>>(p32, q32, n, part_a, d_st);
-                update_dr32_kernel<<<G, T, 0, s>>>(d32, r32, p32, q32, n, part_a, part_b, d_st);
-                update_p32_kernel<<<G, T, 0, s>>>(p32, r32, n, part_b, d_st);
-                finalize32_kernel<<<1, 32, 0, s>>>(part_b, d_st);
+                update_dr32_kernel<<<G, T, 0, s>>>(d32, r32, p32, q32, n, part_a, part_b, d_st, par);
+                update_p32_kernel<<<G, T, 0, s>>>(p32, r32, n, part_b, d_st, par);
                 CG_CUDA(cudaGetLastError());
                 return SPMV_OK;
             };
-            const int replays = (o.inner_max_iter + o.check_every - 1) / o.check_every + 1;
-            CG_ST(run_until_done(s, o.use_graph != 0, o.check_every, d_st, replays, body));
+            const int chunk = (o.check_every + 1) & ~1;
+            const int replays = (o.inner_max_iter + chunk - 1) / chunk + 1;
+            CG_ST(run_until_done(s, o.use_graph != 0, chunk, d_st, replays, body));
             CgState h;
             CG_CUDA(cudaMemcpyAsync(&h, d_st, sizeof(h), cudaMemcpyDeviceToHost, s));
             CG_CUDA(cudaStreamSynchronize(s));

@@ -1392,28 +1392,60 @@ __global__ void __launch_bounds__(kBlock) pattern_f32_kernel(PatternView a, cons
 }
 
 // ------------------------------------------------------------ delta ------
-template <typename T, bool CRAW, bool VRAW>
-__device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, uint32_t w, int64_t r, int l,
-                                       int len, const T* sdict, const T* __restrict__ x) {
-    const uint8_t* cols = base + 32;
-    const uint8_t* vals = base + ((32 + uint64_t(w) * 32 * (CRAW ? 4 : 2) + 15) & ~uint64_t(15));
+// One row of a delta slice.  CM: column encoding (0 int16 delta, 1 24-bit
+// delta, 2 raw int32); VM: value encoding (0 code, 1 code into the global
+// table or, from dict_size up, into the slice's own table, 2 raw double).
+template <typename T, int CM, int VM>
+__device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, uint32_t w, uint32_t flags, int64_t r,
+                                       int l, int len, const T* sdict, const T* __restrict__ x, int64_t ldx, int j) {
+    const DeltaParts pt = delta_parts(w, flags);
+    const double* local = reinterpret_cast<const double*>(base + pt.local) + 2;   // after its 16-byte count
     T acc = T(0);
     for (int t = 0; t < len; ++t) {
         const int64_t slot = int64_t(t) * 32 + l;
         int64_t c;
-        if constexpr (CRAW) c = __ldcs(reinterpret_cast<const int32_t*>(cols) + slot);
-        else c = r + __ldcs(reinterpret_cast<const int16_t*>(cols) + slot);
+        if constexpr (CM == 2) {
+            c = __ldcs(reinterpret_cast<const int32_t*>(base + pt.cols) + slot);
+        } else {
+            const int16_t lo = __ldcs(reinterpret_cast<const int16_t*>(base + pt.cols) + slot);
+            if constexpr (CM == 1)
+                c = r + int64_t(int8_t(__ldcs(base + pt.hi + slot))) * 65536 + int64_t(uint16_t(lo));
+            else
+                c = r + lo;
+        }
         T v;
-        if constexpr (VRAW) v = T(__ldcs(reinterpret_cast<const double*>(vals) + slot));
-        else {
-            const uint32_t code = __ldcs(vals + slot);
-            if (code >= uint32_t(a.dict_size)) { raise_error(a.err, 2); continue; }
-            v = sdict[code];
+        if constexpr (VM == 2) {
+            v = T(__ldcs(reinterpret_cast<const double*>(base + pt.vals) + slot));
+        } else {
+            const uint32_t code = __ldcs(base + pt.vals + slot);
+            if (code < uint32_t(a.dict_size)) {
+                v = sdict[code];
+            } else if (VM == 1) {
+                v = T(__ldg(local + (code - uint32_t(a.dict_size))));
+            } else {
+                raise_error(a.err, 2);
+                continue;
+            }
         }
         if (uint64_t(c) >= uint64_t(a.n)) { raise_error(a.err, 2); continue; }
-        acc = fma(v, __ldg(x + c), acc);
+        acc = fma(v, __ldg(x + c * ldx + j), acc);
     }
     return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T delta_row_any(const DeltaView& a, const uint8_t* base, const DeltaSlice& h, int64_t r,
+                                           int l, int len, const T* sdict, const T* __restrict__ x, int64_t ldx,
+                                           int j) {
+    const int cm = (h.flags & kSliceColRaw) ? 2 : (h.flags & kSliceCol24) ? 1 : 0;
+    const int vm = (h.flags & kSliceValRaw) ? 2 : (h.flags & kSliceValLocal) ? 1 : 0;
+#define SPMVC_DELTA_ROW(C_, V_) \
+    if (cm == C_ && vm == V_) return delta_row<T, C_, V_>(a, base, h.w, h.flags, r, l, len, sdict, x, ldx, j);
+    SPMVC_DELTA_ROW(0, 0) SPMVC_DELTA_ROW(0, 1) SPMVC_DELTA_ROW(0, 2)
+    SPMVC_DELTA_ROW(1, 0) SPMVC_DELTA_ROW(1, 1) SPMVC_DELTA_ROW(1, 2)
+    SPMVC_DELTA_ROW(2, 0) SPMVC_DELTA_ROW(2, 1) SPMVC_DELTA_ROW(2, 2)
+#undef SPMVC_DELTA_ROW
+    return T(0);
 }
 
 template <typename T>
@@ -1436,12 +1468,7 @@ __global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __r
     const int64_t r = s * 32 + l;
     int len = r < a.n ? int(base[l]) : 0;
     if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
-    T acc;
-    const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
-    if (craw) acc = vraw ? delta_row<T, true, true>(a, base, h.w, r, l, len, sdict, x)
-                         : delta_row<T, true, false>(a, base, h.w, r, l, len, sdict, x);
-    else acc = vraw ? delta_row<T, false, true>(a, base, h.w, r, l, len, sdict, x)
-                    : delta_row<T, false, false>(a, base, h.w, r, l, len, sdict, x);
+    const T acc = delta_row_any<T>(a, base, h, r, l, len, sdict, x, 1, 0);
     if (r < a.n) y[r] = acc;
 }
 
@@ -1568,6 +1595,9 @@ __global__ void __launch_bounds__(kBlock) ell_spmm_kernel(EllView a, int k, cons
 
 __global__ void __launch_bounds__(kBlock) delta_spmm_kernel(DeltaView a, int k, const double* __restrict__ X,
                                                             int64_t ldx, double* __restrict__ Y, int64_t ldy) {
+    __shared__ double sdict[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sdict[i] = i < a.dict_size ? a.dict[i] : 0.0;
+    __syncthreads();
     const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int64_t r = idx / k;
     const int j = int(idx - r * k);
@@ -1576,27 +1606,9 @@ __global__ void __launch_bounds__(kBlock) delta_spmm_kernel(DeltaView a, int k, 
     const int l = int(r & 31);
     const DeltaSlice h = a.hdr[s];
     const uint8_t* base = a.payload + h.off;
-    const bool craw = h.flags & kSliceColRaw, vraw = h.flags & kSliceValRaw;
-    const uint8_t* cols = base + 32;
-    const uint8_t* vals = base + ((32 + uint64_t(h.w) * 32 * (craw ? 4 : 2) + 15) & ~uint64_t(15));
     int len = base[l];
     if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
-    double acc = 0.0;
-    for (int t = 0; t < len; ++t) {
-        const int64_t slot = int64_t(t) * 32 + l;
-        const int64_t c = craw ? int64_t(reinterpret_cast<const int32_t*>(cols)[slot])
-                               : r + reinterpret_cast<const int16_t*>(cols)[slot];
-        double v;
-        if (vraw) v = reinterpret_cast<const double*>(vals)[slot];
-        else {
-            const uint32_t code = vals[slot];
-            if (code >= uint32_t(a.dict_size)) { raise_error(a.err, 2); continue; }
-            v = a.dict[code];
-        }
-        if (uint64_t(c) >= uint64_t(a.n)) { raise_error(a.err, 2); continue; }
-        acc = fma(v, __ldg(X + c * ldx + j), acc);
-    }
-    Y[r * ldy + j] = acc;
+    Y[r * ldy + j] = delta_row_any<double>(a, base, h, r, l, len, sdict, X, ldx, j);
 }
 
 __global__ void fill_u32_kernel(uint32_t* p, uint32_t v, int64_t n) {
@@ -1665,6 +1677,75 @@ cudaError_t launch_pattern_col_f64(const PatternView& a, const double* x, double
     SPMVC_DISPATCH_WORDS(a.words, (pattern_col_kernel<W, double><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y)));
     return cudaGetLastError();
 }
+// Binary32 product from the one-byte row types (values registered in the
+// pattern, Sec. V): a row's record is the type's, held in shared memory, so
+// the matrix costs one byte a row.  The same fmaf chain over ascending
+// columns as the record kernel above, so the same bits.
+constexpr int kTypeWords = 256 * 8;
+
+template <int NU, int RUN>
+__global__ void __launch_bounds__(kBlock) pattern_types_f32_kernel(PatternView a, const float* __restrict__ x,
+                                                                   float* __restrict__ y) {
+    __shared__ uint32_t stypes[kTypeWords];
+    __shared__ float sdict[256];
+    __shared__ uint32_t smask[32];
+    for (int i = threadIdx.x; i < a.ntypes * 8; i += blockDim.x) stypes[i] = __ldg(a.rtypes + i);
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sdict[i] = i < a.dict_size ? a.dict32[i] : 0.0f;
+    if (threadIdx.x < 32) smask[threadIdx.x] = threadIdx.x < a.npat ? a.pmask[threadIdx.x] : 0u;
+    __syncthreads();
+    const int64_t r0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    // every lane stays for the warp vote: a lane past the last row reads the
+    // last row's type and returns after the vote
+    const bool valid = r0 < a.n;
+    const int64_t r = valid ? r0 : a.n - 1;
+    uint32_t t = __ldg(a.rtype + r);
+    if (t >= uint32_t(a.ntypes)) {
+        raise_error(a.err, 2);
+        t = 0;
+    }
+    const float* __restrict__ xr = x + r;
+    float acc = 0.0f;
+    const bool dom = __all_sync(0xFFFFFFFFu, !valid || int32_t(t) == a.dom_type);
+    if (!valid) return;
+    if (dom) {
+        // every row of the warp carries the dominant record
+#pragma unroll
+        for (int k = 0; k < NU / RUN; ++k) {
+            const float* __restrict__ p = xr + a.uoff[k * RUN];
+#pragma unroll
+            for (int j = 0; j < RUN; ++j) acc = fmaf(a.dom_v32[k * RUN + j], __ldg(p + j), acc);
+        }
+        y[r] = acc;
+        return;
+    }
+    uint32_t w[kMaxRecordWords];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) w[k] = stypes[t * 8 + k];
+    const uint32_t pat = byte_of(w, NU);
+    if (pat >= uint32_t(a.npat)) raise_error(a.err, 1);
+    const uint32_t mask = smask[pat & 31];
+#pragma unroll
+    for (int k = 0; k < NU / RUN; ++k) {
+        const float* __restrict__ p = xr + a.uoff[k * RUN];
+#pragma unroll
+        for (int j = 0; j < RUN; ++j) {
+            const int u = k * RUN + j;
+            if ((mask >> u) & 1u) acc = fmaf(sdict[byte_of(w, u)], __ldg(p + j), acc);
+        }
+    }
+    y[r] = acc;
+}
+
+cudaError_t launch_pattern_types_f32(const PatternView& a, const float* x, float* y, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    // the 27-slot union of a 3-D grid stencil, nine runs of three columns
+    if (a.words != 7 || a.nu != 27 || a.run_len != 3 || !a.rtype || !a.rtypes || a.ntypes < 1 || a.ntypes > 256 ||
+        a.dict_size > 256)
+        return cudaErrorNotSupported;
+    pattern_types_f32_kernel<27, 3><<<grid_of(a.n), kBlock, 0, s>>>(a, x, y);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pattern_col_f32(const PatternView& a, const float* x, float* y, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.run_len == 3 && a.nu == 27) {

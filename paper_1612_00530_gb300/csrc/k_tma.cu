@@ -46,128 +46,12 @@ namespace spmvc {
 namespace {
 
 #include "fast_fixed.cuh"
+#include "tma_ptx.cuh"
 
 constexpr int kSlotElems = 2048;                // elements a ring slot holds (16 KB)
 constexpr int kRawStages = 2;
 constexpr int kRecStages = 3;
 constexpr int kMaxBlockRows = 1536;             // C
-constexpr int32_t kErrWaitTimeout = 16;
-constexpr long long kWaitCycles = 2000000000LL; // about one second at 2 GHz
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
-}
-
-// Waits until the phase of `bar` with the given parity has completed; false
-// when that has not happened within kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = saddr(bar);
-    uint32_t done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    const long long t0 = clock64();
-    do {
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
-            : "=r"(done)
-            : "r"(a), "r"(parity), "r"(20000u)
-            : "memory");
-        if (done) return true;
-    } while (clock64() - t0 < kWaitCycles);
-    return false;
-}
-
-// Orders this thread's generic-proxy shared-memory accesses before later
-// async-proxy (TMA, bulk copy) accesses of the same memory.
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(saddr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(bar))
-        : "memory");
-}
-
-// Streams that are read once (the row records) are marked evict-first in L2
-// so that x, read by neighbouring blocks too, stays there.
-__device__ __forceinline__ uint64_t evict_first_policy() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(saddr(dst)),
-        "l"(src), "r"(bytes), "r"(saddr(bar)), "l"(policy)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
-}
-
-// Barrier 1 over the n compute threads only (the producer warp never joins).
-__device__ __forceinline__ void compute_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
-
-// The same barrier, returning whether any of the n threads passed true.
-__device__ __forceinline__ bool compute_sync_or(int n, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{ .reg .pred pi, po; setp.ne.u32 pi, %1, 0; bar.red.or.pred po, 1, %2, pi; selp.u32 %0, 1, 0, po; }"
-        : "=r"(r)
-        : "r"(uint32_t(v)), "r"(n)
-        : "memory");
-    return r != 0;
-}
-
-// A CTA's share of the (block, plane) sequence, visited block-major, as
-// runs of planes z0 .. z1-1 of one column block.  A run costs its planes
-// plus about kRunCost steps of start-up, so each block counts kRunCost
-// more units than it has planes (the start-up of the run that begins it)
-// and the CTAs take equal ranges of those units: a CTA whose range crosses
-// a block boundary gets fewer planes.
-constexpr int kRunCost = 2;
-struct Share {
-    int64_t u, uend;      // units of this CTA still to visit: [u, uend)
-    int nzr, z_lo;
-    __device__ bool next(int& b, int& z0, int& z1) {
-        const int per = nzr + kRunCost;
-        while (u < uend) {
-            b = int(u / per);
-            const int o0 = int(u - int64_t(b) * per);
-            const int o1 = int(min(uend - int64_t(b) * per, int64_t(per)));
-            u = int64_t(b) * per + o1;
-            // unit offsets 0 .. kRunCost-1 of a block stand for its start-up
-            const int p0 = max(o0 - kRunCost, 0), p1 = max(o1 - kRunCost, 0);
-            if (p1 > p0) {
-                z0 = z_lo + p0;
-                z1 = z_lo + p1;
-                return true;
-            }
-        }
-        return false;
-    }
-};
 
 // A compute thread sums a tile of TY grid lines by four columns (K = 4 TY
 // rows).  A ring slot holds four sub-arrays, sub-array s the window elements
@@ -599,6 +483,39 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
+// The record each boundary class of grid position implies (64 classes: two
+// bits a dimension, bit 0 set when the lower neighbour is inside the grid,
+// bit 1 the upper): the dominant record's codes at the in-grid slots, the
+// absent code elsewhere, and the pattern number of that slot set; all ones
+// (never a record) for a class no row has.
+void expected_records(const PatternFormat& p, const PatternView& v, std::vector<uint32_t>* out) {
+    std::vector<uint32_t> tab(64 * 8, 0xFFFFFFFFu);
+    const uint32_t absent = uint32_t(p.dict.size());
+    for (int cls = 0; cls < 64; ++cls) {
+        const int c[3] = {cls & 3, (cls >> 2) & 3, (cls >> 4) & 3};   // x, y, z
+        uint32_t mask = 0;
+        for (int u = 0; u < 27; ++u) {
+            const int d[3] = {u % 3 - 1, (u / 3) % 3 - 1, u / 9 - 1};
+            bool present = true;
+            for (int k = 0; k < 3; ++k)
+                if ((d[k] == -1 && !(c[k] & 1)) || (d[k] == 1 && !(c[k] & 2))) present = false;
+            if (present) mask |= 1u << u;
+        }
+        int pn = -1;
+        for (size_t i = 0; i < p.pmask.size(); ++i)
+            if (p.pmask[i] == mask) pn = int(i);
+        if (pn < 0) continue;   // no row of this class exists: the table entry never matches
+        uint8_t bytes[32] = {};
+        for (int u = 0; u < 27; ++u)
+            bytes[u] = (mask >> u) & 1u ? uint8_t((v.dom_w[u >> 2] >> (8 * (u & 3))) & 0xFFu) : uint8_t(absent);
+        bytes[27] = uint8_t(pn);
+        for (int k = 0; k < 8; ++k)
+            tab[cls * 8 + k] = uint32_t(bytes[4 * k]) | uint32_t(bytes[4 * k + 1]) << 8 |
+                               uint32_t(bytes[4 * k + 2]) << 16 | uint32_t(bytes[4 * k + 3]) << 24;
+    }
+    *out = std::move(tab);
+}
+
 bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
                    std::vector<uint32_t>* expected) {
     if (ty != 1 && ty != 2) return false;
@@ -645,31 +562,8 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
     t.off_mbar = t.off_words + 64;
     t.smem_bytes = int32_t(up(t.off_mbar + 8 * 2 * (kRawStages + kRecStages), 128));
     if (t.smem_bytes > 227 * 1024) return false;
-    // the record each boundary class of grid position implies
-    std::vector<uint32_t> tab(64 * 8, 0xFFFFFFFFu);
-    const uint32_t absent = uint32_t(p.dict.size());
-    for (int cls = 0; cls < 64; ++cls) {
-        const int c[3] = {cls & 3, (cls >> 2) & 3, (cls >> 4) & 3};   // x, y, z
-        uint32_t mask = 0;
-        for (int u = 0; u < 27; ++u) {
-            const int d[3] = {u % 3 - 1, (u / 3) % 3 - 1, u / 9 - 1};
-            bool present = true;
-            for (int k = 0; k < 3; ++k)
-                if ((d[k] == -1 && !(c[k] & 1)) || (d[k] == 1 && !(c[k] & 2))) present = false;
-            if (present) mask |= 1u << u;
-        }
-        int pn = -1;
-        for (size_t i = 0; i < p.pmask.size(); ++i)
-            if (p.pmask[i] == mask) pn = int(i);
-        if (pn < 0) continue;   // no row of this class exists: the table entry never matches
-        uint8_t bytes[32] = {};
-        for (int u = 0; u < 27; ++u)
-            bytes[u] = (mask >> u) & 1u ? uint8_t((v.dom_w[u >> 2] >> (8 * (u & 3))) & 0xFFu) : uint8_t(absent);
-        bytes[27] = uint8_t(pn);
-        for (int k = 0; k < 8; ++k)
-            tab[cls * 8 + k] = uint32_t(bytes[4 * k]) | uint32_t(bytes[4 * k + 1]) << 8 |
-                               uint32_t(bytes[4 * k + 2]) << 16 | uint32_t(bytes[4 * k + 3]) << 24;
-    }
+    std::vector<uint32_t> tab;
+    expected_records(p, v, &tab);
     *out = t;
     *expected = std::move(tab);
     return true;

@@ -77,15 +77,39 @@ int compress_pattern(const Csr& a, int max_dict, PatternFormat* out);
 void derive_fast_order(int64_t n, PatternFormat* p);
 
 // -------------------------------------------------------------- delta ----
-enum : uint32_t { kSliceValRaw = 1u, kSliceColRaw = 2u };
+// Per slice, one column encoding (int16 delta col-row by default, 24-bit
+// delta, or raw int32 column) and one value encoding (uint8 code into the
+// global table by default; codes into the global table and, from its size
+// up, into a table of the slice's own values; or raw double).
+enum : uint32_t { kSliceValRaw = 1u, kSliceColRaw = 2u, kSliceCol24 = 4u, kSliceValLocal = 8u };
 struct DeltaSlice {                 // 16 bytes, one per 32-row slice
     uint64_t off;                   // byte offset of the slice payload
     uint32_t w;                     // slots per row
-    uint32_t flags;                 // kSliceValRaw | kSliceColRaw
+    uint32_t flags;                 // kSlice* bits
 };
-// Slice payload (each part 16-byte aligned): row lengths uint8[32]; columns
-// (int16 delta col-row, or int32) [w][32]; values (uint8 code, or double)
-// [w][32].
+// Slice payload, each part 16-byte aligned:
+//   row lengths uint8[32];
+//   columns [w][32]: int16 delta (col - row), or int32 column (ColRaw), or
+//     (Col24) the low 16 bits of a 24-bit delta as int16 followed by an
+//     int8 plane [w][32] of its high bits: delta = hi * 65536 + (uint16)lo;
+//   values [w][32]: uint8 codes, or doubles (ValRaw); with ValLocal a code
+//     c >= |global table| names entry c - |global table| of the slice's own
+//     table: a uint32 count (padded to 16 bytes), then that many doubles.
+struct DeltaParts {
+    uint64_t cols, hi, vals, local;   // byte offsets inside the slice payload
+};
+__host__ __device__ inline uint64_t delta_up16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
+__host__ __device__ inline DeltaParts delta_parts(uint32_t w, uint32_t flags) {
+    const uint64_t slots = uint64_t(w) * 32;
+    DeltaParts p;
+    p.cols = 32;
+    uint64_t o = delta_up16(32 + slots * ((flags & kSliceColRaw) ? 4 : 2));
+    p.hi = o;
+    if (flags & kSliceCol24) o = delta_up16(o + slots);
+    p.vals = o;
+    p.local = delta_up16(o + slots * ((flags & kSliceValRaw) ? 8 : 1));
+    return p;
+}
 struct DeltaFormat {
     std::vector<double> dict;
     int64_t nslices = 0;
@@ -176,6 +200,7 @@ struct PatternView {
     const uint8_t* rtype;
     const uint32_t* rtypes;
     int32_t ntypes;
+    int32_t dom_type;               // the type number of the dominant record (-1: none)
     int32_t* err;                   // sticky device error word
 };
 
@@ -298,6 +323,39 @@ struct TmaPlan {
     int32_t smem_bytes;
     const uint32_t* expected;       // device copy of the 64 x 8-word table
 };
+// FAST-order SpMM fed by TMA (k_tma_spmm.cu): blocks of L lines by W
+// columns of a plane, kc right-hand sides a pass, a compute thread a tile of
+// four rows of a line for one column.
+struct TmaSpmmPlan {
+    int32_t nx, ny, nz;
+    int32_t L, W, C, kc, threads;   // block lines and columns, rows (L*W), columns a pass, C/4*kc threads
+    int32_t pitch, win_elems;       // W + 4, (L + 2) * pitch
+    int32_t nbx, nby, nblk;         // blocks across a line, down a plane, in a plane
+    int32_t ctas;                   // CTAs an SM (1 to 3; a step has at most 1536 / ctas outputs)
+    int32_t grid;                   // persistent CTAs at most (the SM count times ctas)
+    int64_t S;                      // plane stride nx*ny
+    int32_t sub, col_bytes;         // converted window: a column's 4 sub-arrays of `sub` int2 (padded)
+    // dynamic shared memory: 2 converted windows (kc columns each) at 0, then
+    int32_t off_raw, raw_bytes;     // 2 raw window stages
+    int32_t off_rec;                // 3 record stages of 28*C bytes
+    int32_t off_exp;                // 64 expected records x 8 words
+    int32_t off_flags;              // 3 x C/32 words of per-row match bits
+    int32_t off_words;              // per-column exponent words, abort and producer words
+    int32_t off_mbar;
+    int32_t smem_bytes;
+    const uint32_t* expected;       // device copy of the 64 x 8-word table
+};
+bool make_tma_spmm_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int kc, int ctas,
+                        TmaSpmmPlan* out);
+// Y = A X with the plan's kernel, ceil(k / kc) passes; cudaErrorNotSupported
+// (nothing launched) when X is not 16-byte aligned, ldx is odd (the 4-D
+// tensor view needs both) or k < kc.
+cudaError_t launch_pattern_spmm_tma(const PatternView& a, const TmaSpmmPlan& tp, int k, const double* X, int64_t ldx,
+                                    double* Y, int64_t ldy, cudaStream_t s);
+
+// The record each boundary class of grid position implies, 64 classes x 8
+// words (the TMA-fed kernels compare every row's record with it).
+void expected_records(const PatternFormat& p, const PatternView& v, std::vector<uint32_t>* out);
 // Builds the plan and the expected-record table (64 classes x 8 words);
 // false when the matrix or its grid has no compiled shape for variant 11.
 bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
@@ -340,6 +398,8 @@ cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double*
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s);
+// binary32 product from the one-byte row types (pattern format, 7-word records)
+cudaError_t launch_pattern_types_f32(const PatternView& a, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_data_table_f64(const DataTableView& a, const double* x, double* y, cudaStream_t s);
 // k_check.cu: *out = max |x_j| as bits (atomicMax; *out zeroed by the
 // caller); *bad += count of i with |y_i - yref_i| > abs_tol + rel_tol |yref_i|
@@ -418,6 +478,12 @@ struct spmv_mat_s {
     bool zbplan_ok = false;
     spmvc::TmaPlan tplan{};            // FAST order, TMA z-marching kernel (variant 11)
     bool tplan_ok = false;
+    // FAST order, TMA SpMM: [4 or 8 columns a pass][1 to 3 CTAs an SM]
+    spmvc::TmaSpmmPlan splan[2][3]{};
+    bool splan_ok[2][3] = {};
+    int32_t spmm_kind = 1;             // 0 per-(row, column) kernel, 1 to 3: TMA kernel, CTAs an SM
+    bool f32_types = true;             // binary32 products may read the row types
+    bool types_failed = false;         // more than 256 distinct records: no row types
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;
     int32_t num_sms = 0;

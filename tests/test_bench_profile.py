@@ -14,7 +14,7 @@ def test_profiled_figures_follow_the_source_hash(tmp_path, monkeypatch):
         "traffic: kernel=k2 source_sha256_16=fedcba9876543210 bytes=789\n"
         f"traffic: kernel=k3 source_sha256_16={h} bytes=not-a-number\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda kernel="": h)
     assert bench.profiled_traffic("k1") == 123.0
     assert bench.profiled("k1", "issue", "warp_inst") == 456.0
     assert bench.profiled_traffic("k2") is None          # taken on another source

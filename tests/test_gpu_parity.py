@@ -189,6 +189,41 @@ def test_binary32_rows_off_the_dominant_record():
         assert P.spmv_device_error(M) == 0
 
 
+def test_binary32_row_types_and_records():
+    """The binary32 product from the one-byte row types (at most 256 distinct
+    records) and, for a matrix with more distinct records, from the records
+    themselves: both bit-equal to the binary32 CSR oracle."""
+    g = (24, 20, 18)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    x32 = spmv_inputs.uniform_vector(n, seed=32).astype(np.float32)
+    M = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern")
+    x = torch.from_numpy(x32).cuda()
+    y = torch.full_like(x, float("nan"))
+    P.spmv_apply_f32(M, x, y)
+    torch.cuda.synchronize()
+    assert P.spmv_info(M)["row_types"] == 27
+    assert np.array_equal(y.cpu().numpy(), oracle.spmv_f32(rowptr, col, val, x32))
+    P.spmv_set_f32_kernel(M, 0)                 # the records kernel: the same bits
+    y.fill_(float("nan"))
+    P.spmv_apply_f32(M, x, y)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), oracle.spmv_f32(rowptr, col, val, x32))
+    P.spmv_set_f32_kernel(M, 1)
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_f32_kernel(M, 2)
+    # off-diagonals drawn from three values: thousands of distinct records
+    rng = np.random.default_rng(5)
+    v2 = np.where(val == 26.0, 26.0, rng.choice([-1.0, -0.5, -0.25], size=len(val)))
+    M2 = P.spmv_compress(P.spmv_build_csr(rowptr, col, v2), format="pattern")
+    y.fill_(float("nan"))
+    P.spmv_apply_f32(M2, x, y)
+    torch.cuda.synchronize()
+    assert P.spmv_info(M2)["row_types"] == 0
+    assert np.array_equal(y.cpu().numpy(), oracle.spmv_f32(rowptr, col, v2, x32))
+    assert P.spmv_device_error(M) == 0 and P.spmv_device_error(M2) == 0
+
+
 def test_config2_192cubed_sampled():
     """192^3 HPCG, x ~ U[-1,1) seed 1, in the launch configuration the
     benchmark times: ELL and pattern (COLUMN) bit-exact and pattern FAST
@@ -726,6 +761,141 @@ def test_fast_spmm_preconverted_block(k):
     P.spmm_apply(C, X2, Y2)
     torch.cuda.synchronize()
     check_fast(Y2.cpu().numpy()[:, 0], Y_ref[:, 0], scale[:, 0])
+
+
+def spmm_fast_check(rowptr, col, val, X_np, Yh, whole_scale_cols=()):
+    """Every column of a FAST SpMM against the oracle: componentwise 1e-14
+    where sum_j |a_ij x_j| > 0, exact zeros elsewhere; non-finite entries
+    where the oracle has them.  Columns in whole_scale_cols are held only to
+    the header's first bound, sum_j |a_ij| ulp(max_j |x_j|) + ulp(y_i)/2 (plus
+    the oracle's own rounding): a kernel that scales by the whole column's
+    largest exponent promises no more where a row's entries are far below
+    that maximum."""
+    Y_ref = oracle.spmm(rowptr, col, val, X_np)
+    scale = oracle.spmm(rowptr, col, np.abs(val), np.abs(X_np))
+    assert np.array_equal(np.isnan(Yh), np.isnan(Y_ref))
+    assert np.array_equal(Yh[np.isinf(Y_ref)], Y_ref[np.isinf(Y_ref)])
+    for j in range(X_np.shape[1]):
+        fin = np.isfinite(Y_ref[:, j])
+        d = np.abs(Yh[fin, j] - Y_ref[fin, j])
+        sc = scale[fin, j]
+        assert np.all(d[sc == 0] == 0)
+        if j in whole_scale_cols:
+            abs_a = oracle.spmv(rowptr, col, np.abs(val), np.ones(len(rowptr) - 1))[fin]
+            m = np.max(np.abs(X_np[:, j][np.isfinite(X_np[:, j])]))
+            bound = abs_a * np.spacing(m) + np.spacing(np.abs(Yh[fin, j])) + 64 * 2.0 ** -52 * sc
+            assert np.all(d <= bound), j
+        else:
+            assert np.max(d[sc > 0] / sc[sc > 0], initial=0.0) <= TOL, j
+
+
+@pytest.mark.parametrize("g", [(32, 24, 20), (48, 36, 17), (160, 32, 6)])
+@pytest.mark.parametrize("k", [4, 6, 8, 12, 32])
+def test_spmm_tma_kernel(g, k):
+    """The TMA-fed FAST SpMM (4 or 8 columns a pass, a partial last pass):
+    columns of very different ranges, one all zero, one growing plane by
+    plane (its scale rises inside runs), one with an infinity (its runs take
+    the COLUMN order); strided X and Y; the same through the per-(row,
+    column) kernel; no device error."""
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    S = g[0] * g[1]
+    X_np = spmv_inputs.uniform_matrix(n, k, seed=7)
+    for j in range(k):
+        X_np[:, j] *= 10.0 ** (j % 7 - 3)
+    X_np[:, 1] = 0.0
+    X_np[:, 3] *= 4.0 ** (np.arange(n) // S)
+    X_np[n // 2, 2] = np.inf
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    Xw = torch.zeros(n, k + 2, dtype=torch.float64, device="cuda")
+    Xw[:, :k] = torch.from_numpy(X_np).cuda()
+    X = Xw[:, :k]                                 # ldx = k + 2 (even)
+    Yw = torch.full((n, k + 3), float("nan"), dtype=torch.float64, device="cuda")
+    Y = Yw[:, :k]                                 # ldy = k + 3
+    P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    Yh = Y.cpu().numpy()
+    spmm_fast_check(rowptr, col, val, X_np, Yh)
+    assert np.all(np.isnan(Yw[:, k:].cpu().numpy()))      # nothing past column k written
+    assert P.spmv_device_error(C) == 0
+    # X with an odd leading dimension cannot take the 4-D view: the call
+    # takes the per-(row, column) kernel, the same rule
+    Xo = torch.zeros(n, k + 1, dtype=torch.float64, device="cuda")
+    Xo[:, :k] = torch.from_numpy(X_np).cuda()
+    Y2 = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
+    P.spmm_apply(C, Xo[:, :k], Y2)
+    P.spmv_set_spmm_kernel(C, 0)
+    Y3 = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
+    P.spmm_apply(C, X, Y3)
+    P.spmv_set_spmm_kernel(C, 1)
+    torch.cuda.synchronize()
+    # column 3 grows 4x a plane: the per-(row, column) kernel scales it by its
+    # largest entry, so early planes get only the first bound
+    spmm_fast_check(rowptr, col, val, X_np, Y2.cpu().numpy(), whole_scale_cols=(3,))
+    spmm_fast_check(rowptr, col, val, X_np, Y3.cpu().numpy(), whole_scale_cols=(3,))
+    # two and three CTAs an SM (smaller blocks): the same rule
+    for kind in (2, 3):
+        P.spmv_set_spmm_kernel(C, kind)
+        Y4 = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
+        P.spmm_apply(C, X, Y4)
+        torch.cuda.synchronize()
+        spmm_fast_check(rowptr, col, val, X_np, Y4.cpu().numpy())
+    P.spmv_set_spmm_kernel(C, 1)
+    assert P.spmv_device_error(C) == 0
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_spmm_kernel(C, 4)
+
+
+def test_spmm_tma_kernel_exact_bound_and_integer_x():
+    """Per column, the FAST claim of the header (exact sum within
+    sum_j |a_ij| ulp(max|x_j|) + ulp(y_i)/2, checked in rationals), and
+    integer X gives the exact product bit for bit."""
+    g = (32, 24, 6)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    k = 8
+    X_np = spmv_inputs.uniform_matrix(n, k, seed=8)
+    X_np[:, 5] *= 1e-3
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    X = torch.from_numpy(X_np).cuda()
+    Y = torch.empty_like(X)
+    P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    Yh = Y.cpu().numpy()
+    from fractions import Fraction
+    for j in (0, 5):
+        xj = np.ascontiguousarray(X_np[:, j])
+        exact, bound, _ = fast_order_claim(rowptr, col, val, xj)
+        for i in range(n):
+            err = abs(Fraction(float(Yh[i, j])) - exact[i])
+            assert err <= Fraction(float(bound[i])) + Fraction(float(np.spacing(abs(Yh[i, j])))) / 2, (i, j)
+    Xi = np.stack([spmv_inputs.integer_vector(n, seed=60 + j) for j in range(k)], axis=1)
+    X = torch.from_numpy(np.ascontiguousarray(Xi)).cuda()
+    P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    assert np.array_equal(Y.cpu().numpy(), oracle.spmm(rowptr, col, val, Xi))
+
+
+@pytest.mark.parametrize("k", [8, 32])
+def test_spmm_tma_160cubed_sampled(k):
+    """The benchmark's SpMM workload (160^3, X seed 3) through the TMA
+    kernel, on sampled rows of three columns, componentwise 1e-14."""
+    nx = 160
+    n = nx ** 3
+    X_np = spmv_inputs.uniform_matrix(n, k, seed=3)
+    rows = np.random.default_rng(9).integers(0, n, 4000)
+    C = P.spmv_compress(P.spmv_build("hpcg", nx, nx, nx), format="pattern", order="fast")
+    X = torch.from_numpy(X_np).cuda()
+    Y = torch.empty_like(X)
+    P.spmm_apply(C, X, Y)
+    torch.cuda.synchronize()
+    Yh = Y.cpu().numpy()
+    for j in (0, k // 2, k - 1):
+        xj = np.ascontiguousarray(X_np[:, j])
+        ref = oracle.hpcg_spmv_rows(nx, nx, nx, rows, xj)
+        sc = 52.0 * np.abs(xj[rows]) - oracle.hpcg_spmv_rows(nx, nx, nx, rows, np.abs(xj))   # sum_j |a_ij x_j|
+        assert np.max(np.abs(Yh[rows, j] - ref) / sc) <= TOL
+    assert P.spmv_device_error(C) == 0
 
 
 def test_fast_variant_persistent_many_tiles():

@@ -89,10 +89,56 @@ def test_delta_irregular_fallback_fractions():
     got = P.spmv_decompress(C)
     assert np.array_equal(got[0], rp) and np.array_equal(got[1], c)
     assert np.array_equal(got[2].view(np.uint64), v.view(np.uint64))
-    # random renumbering spreads columns: almost every slice needs raw columns
-    assert info["slices_col_raw"] >= 0.9 * info["n_slices"]
-    # 16 levels + 26.0 make the table
+    # random renumbering spreads columns beyond int16: almost every slice
+    # takes 24-bit deltas (n < 2^23, so none needs raw int32 columns)
+    assert info["slices_col24"] >= 0.9 * info["n_slices"] and info["slices_col_raw"] == 0
+    # 16 levels + 26.0 make the table; the unique values of the special rows'
+    # links are escaped entry by entry, so few slices store raw values
     assert info["dict_size"] >= 17
+    assert info["slices_value_raw"] <= 0.05 * info["n_slices"]
+    assert info["format_bytes"] / info["nnz"] < 6.5
+
+
+def test_delta_encodings_round_trip():
+    """Every delta encoding bit-exact through decompress: int16, 24-bit and
+    raw int32 columns (a column 2^23 away from its row), table codes, codes
+    with a few escaped entries, raw values where most entries escape."""
+    n = (1 << 23) + 64
+    rng = np.random.default_rng(3)
+    cols = [np.array([i]) for i in range(n)]
+    # slice 0: row 0 reaches the last column (a delta above 2^23 - 1)
+    cols[0] = np.array([0, n - 1])
+    # slice 1: deltas of +-40000 (24-bit)
+    for i in range(32, 64):
+        cols[i] = np.array([i, i + 40000])
+    # slice 2: int16 deltas
+    for i in range(64, 96):
+        cols[i] = np.unique(np.array([i - 3, i, i + 5]))
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in cols])
+    col = np.concatenate(cols).astype(np.int32)
+    val = np.full(len(col), 2.0)
+    val[col == np.arange(n).repeat(np.diff(rowptr))] = 26.0
+    # slice 3: two entries outside the table (escaped)
+    k3 = rowptr[96]
+    val[k3] = 0.123456789
+    val[k3 + 5] = -7.5e-300
+    # slice 4: every entry a unique value (raw)
+    k4a, k4b = rowptr[128], rowptr[160]
+    val[k4a:k4b] = rng.uniform(-1, 1, k4b - k4a)
+    A = P.spmv_build_csr(rowptr, col, val)
+    C = P.spmv_compress(A, format="delta", min_count=64)
+    info = P.spmv_info(C)
+    assert info["format_name"] == "delta"
+    assert info["slices_col_raw"] == 1 and info["slices_col24"] == 1
+    assert info["slices_value_raw"] == 1
+    got = P.spmv_decompress(C)
+    assert np.array_equal(got[0], rowptr) and np.array_equal(got[1], col)
+    assert np.array_equal(got[2].view(np.uint64), val.view(np.uint64))
+    # and through a stream (every field checked on import)
+    D = P.spmv_import(P.spmv_export(C))
+    got = P.spmv_decompress(D)
+    assert np.array_equal(got[2].view(np.uint64), val.view(np.uint64))
 
 
 def test_round_trip_random_csr_with_signed_zeros():
@@ -278,8 +324,8 @@ def test_data_table_irregular_signed_zeros_and_refusals():
 @pytest.mark.parametrize("g,seed", [((8, 8, 8), 2), ((16, 16, 16), 5)])
 def test_reorder_round_trip_and_locality(g, seed):
     """Locality reordering inside spmv_compress: a permutation, the exact
-    original matrix back from decompress, a narrower band, and fewer
-    raw-value slices than the random numbering gives."""
+    original matrix back from decompress, a narrower band, no more raw-value
+    or wide-column slices and fewer bytes than the random numbering gives."""
     A = P.spmv_build("irregular", *g, seed=seed)
     C0 = P.spmv_compress(A, format="delta")
     C = P.spmv_compress(A, format="delta", reorder=True)
@@ -290,7 +336,8 @@ def test_reorder_round_trip_and_locality(g, seed):
     i0, i1 = P.spmv_info(C0), P.spmv_info(C)
     assert i1["reordered"] == 1 and i0["reordered"] == 0
     assert i1["bandwidth"] < i0["bandwidth"] / 2
-    assert i1["slices_value_raw"] < i0["slices_value_raw"]
+    assert i1["slices_value_raw"] <= i0["slices_value_raw"]
+    assert i1["slices_col24"] + i1["slices_col_raw"] <= i0["slices_col24"] + i0["slices_col_raw"]
     assert i1["format_bytes"] < i0["format_bytes"]
     # the stored matrix is P A P^T: its band is what info reports
     rowptr, col, val = P.spmv_decompress(A)
