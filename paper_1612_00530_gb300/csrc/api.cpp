@@ -762,6 +762,11 @@ int spmv_apply(spmv_mat_t A, const double* x, double* y, spmv_stream_t stream) {
         // reordered: xp = P x, yp = B xp, y = P^T yp
         if ((e = launch_gather(A->d_perm, A->n, x, A->d_xp, s)) != cudaSuccess) return cuda_fail(e, "gather launch");
         x = A->d_xp;
+        if (A->fmt == SPMV_FMT_DELTA) {   // the scatter folded into the product
+            if ((e = launch_delta_f64_scatter(A->dlt_view, x, y, A->d_perm, s)) != cudaSuccess)
+                return cuda_fail(e, "spmv launch");
+            return SPMV_OK;
+        }
         double* const y_user = y;
         y = A->d_yp;
         st = apply_stored(A, x, y, s);

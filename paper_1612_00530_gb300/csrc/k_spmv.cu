@@ -1401,7 +1401,12 @@ __device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, 
     const DeltaParts pt = delta_parts(w, flags);
     const double* local = reinterpret_cast<const double*>(base + pt.local) + 2;   // after its 16-byte count
     T acc = T(0);
-    for (int t = 0; t < len; ++t) {
+    // the slice's full width, the same for every lane of the warp, so the
+    // loop unrolls and independent loads overlap; a lane's slots past its
+    // row's length (zero padding inside the slice) are loaded but skipped
+#pragma unroll 4
+    for (int t = 0; t < int(w); ++t) {
+        const bool on = t < len;
         const int64_t slot = int64_t(t) * 32 + l;
         int64_t c;
         if constexpr (CM == 2) {
@@ -1413,7 +1418,8 @@ __device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, 
             else
                 c = r + lo;
         }
-        T v;
+        bool ok = on;
+        T v = T(0);
         if constexpr (VM == 2) {
             v = T(__ldcs(reinterpret_cast<const double*>(base + pt.vals) + slot));
         } else {
@@ -1421,14 +1427,18 @@ __device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, 
             if (code < uint32_t(a.dict_size)) {
                 v = sdict[code];
             } else if (VM == 1) {
-                v = T(__ldg(local + (code - uint32_t(a.dict_size))));
+                if (on) v = T(__ldg(local + (code - uint32_t(a.dict_size))));
             } else {
-                raise_error(a.err, 2);
-                continue;
+                if (on) raise_error(a.err, 2);
+                ok = false;
             }
         }
-        if (uint64_t(c) >= uint64_t(a.n)) { raise_error(a.err, 2); continue; }
-        acc = fma(v, __ldg(x + c * ldx + j), acc);
+        if (uint64_t(c) >= uint64_t(a.n)) {
+            if (on) raise_error(a.err, 2);
+            ok = false;
+        }
+        const T xv = ok ? __ldg(x + c * ldx + j) : T(0);
+        if (ok) acc = fma(v, xv, acc);
     }
     return acc;
 }
@@ -1448,8 +1458,11 @@ __device__ __forceinline__ T delta_row_any(const DeltaView& a, const uint8_t* ba
     return T(0);
 }
 
+// y[r] = row r, or y[scatter[r]] = row r for a reordered handle (the
+// scatter of P^T folded into the product)
 template <typename T>
-__global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __restrict__ x, T* __restrict__ y) {
+__global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __restrict__ x, T* __restrict__ y,
+                                                     const int32_t* __restrict__ scatter) {
     __shared__ T sdict[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         T v = T(0);
@@ -1469,7 +1482,7 @@ __global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __r
     int len = r < a.n ? int(base[l]) : 0;
     if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
     const T acc = delta_row_any<T>(a, base, h, r, l, len, sdict, x, 1, 0);
-    if (r < a.n) y[r] = acc;
+    if (r < a.n) y[scatter ? int64_t(__ldg(scatter + r)) : r] = acc;
 }
 
 // ------------------------------------------------------------ SpMM -------
@@ -2189,12 +2202,18 @@ cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStr
 
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    delta_kernel<double><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y);
+    delta_kernel<double><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y, nullptr);
     return cudaGetLastError();
 }
 cudaError_t launch_delta_f32(const DeltaView& a, const float* x, float* y, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    delta_kernel<float><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y);
+    delta_kernel<float><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y, nullptr);
+    return cudaGetLastError();
+}
+cudaError_t launch_delta_f64_scatter(const DeltaView& a, const double* x, double* y, const int32_t* perm,
+                                     cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    delta_kernel<double><<<grid_of(a.nslices * 32), kBlock, 0, s>>>(a, x, y, perm);
     return cudaGetLastError();
 }
 cudaError_t launch_pattern_spmm_col(const PatternView& a, int k, const double* X, int64_t ldx, double* Y,

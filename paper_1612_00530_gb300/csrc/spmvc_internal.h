@@ -397,6 +397,9 @@ cudaError_t launch_pattern_fast_async_x(const PatternView& a, const StagePlan& s
 cudaError_t launch_pattern_fast_x(const PatternView& a, const double* x, double* y, uint32_t* partial,
                                   int2* X_guarded, int64_t guard, cudaStream_t s);
 cudaError_t launch_delta_f64(const DeltaView& a, const double* x, double* y, cudaStream_t s);
+// the same writing y[perm[r]] (a reordered handle's product and scatter in one pass)
+cudaError_t launch_delta_f64_scatter(const DeltaView& a, const double* x, double* y, const int32_t* perm,
+                                     cudaStream_t s);
 cudaError_t launch_dit_f64(const DitView& a, const double* x, double* y, cudaStream_t s);
 // binary32 product from the one-byte row types (pattern format, 7-word records)
 cudaError_t launch_pattern_types_f32(const PatternView& a, const float* x, float* y, cudaStream_t s);
