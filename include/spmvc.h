@@ -360,11 +360,14 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
  * for another kind. */
 int spmv_set_spmm_kernel(spmv_mat_t A, int32_t kind);
 
-/* The binary32 product kernel of a pattern-format handle: kind 1 (the
- * default) reads the one-byte row types (values registered in the pattern,
- * Sec. V; built on the first binary32 call, when the matrix has at most 256
- * distinct records), kind 0 the row records.  Both compute the same fmaf
- * chain.  SPMV_EINVAL for another kind. */
+/* The binary32 product kernel of a pattern-format handle.  kind 2 (the
+ * default): for a 27-point grid stencil, the TMA-fed kernel that sums each
+ * row from shared-memory windows of x and reads the one-byte row types
+ * (values registered in the pattern, Sec. V); x must be 16-byte aligned,
+ * else the call takes kind 1.  kind 1: the row types with x read through
+ * L1.  kind 0: the row records.  Row types are built on the first binary32
+ * call, when the matrix has at most 256 distinct records (else kind 0
+ * runs).  All compute the same fmaf chain.  SPMV_EINVAL for another kind. */
 int spmv_set_f32_kernel(spmv_mat_t A, int32_t kind);
 
 /* Y = A X like spmm_apply, for callers that cannot allocate device memory

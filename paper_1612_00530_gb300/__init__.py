@@ -368,8 +368,8 @@ def spmv_set_spmm_kernel(A: SpmvMatrix, kind: int) -> None:
 
 
 def spmv_set_f32_kernel(A: SpmvMatrix, kind: int) -> None:
-    """Binary32 product kernel: 1 the one-byte row types (default), 0 the row
-    records."""
+    """Binary32 product kernel: 2 TMA-fed with row types (default), 1 row
+    types, 0 the row records."""
     _check(library().spmv_set_f32_kernel(A, kind))
 
 

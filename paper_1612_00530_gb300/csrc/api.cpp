@@ -334,6 +334,7 @@ int ensure_device(spmv_mat_s* m) {
             for (int ki = 0; ki < 2; ++ki)
                 for (int c = 0; c < 3; ++c) m->splan[ki][c].expected = table;
         }
+        m->f32plan_ok = make_tma_f32_plan(p, v, m->n, m->num_sms, &m->f32plan);
         if (m->fast_variant == 11 && !m->tplan_ok) m->fast_variant = 1;
         if (m->fast_variant == 7 && !m->zplan_ok) m->fast_variant = 1;
         if (m->fast_variant == 10 && !m->zbplan_ok) m->fast_variant = 1;
@@ -527,6 +528,23 @@ bool ensure_row_types(spmv_mat_s* A) {
                 A->pat_view.dom_type = t;
                 break;
             }
+    // the type of the record each boundary class of grid position implies
+    // (the binary32 TMA kernel's fast rows)
+    for (int c = 0; c < 64; ++c) A->f32plan.exp_type[c] = -1;
+    // (an out-of-grid slot adds its value times a zero, a no-op only for a
+    // finite value)
+    bool dom_finite = A->pat_view.dom_ok != 0;
+    for (int u = 0; u < A->pat_view.nu && dom_finite; ++u) dom_finite = std::isfinite(A->pat_view.dom_v32[u]);
+    if (A->f32plan_ok && dom_finite) {
+        std::vector<uint32_t> tab;
+        expected_records(A->pat, A->pat_view, &tab);
+        for (int c = 0; c < 64; ++c)
+            for (int32_t t = 0; t < A->pat_view.ntypes; ++t)
+                if (std::equal(A->pat.rtypes.begin() + t * 8, A->pat.rtypes.begin() + t * 8 + 7, tab.begin() + c * 8)) {
+                    A->f32plan.exp_type[c] = int16_t(t);
+                    break;
+                }
+    }
     return true;
 }
 
@@ -915,8 +933,11 @@ int spmv_apply_f32(spmv_mat_t A, const float* x, float* y, spmv_stream_t stream)
         // matrix has at most 256 distinct records
         int st = ensure_device(A);
         if (st) return st;
-        if (A->f32_types && ensure_row_types(A)) {
-            const cudaError_t e = launch_pattern_types_f32(A->pat_view, x, y, as_stream(stream));
+        if (A->f32_kind >= 1 && ensure_row_types(A)) {
+            cudaError_t e = cudaErrorNotSupported;
+            if (A->f32_kind == 2 && A->f32plan_ok)
+                e = launch_pattern_f32_tma(A->pat_view, A->f32plan, x, y, as_stream(stream));
+            if (e == cudaErrorNotSupported) e = launch_pattern_types_f32(A->pat_view, x, y, as_stream(stream));
             if (e == cudaSuccess) return SPMV_OK;
             if (e != cudaErrorNotSupported) return cuda_fail(e, "spmv_f32 launch");
         }
@@ -1137,8 +1158,8 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
 
 int spmv_set_f32_kernel(spmv_mat_t A, int32_t kind) {
     if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
-    if (kind != 0 && kind != 1) return fail(SPMV_EINVAL, "binary32 kernel kind must be 0 or 1");
-    A->f32_types = kind == 1;
+    if (kind < 0 || kind > 2) return fail(SPMV_EINVAL, "binary32 kernel kind must be 0, 1 or 2");
+    A->f32_kind = kind;
     return SPMV_OK;
 }
 
@@ -1290,7 +1311,7 @@ int api_ensure_device(spmv_mat_s* m) { return ensure_device(m); }
 // the one-byte row types (built on the host once).
 int api_prepare_f32(spmv_mat_s* m) {
     const int st = ensure_device(m);
-    if (st == SPMV_OK && m->fmt == SPMV_FMT_PATTERN && m->perm.empty() && m->f32_types) ensure_row_types(m);
+    if (st == SPMV_OK && m->fmt == SPMV_FMT_PATTERN && m->perm.empty() && m->f32_kind >= 1) ensure_row_types(m);
     return st;
 }
 bool api_valid(spmv_mat_t m) { return valid(m); }

@@ -353,6 +353,25 @@ bool make_tma_spmm_plan(const PatternFormat& p, const PatternView& v, int64_t n,
 cudaError_t launch_pattern_spmm_tma(const PatternView& a, const TmaSpmmPlan& tp, int k, const double* X, int64_t ldx,
                                     double* Y, int64_t ldy, cudaStream_t s);
 
+// Binary32 product fed by TMA (k_tma_f32.cu): blocks of L lines (a multiple
+// of four), a compute thread four vertically consecutive rows of a column,
+// the rows' one-byte types copied beside the x windows.
+struct TmaF32Plan {
+    int32_t nx, ny, nz;
+    int32_t L, C, threads;          // block lines, rows (L*nx), compute threads (C/4)
+    int32_t pitch, win_floats;      // nx + 8, (L + 2) * pitch
+    int32_t raw_stride;             // floats between window stages (128-byte multiple)
+    int32_t nblk, grid;             // column blocks a plane, persistent CTAs at most
+    int64_t S;                      // plane stride nx*ny
+    int32_t off_raw, off_types, off_tab, off_tmask, off_dict, off_words, off_mbar, smem_bytes;
+    int16_t exp_type[64];           // the row type whose record a row of each boundary class holds (-1: none)
+};
+bool make_tma_f32_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, TmaF32Plan* out);
+// cudaErrorNotSupported (nothing launched) without row types or when x is
+// not 16-byte aligned.
+cudaError_t launch_pattern_f32_tma(const PatternView& a, const TmaF32Plan& tp, const float* x, float* y,
+                                   cudaStream_t s);
+
 // The record each boundary class of grid position implies, 64 classes x 8
 // words (the TMA-fed kernels compare every row's record with it).
 void expected_records(const PatternFormat& p, const PatternView& v, std::vector<uint32_t>* out);
@@ -485,7 +504,9 @@ struct spmv_mat_s {
     spmvc::TmaSpmmPlan splan[2][3]{};
     bool splan_ok[2][3] = {};
     int32_t spmm_kind = 1;             // 0 per-(row, column) kernel, 1 to 3: TMA kernel, CTAs an SM
-    bool f32_types = true;             // binary32 products may read the row types
+    int32_t f32_kind = 2;              // binary32 kernel: 0 records, 1 row types, 2 TMA-fed with row types
+    spmvc::TmaF32Plan f32plan{};
+    bool f32plan_ok = false;
     bool types_failed = false;         // more than 256 distinct records: no row types
     spmvc::StagePlan async_plan{};     // FAST order, persistent double-buffered kernel (1024-row tiles)
     bool async_ok = false;

@@ -209,9 +209,9 @@ def test_binary32_row_types_and_records():
     P.spmv_apply_f32(M, x, y)
     torch.cuda.synchronize()
     assert np.array_equal(y.cpu().numpy(), oracle.spmv_f32(rowptr, col, val, x32))
-    P.spmv_set_f32_kernel(M, 1)
+    P.spmv_set_f32_kernel(M, 2)
     with pytest.raises(P.SpmvError):
-        P.spmv_set_f32_kernel(M, 2)
+        P.spmv_set_f32_kernel(M, 3)
     # off-diagonals drawn from three values: thousands of distinct records
     rng = np.random.default_rng(5)
     v2 = np.where(val == 26.0, 26.0, rng.choice([-1.0, -0.5, -0.25], size=len(val)))
@@ -222,6 +222,65 @@ def test_binary32_row_types_and_records():
     assert P.spmv_info(M2)["row_types"] == 0
     assert np.array_equal(y.cpu().numpy(), oracle.spmv_f32(rowptr, col, v2, x32))
     assert P.spmv_device_error(M) == 0 and P.spmv_device_error(M2) == 0
+
+
+def test_binary32_tma_kernel_all_row_kinds():
+    """The TMA-fed binary32 product (kind 2) against the binary32 CSR oracle
+    bit for bit, beside kinds 1 and 0: rows of the dominant record, rows
+    with other values (other types), a row holding a column outside its grid
+    box (the previous line's last element: summed from x itself), x with an
+    infinity and a NaN, and x one element into a buffer (no TMA: kind 1)."""
+    g = (32, 32, 20)
+    nx, ny, nz = g
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    val = val.copy()
+    for r in (5, 4000, 4001, 7777, 15000, n - 1):
+        val[rowptr[r] + 1] = -0.5
+    # row r0 at ix = 0 also reads column r0 - 1 (inside the 27 offsets, outside its box)
+    r0 = 3 * nx * ny + 5 * nx
+    rows = []
+    for r in range(n):
+        c = list(col[rowptr[r]:rowptr[r + 1]])
+        v = list(val[rowptr[r]:rowptr[r + 1]])
+        if r == r0:
+            c.insert(c.index(r0), r0 - 1)
+            v.insert(c.index(r0 - 1), -1.0)
+        rows.append((c, v))
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(c) for c, _ in rows])
+    cc = np.concatenate([np.array(c, np.int32) for c, _ in rows])
+    vv = np.concatenate([np.array(v, np.float64) for _, v in rows])
+    M = P.spmv_compress(P.spmv_build_csr(rp, cc, vv), format="pattern")
+    for xs in (spmv_inputs.uniform_vector(n, seed=41), None):
+        if xs is None:
+            xs = spmv_inputs.uniform_vector(n, seed=42)
+            xs[100] = np.inf
+            xs[20000] = np.nan
+        x32 = xs.astype(np.float32)
+        want = oracle.spmv_f32(rp, cc, vv, x32)
+        x = torch.from_numpy(x32).cuda()
+        for kind in (2, 1, 0):
+            P.spmv_set_f32_kernel(M, kind)
+            y = torch.full_like(x, float("nan"))
+            P.spmv_apply_f32(M, x, y)
+            torch.cuda.synchronize()
+            got = y.cpu().numpy()
+            assert np.array_equal(got.view(np.uint32), want.view(np.uint32)) or \
+                np.array_equal(np.isnan(got), np.isnan(want)) and \
+                np.array_equal(got[~np.isnan(want)].view(np.uint32), want[~np.isnan(want)].view(np.uint32)), kind
+    P.spmv_set_f32_kernel(M, 2)
+    xbuf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    xbuf[1:] = x
+    y = torch.full_like(x, float("nan"))
+    P.spmv_apply_f32(M, xbuf[1:], y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(got[~np.isnan(want)].view(np.uint32), want[~np.isnan(want)].view(np.uint32))
+    assert P.spmv_device_error(M) == 0
+    with pytest.raises(P.SpmvError):
+        P.spmv_set_f32_kernel(M, 3)
 
 
 def test_config2_192cubed_sampled():
