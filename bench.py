@@ -330,7 +330,7 @@ def bench_cg(P, torch, dev, A, C, batched=True, one_at_a_time=True):
     P.spmv_apply(A, ones, b)            # ELL, column order: integer sums, exact
     xx = torch.zeros_like(b)
     res = {}
-    for mode, extra in (("fp64", {}), ("ir_fp32", {"inner_max_iter": 200, "inner_tol": 1e-6})):
+    for mode, extra in (("fp64", {}), ("ir_fp32", {"inner_max_iter": 300, "inner_tol": 1e-6})):
         xx.zero_()
         r = P.cg_solve(C, b, xx, tol=1e-10, mode=mode, max_iter=5000, **extra)
         res[mode] = {"seconds": r["seconds"], "iterations": r["iterations"], "outer": r["outer_iterations"],

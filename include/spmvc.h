@@ -419,8 +419,10 @@ typedef struct {
     int32_t mode;          /* SPMV_CG_FP64 or SPMV_CG_IR_FP32 */
     int32_t check_every;   /* host reads the device convergence flag every
                               this many steps (default 16) */
-    int32_t inner_max_iter;/* IR: cap per inner solve (default 200) */
-    double inner_tol;      /* IR: inner relative reduction (default 1e-6) */
+    int32_t inner_max_iter;/* IR: cap per inner solve (default 300) */
+    double inner_tol;      /* IR: inner relative reduction (default 1e-6); an
+                              inner solve stops at the larger of this and
+                              tol / (4 x the current relative residual) */
     int32_t nrhs;          /* right-hand sides solved together (1..32, default 1):
                               b and x are n x nrhs row-major */
     int32_t use_graph;     /* 1 (default): replay captured CUDA graphs */

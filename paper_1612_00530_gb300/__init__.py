@@ -321,7 +321,7 @@ def spmv_apply_batched(mats, xs, ys, stream=None) -> None:
 
 
 def cg_solve(A: SpmvMatrix, b, x, tol: float = 1e-10, max_iter: int = 10000, mode: str = "fp64",
-             check_every: int = 16, inner_max_iter: int = 200, inner_tol: float = 1e-6,
+             check_every: int = 16, inner_max_iter: int = 300, inner_tol: float = 1e-6,
              use_graph: bool = True) -> dict:
     """Solves A x = b; b and x are CUDA float64 of shape (n,) or (n, nrhs)."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]

@@ -1319,16 +1319,36 @@ bool api_valid(spmv_mat_t m) { return valid(m); }
 // y = A x where the caller also has the partial maxima of x's high words
 // (xmax_n words, sign cleared): the TMA kernel then scales by the whole
 // vector's exponent (no rescaling of windows); other kernels ignore them.
+// With dot_part, the kernel that can also writes per-CTA partial sums of
+// x.y there and *dot_n their count; *dot_n = 0 means the caller forms x.y.
 int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xmax_part, int xmax_n,
-                   cudaStream_t s) {
+                   cudaStream_t s, double* dot_part, int* dot_n) {
+    if (dot_n) *dot_n = 0;
     int st = ensure_device(A);
     if (st) return st;
     if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty() && A->fast_variant == 11 &&
         A->tplan_ok && A->n > 0 && x != y) {
-        const cudaError_t e = launch_pattern_fast_tma(A->pat_view, A->tplan, x, y, s, xmax_part, xmax_n);
+        const cudaError_t e =
+            launch_pattern_fast_tma(A->pat_view, A->tplan, x, y, s, xmax_part, xmax_n, dot_part, dot_n);
         if (e == cudaSuccess) return SPMV_OK;
         if (e != cudaErrorNotSupported) return cuda_fail(e, "spmv launch");
     }
     return spmv_apply(A, x, y, s);
+}
+
+// The binary32 product with x.y as above (the TMA-fed kernel only).
+int api_apply_f32_dot(spmv_mat_s* A, const float* x, float* y, cudaStream_t s, double* dot_part, int* dot_n) {
+    if (dot_n) *dot_n = 0;
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    if (A->fmt == SPMV_FMT_PATTERN && A->perm.empty() && A->n > 0 && x && y && x != y && A->f32_kind == 2) {
+        int st = ensure_device(A);
+        if (st) return st;
+        if (ensure_row_types(A) && A->f32plan_ok) {
+            const cudaError_t e = launch_pattern_f32_tma(A->pat_view, A->f32plan, x, y, s, dot_part, dot_n);
+            if (e == cudaSuccess) return SPMV_OK;
+            if (e != cudaErrorNotSupported) return cuda_fail(e, "spmv_f32 launch");
+        }
+    }
+    return spmv_apply_f32(A, x, y, s);
 }
 }  // namespace spmvc

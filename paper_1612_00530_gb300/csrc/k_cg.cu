@@ -9,7 +9,14 @@
 // residual b - A x, its norm and the update x += d in binary64, the inner
 // correction solve A d = r with the binary32 product and binary32 vectors;
 // inner dot products sum 8 products in binary32 and accumulate those chunks
-// in binary64).
+// in binary64, or, where the product forms p.q itself, chunks of 4).
+//
+// A step is three launches: the product q = A p, which also returns
+// per-CTA partial sums of p.q where its kernel can (else a dot kernel
+// follows); r -= alpha q with the partial sums of r.r; and x += alpha p,
+// p = r + beta p, whose last block to finish closes the step (the new r.r,
+// the count, the stopping test).  Eight vector passes a step, none of them
+// for p.q when the product forms it.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -20,12 +27,19 @@ namespace spmvc {
 int api_ensure_device(spmv_mat_s* m);
 bool api_valid(spmv_mat_t m);
 int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xmax_part, int xmax_n,
-                   cudaStream_t s);
+                   cudaStream_t s, double* dot_part, int* dot_n);
+int api_apply_f32_dot(spmv_mat_s* A, const float* x, float* y, cudaStream_t s, double* dot_part, int* dot_n);
 int api_prepare_f32(spmv_mat_s* m);
 
 namespace {
 
-constexpr int kRedBlocks = 1216;   // 8 blocks per SM; partial sums reduced by one warp
+// Streaming kernels: grid-stride loops over a fixed grid that is one wave
+// on 152 SMs (4 blocks of 256 an SM, so up to 64 registers a thread: the
+// unrolled loops keep several 16-byte loads in flight without spilling).
+// A grid larger than what the SMs hold at once would leave a second,
+// partly empty wave at the end of every pass.
+constexpr int kRedPerSm = 4;
+constexpr int kRedBlocks = 152 * kRedPerSm;
 constexpr int kRedThreads = 256;
 
 struct CgState {
@@ -34,10 +48,11 @@ struct CgState {
     double rr0;         // inner: initial r.r
     double bnorm;
     double tol;
+    double alpha;       // the step's alpha (block 0 of the r update writes it)
     int32_t it;         // steps taken
     int32_t max_it;
     int32_t done;
-    int32_t pad;
+    uint32_t closed;    // blocks of the step's last kernel that have finished
 };
 
 // Sum of the kRedBlocks partials by one warp in a fixed order.
@@ -60,143 +75,35 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
     return s;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kRedThreads) dot_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                                          int64_t n, double* __restrict__ partial,
-                                                          const CgState* __restrict__ st) {
-    if (st && st->done) return;
-    __shared__ double sm[32];
-    double s = 0.0, s2 = 0.0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const int64_t n2 = n / 2;
-    const double2* a2 = reinterpret_cast<const double2*>(a);
-    const double2* b2 = reinterpret_cast<const double2*>(b);
-    const bool vec = ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
-    if (vec) {
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2; i += stride) {
-            const double2 u = a2[i], v = b2[i];
-            s = fma(u.x, v.x, s);
-            s2 = fma(u.y, v.y, s2);
-        }
-        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s = fma(a[n - 1], b[n - 1], s);
-    } else {
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) s = fma(a[i], b[i], s);
-    }
-    s = block_sum(s + s2, sm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-// alpha = rr / (p.q); x += alpha p; r -= alpha q; partial sums of r.r
-// (par: the step's parity, which of st->rr2 holds its r.r)
-__global__ void __launch_bounds__(kRedThreads) update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
-                                                                const double* __restrict__ p,
-                                                                const double* __restrict__ q, int64_t n,
-                                                                const double* __restrict__ partial_pq,
-                                                                double* __restrict__ partial_rr,
-                                                                const CgState* __restrict__ st, int par) {
-    if (st->done) return;
-    __shared__ double sm[32];
-    __shared__ double s_alpha;
-    if (threadIdx.x < 32) {
-        const double pq = sum_partials(partial_pq);
-        if (threadIdx.x == 0) s_alpha = st->rr2[par] / pq;
-    }
+// Sum of `count` partials by the whole block in a fixed order, returned to
+// every thread (sm: 33 doubles).
+__device__ __forceinline__ double block_sum_partials(const double* __restrict__ p, int count, double* sm) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += p[i];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) sm[32] = s;
     __syncthreads();
-    const double alpha = s_alpha;
-    double s = 0.0, s2 = 0.0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
-                       reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15u) == 0;
-    if (vec) {
-        const int64_t n2 = n / 2;
-        double2* x2 = reinterpret_cast<double2*>(x);
-        double2* r2 = reinterpret_cast<double2*>(r);
-        const double2* p2 = reinterpret_cast<const double2*>(p);
-        const double2* q2 = reinterpret_cast<const double2*>(q);
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2; i += stride) {
-            double2 xv = x2[i], rv = r2[i];
-            const double2 pv = p2[i], qv = q2[i];
-            xv.x = fma(alpha, pv.x, xv.x);
-            xv.y = fma(alpha, pv.y, xv.y);
-            rv.x = fma(-alpha, qv.x, rv.x);
-            rv.y = fma(-alpha, qv.y, rv.y);
-            x2[i] = xv;
-            r2[i] = rv;
-            s = fma(rv.x, rv.x, s);
-            s2 = fma(rv.y, rv.y, s2);
-        }
-        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-            const int64_t i = n - 1;
-            x[i] = fma(alpha, p[i], x[i]);
-            const double ri = fma(-alpha, q[i], r[i]);
-            r[i] = ri;
-            s = fma(ri, ri, s);
-        }
-    } else {
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
-            x[i] = fma(alpha, p[i], x[i]);
-            const double ri = fma(-alpha, q[i], r[i]);
-            r[i] = ri;
-            s = fma(ri, ri, s);
-        }
-    }
-    s = block_sum(s + s2, sm);
-    if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
+    return sm[32];
 }
 
-// beta = rr_new / rr; p = r + beta p.  Block 0 also closes the step: the
-// new r.r into the other parity's slot, the step count, the history and
-// the convergence flag.  A block that starts after the flag is set skips
-// the update of p, which no later step reads then.
-__global__ void __launch_bounds__(kRedThreads) update_p_kernel(double* __restrict__ p, const double* __restrict__ r,
-                                                               int64_t n, const double* __restrict__ partial_rr,
-                                                               CgState* __restrict__ st, double* __restrict__ hist,
-                                                               int par, uint32_t* __restrict__ pmax) {
-    if (st->done) return;
-    __shared__ double s_beta;
+// True in thread 0 of the block that finishes the kernel last (the others'
+// stores are then all issued); it resets the count for the next launch.
+__device__ __forceinline__ bool last_block(CgState* st) {
+    __syncthreads();
+    if (threadIdx.x != 0) return false;
+    __threadfence();
+    const bool last = atomicAdd(&st->closed, 1u) == gridDim.x - 1;
+    if (last) {
+        __threadfence();
+        st->closed = 0u;
+    }
+    return last;
+}
+
+// Per block, the largest high word of |v| over the values the block wrote
+// (the next product's scale), into pmax[blockIdx.x].
+__device__ __forceinline__ void block_hi_max(uint32_t mx, uint32_t* __restrict__ pmax) {
     __shared__ uint32_t s_mx[32];
-    uint32_t mx = 0u;
-    if (threadIdx.x < 32) {
-        const double rr_new = sum_partials(partial_rr);
-        if (threadIdx.x == 0) {
-            s_beta = rr_new / st->rr2[par];
-            if (blockIdx.x == 0) {
-                st->rr2[par ^ 1] = rr_new;
-                const int32_t it = st->it + 1;
-                st->it = it;
-                const double rel = sqrt(rr_new) / st->bnorm;
-                hist[it] = rel;
-                if (rel <= st->tol || it >= st->max_it) st->done = 1;
-            }
-        }
-    }
-    __syncthreads();
-    const double beta = s_beta;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    if (((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(r)) & 15u) == 0) {
-        const int64_t n2 = n / 2;
-        double2* p2 = reinterpret_cast<double2*>(p);
-        const double2* r2 = reinterpret_cast<const double2*>(r);
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2; i += stride) {
-            double2 pv = p2[i];
-            const double2 rv = r2[i];
-            pv.x = fma(beta, pv.x, rv.x);
-            pv.y = fma(beta, pv.y, rv.y);
-            p2[i] = pv;
-            mx = max(mx, max(uint32_t(__double2hiint(pv.x)) & 0x7FFFFFFFu, uint32_t(__double2hiint(pv.y)) & 0x7FFFFFFFu));
-        }
-        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-            const double pl = fma(beta, p[n - 1], r[n - 1]);
-            p[n - 1] = pl;
-            mx = max(mx, uint32_t(__double2hiint(pl)) & 0x7FFFFFFFu);
-        }
-    } else {
-        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
-            const double pv = fma(beta, p[i], r[i]);
-            p[i] = pv;
-            mx = max(mx, uint32_t(__double2hiint(pv)) & 0x7FFFFFFFu);
-        }
-    }
-    // the block's largest high word of |p| (the next product's scale)
     mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -207,8 +114,171 @@ __global__ void __launch_bounds__(kRedThreads) update_p_kernel(double* __restric
     }
 }
 
+__device__ __forceinline__ uint32_t hi_abs(double v) { return uint32_t(__double2hiint(v)) & 0x7FFFFFFFu; }
+
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) dot_kernel(const double* __restrict__ a,
+                                                                    const double* __restrict__ b, int64_t n,
+                                                                    double* __restrict__ partial,
+                                                                    const CgState* __restrict__ st) {
+    if (st && st->done) return;
+    __shared__ double sm[32];
+    double s = 0.0, s2 = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0) {
+        const int64_t n2 = n / 2;
+        const double2* a2 = reinterpret_cast<const double2*>(a);
+        const double2* b2 = reinterpret_cast<const double2*>(b);
+        for (; i + 3 * stride < n2; i += 4 * stride) {
+            double2 u[4], v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                u[k] = a2[i + k * stride];
+                v[k] = b2[i + k * stride];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s = fma(u[k].x, v[k].x, s);
+                s2 = fma(u[k].y, v[k].y, s2);
+            }
+        }
+        for (; i < n2; i += stride) {
+            const double2 u = a2[i], v = b2[i];
+            s = fma(u.x, v.x, s);
+            s2 = fma(u.y, v.y, s2);
+        }
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) s = fma(a[n - 1], b[n - 1], s);
+    } else {
+        for (; i < n; i += stride) s = fma(a[i], b[i], s);
+    }
+    s = block_sum(s + s2, sm);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// alpha = rr / (p.q) (npq partial sums of p.q); r -= alpha q; partial sums
+// of r.r.  par: the step's parity, which of st->rr2 holds its r.r.
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_r_kernel(double* __restrict__ r, const double* __restrict__ q,
+                                                               int64_t n, const double* __restrict__ partial_pq,
+                                                               int npq, double* __restrict__ partial_rr,
+                                                               CgState* __restrict__ st, int par) {
+    if (st->done) return;
+    __shared__ double sm[33];
+    const double alpha = st->rr2[par] / block_sum_partials(partial_pq, npq, sm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->alpha = alpha;
+    double s = 0.0, s2 = 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(q)) & 15u) == 0) {
+        const int64_t n2 = n / 2;
+        double2* r2 = reinterpret_cast<double2*>(r);
+        const double2* q2 = reinterpret_cast<const double2*>(q);
+        auto one = [&](double2 rv, const double2 qv, int64_t j) {
+            rv.x = fma(-alpha, qv.x, rv.x);
+            rv.y = fma(-alpha, qv.y, rv.y);
+            r2[j] = rv;
+            s = fma(rv.x, rv.x, s);
+            s2 = fma(rv.y, rv.y, s2);
+        };
+        int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+        // four elements in flight a thread: loads first, then the updates
+        for (; i + 3 * stride < n2; i += 4 * stride) {
+            double2 rv[4], qv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                rv[k] = r2[i + k * stride];
+                qv[k] = q2[i + k * stride];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) one(rv[k], qv[k], i + k * stride);
+        }
+        for (; i < n2; i += stride) one(r2[i], q2[i], i);
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            const double ri = fma(-alpha, q[n - 1], r[n - 1]);
+            r[n - 1] = ri;
+            s = fma(ri, ri, s);
+        }
+    } else {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            s = fma(ri, ri, s);
+        }
+    }
+    s = block_sum(s + s2, sm);
+    if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
+}
+
+// beta = rr_new / rr; x += alpha p; p = r + beta p; per block the largest
+// high word of |p|.  The block that finishes last closes the step: the new
+// r.r into the other parity's slot, the step count, the history and the
+// convergence flag (every block has read the flag by then).
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_xp_kernel(double* __restrict__ x, double* __restrict__ p,
+                                                                const double* __restrict__ r, int64_t n,
+                                                                const double* __restrict__ partial_rr,
+                                                                CgState* __restrict__ st, double* __restrict__ hist,
+                                                                int par, uint32_t* __restrict__ pmax) {
+    if (st->done) return;
+    __shared__ double sm[33];
+    const double rr_new = block_sum_partials(partial_rr, kRedBlocks, sm);
+    const double alpha = st->alpha, beta = rr_new / st->rr2[par];
+    uint32_t mx = 0u;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(r)) & 15u) ==
+        0) {
+        const int64_t n2 = n / 2;
+        double2* x2 = reinterpret_cast<double2*>(x);
+        double2* p2 = reinterpret_cast<double2*>(p);
+        const double2* r2 = reinterpret_cast<const double2*>(r);
+        auto one = [&](double2 xv, double2 pv, const double2 rv, int64_t j) {
+            xv.x = fma(alpha, pv.x, xv.x);
+            xv.y = fma(alpha, pv.y, xv.y);
+            pv.x = fma(beta, pv.x, rv.x);
+            pv.y = fma(beta, pv.y, rv.y);
+            x2[j] = xv;
+            p2[j] = pv;
+            mx = max(mx, max(hi_abs(pv.x), hi_abs(pv.y)));
+        };
+        int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+        for (; i + 3 * stride < n2; i += 4 * stride) {
+            double2 xv[4], pv[4], rv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                xv[k] = x2[i + k * stride];
+                pv[k] = p2[i + k * stride];
+                rv[k] = r2[i + k * stride];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) one(xv[k], pv[k], rv[k], i + k * stride);
+        }
+        for (; i < n2; i += stride) one(x2[i], p2[i], r2[i], i);
+        if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+            const double po = p[n - 1];
+            x[n - 1] = fma(alpha, po, x[n - 1]);
+            const double pl = fma(beta, po, r[n - 1]);
+            p[n - 1] = pl;
+            mx = max(mx, hi_abs(pl));
+        }
+    } else {
+        for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
+            const double po = p[i];
+            x[i] = fma(alpha, po, x[i]);
+            const double pl = fma(beta, po, r[i]);
+            p[i] = pl;
+            mx = max(mx, hi_abs(pl));
+        }
+    }
+    block_hi_max(mx, pmax);
+    if (last_block(st)) {
+        st->rr2[par ^ 1] = rr_new;
+        const int32_t it = st->it + 1;
+        st->it = it;
+        const double rel = sqrt(rr_new) / st->bnorm;
+        hist[it] = rel;
+        if (rel <= st->tol || it >= st->max_it) st->done = 1;
+    }
+}
+
 // r = b - q, partial sums of r.r
-__global__ void __launch_bounds__(kRedThreads) residual_kernel(const double* __restrict__ b, const double* __restrict__ q,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) residual_kernel(const double* __restrict__ b, const double* __restrict__ q,
                                                                double* __restrict__ r, int64_t n,
                                                                double* __restrict__ partial) {
     __shared__ double sm[32];
@@ -223,29 +293,20 @@ __global__ void __launch_bounds__(kRedThreads) residual_kernel(const double* __r
 }
 
 // dst = src; pmax (optional): per block, the largest high word of |src|
-__global__ void __launch_bounds__(kRedThreads) copy_kernel(double* __restrict__ dst, const double* __restrict__ src,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) copy_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                            int64_t n, uint32_t* __restrict__ pmax) {
-    __shared__ uint32_t s_mx[32];
     uint32_t mx = 0u;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         const double v = src[i];
         dst[i] = v;
-        mx = max(mx, uint32_t(__double2hiint(v)) & 0x7FFFFFFFu);
+        mx = max(mx, hi_abs(v));
     }
-    if (!pmax) return;
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t v = threadIdx.x < (blockDim.x >> 5) ? s_mx[threadIdx.x] : 0u;
-        v = __reduce_max_sync(0xFFFFFFFFu, v);
-        if (threadIdx.x == 0) pmax[blockIdx.x] = v;
-    }
+    if (pmax) block_hi_max(mx, pmax);
 }
 
 // ---------------------------------------------------- binary32 inner CG ---
 // chunks of 8 products summed in binary32, chunk sums accumulated in binary64
-__global__ void __launch_bounds__(kRedThreads) dot32_kernel(const float* __restrict__ a, const float* __restrict__ b,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) dot32_kernel(const float* __restrict__ a, const float* __restrict__ b,
                                                             int64_t n, double* __restrict__ partial,
                                                             const CgState* __restrict__ st) {
     if (st->done) return;
@@ -271,44 +332,43 @@ __global__ void __launch_bounds__(kRedThreads) dot32_kernel(const float* __restr
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kRedThreads) update_dr32_kernel(float* __restrict__ d, float* __restrict__ r,
-                                                                  const float* __restrict__ p, const float* __restrict__ q,
-                                                                  int64_t n, const double* __restrict__ partial_pq,
-                                                                  double* __restrict__ partial_rr,
-                                                                  const CgState* __restrict__ st, int par) {
+// alpha = rr / (p.q) in binary32 (npq partial sums of p.q); r -= alpha q;
+// partial sums of r.r (chunks of four in binary32)
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_r32_kernel(float* __restrict__ r, const float* __restrict__ q,
+                                                                 int64_t n, const double* __restrict__ partial_pq,
+                                                                 int npq, double* __restrict__ partial_rr,
+                                                                 CgState* __restrict__ st, int par) {
     if (st->done) return;
-    __shared__ double sm[32];
-    __shared__ float s_alpha;
-    if (threadIdx.x < 32) {
-        const double pq = sum_partials(partial_pq);
-        if (threadIdx.x == 0) s_alpha = float(st->rr2[par] / pq);
-    }
-    __syncthreads();
-    const float alpha = s_alpha;
+    __shared__ double sm[33];
+    const float alpha = float(st->rr2[par] / block_sum_partials(partial_pq, npq, sm));
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->alpha = alpha;
     double s = 0.0;
-    // four elements per 16-byte access; chunk sums of r.r in binary32
     const int64_t n4 = n / 4, stride = int64_t(gridDim.x) * blockDim.x;
-    float4* d4 = reinterpret_cast<float4*>(d);
     float4* r4 = reinterpret_cast<float4*>(r);
-    const float4* p4 = reinterpret_cast<const float4*>(p);
     const float4* q4 = reinterpret_cast<const float4*>(q);
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += stride) {
-        float4 dv = d4[i], rv = r4[i];
-        const float4 pv = p4[i], qv = q4[i];
-        dv.x = fmaf(alpha, pv.x, dv.x); dv.y = fmaf(alpha, pv.y, dv.y);
-        dv.z = fmaf(alpha, pv.z, dv.z); dv.w = fmaf(alpha, pv.w, dv.w);
+    auto one = [&](float4 rv, const float4 qv, int64_t j) {
         rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
         rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
-        d4[i] = dv;
-        r4[i] = rv;
+        r4[j] = rv;
         float c = rv.x * rv.x;
         c = fmaf(rv.y, rv.y, c); c = fmaf(rv.z, rv.z, c); c = fmaf(rv.w, rv.w, c);
         s += double(c);
+    };
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 rv[4], qv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            rv[k] = r4[i + k * stride];
+            qv[k] = q4[i + k * stride];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) one(rv[k], qv[k], i + k * stride);
     }
+    for (; i < n4; i += stride) one(r4[i], q4[i], i);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         float c = 0.0f;
         for (int64_t i = n4 * 4; i < n; ++i) {
-            d[i] = fmaf(alpha, p[i], d[i]);
             const float ri = fmaf(-alpha, q[i], r[i]);
             r[i] = ri;
             c = fmaf(ri, ri, c);
@@ -319,46 +379,58 @@ __global__ void __launch_bounds__(kRedThreads) update_dr32_kernel(float* __restr
     if (threadIdx.x == 0) partial_rr[blockIdx.x] = s;
 }
 
-// beta; p = r + beta p.  Block 0 also closes the inner step (r.r into the
-// other parity's slot, the step count, the stopping test), as in the FP64
-// loop.
-__global__ void __launch_bounds__(kRedThreads) update_p32_kernel(float* __restrict__ p, const float* __restrict__ r,
-                                                                 int64_t n, const double* __restrict__ partial_rr,
-                                                                 CgState* __restrict__ st, int par) {
+// beta in binary32; d += alpha p; p = r + beta p.  The block that finishes
+// last closes the inner step (r.r into the other parity's slot, the step
+// count, the stopping test), as in the FP64 loop.
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_dp32_kernel(float* __restrict__ d, float* __restrict__ p,
+                                                                  const float* __restrict__ r, int64_t n,
+                                                                  const double* __restrict__ partial_rr,
+                                                                  CgState* __restrict__ st, int par) {
     if (st->done) return;
-    __shared__ float s_beta;
-    if (threadIdx.x < 32) {
-        const double rr_new = sum_partials(partial_rr);
-        if (threadIdx.x == 0) {
-            s_beta = float(rr_new / st->rr2[par]);
-            if (blockIdx.x == 0) {
-                st->rr2[par ^ 1] = rr_new;
-                const int32_t it = st->it + 1;
-                st->it = it;
-                if (sqrt(rr_new / st->rr0) <= st->tol || it >= st->max_it) st->done = 1;
-            }
-        }
-    }
-    __syncthreads();
-    const float beta = s_beta;
+    __shared__ double sm[33];
+    const double rr_new = block_sum_partials(partial_rr, kRedBlocks, sm);
+    const float alpha = float(st->alpha), beta = float(rr_new / st->rr2[par]);
     const int64_t n4 = n / 4, stride = int64_t(gridDim.x) * blockDim.x;
+    float4* d4 = reinterpret_cast<float4*>(d);
     float4* p4 = reinterpret_cast<float4*>(p);
     const float4* r4 = reinterpret_cast<const float4*>(r);
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += stride) {
-        float4 pv = p4[i];
-        const float4 rv = r4[i];
+    auto one = [&](float4 dv, float4 pv, const float4 rv, int64_t j) {
+        dv.x = fmaf(alpha, pv.x, dv.x); dv.y = fmaf(alpha, pv.y, dv.y);
+        dv.z = fmaf(alpha, pv.z, dv.z); dv.w = fmaf(alpha, pv.w, dv.w);
         pv.x = fmaf(beta, pv.x, rv.x); pv.y = fmaf(beta, pv.y, rv.y);
         pv.z = fmaf(beta, pv.z, rv.z); pv.w = fmaf(beta, pv.w, rv.w);
-        p4[i] = pv;
+        d4[j] = dv;
+        p4[j] = pv;
+    };
+    int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 dv[4], pv[4], rv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            dv[k] = d4[i + k * stride];
+            pv[k] = p4[i + k * stride];
+            rv[k] = r4[i + k * stride];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) one(dv[k], pv[k], rv[k], i + k * stride);
     }
+    for (; i < n4; i += stride) one(d4[i], p4[i], r4[i], i);
     if (blockIdx.x == 0 && threadIdx.x < 4 && n4 * 4 + threadIdx.x < n) {
         const int64_t i = n4 * 4 + threadIdx.x;
-        p[i] = fmaf(beta, p[i], r[i]);
+        const float po = p[i];
+        d[i] = fmaf(alpha, po, d[i]);
+        p[i] = fmaf(beta, po, r[i]);
+    }
+    if (last_block(st)) {
+        st->rr2[par ^ 1] = rr_new;
+        const int32_t it = st->it + 1;
+        st->it = it;
+        if (sqrt(rr_new / st->rr0) <= st->tol || it >= st->max_it) st->done = 1;
     }
 }
 
 // inner start: r32 = r / |r|, p32 = r32, d32 = 0; partial sums of r32.r32
-__global__ void __launch_bounds__(kRedThreads) inner_start_kernel(const double* __restrict__ r, double inv_norm,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) inner_start_kernel(const double* __restrict__ r, double inv_norm,
                                                                   float* __restrict__ r32, float* __restrict__ p32,
                                                                   float* __restrict__ d32, int64_t n,
                                                                   double* __restrict__ partial) {
@@ -386,11 +458,12 @@ __global__ void inner_init_state_kernel(const double* __restrict__ partial, CgSt
         st->it = 0;
         st->max_it = inner_max;
         st->done = rr > 0.0 ? 0 : 1;
+        st->closed = 0u;
     }
 }
 
 // x += scale * d32 (binary64)
-__global__ void __launch_bounds__(kRedThreads) ir_update_kernel(double* __restrict__ x, const float* __restrict__ d32,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) ir_update_kernel(double* __restrict__ x, const float* __restrict__ d32,
                                                                 double scale, int64_t n) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         x[i] = fma(scale, double(d32[i]), x[i]);
@@ -411,19 +484,33 @@ struct ColState {
     double rr[kMaxCols], alpha[kMaxCols], beta[kMaxCols], bnorm[kMaxCols];
     double tol;
     int32_t k, it, max_it, done;
+    int32_t live;   // the current step runs (set by the alpha kernel from done)
+    int32_t pad;
 };
 
 // partial[b*k + j]: block b's sum over its rows of a[r,j]*b[r,j]
-__global__ void __launch_bounds__(kRedThreads) dot_cols_kernel(const double* __restrict__ a, const double* __restrict__ b,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) dot_cols_kernel(const double* __restrict__ a, const double* __restrict__ b,
                                                                int64_t n, int k, double* __restrict__ partial,
                                                                const ColState* __restrict__ st) {
     if (st && st->done) return;
     __shared__ double sm[kRedThreads];
     const int R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
     double s = 0.0;
-    if (sub < R)
-        for (int64_t r = blockIdx.x * int64_t(R) + sub; r < n; r += int64_t(gridDim.x) * R)
-            s = fma(a[r * k + j], b[r * k + j], s);
+    if (sub < R) {
+        const int64_t rs = int64_t(gridDim.x) * R;
+        int64_t r = blockIdx.x * int64_t(R) + sub;
+        for (; r + 3 * rs < n; r += 4 * rs) {   // four rows in flight a thread
+            double u[4], v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                u[c] = a[(r + c * rs) * k + j];
+                v[c] = b[(r + c * rs) * k + j];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s = fma(u[c], v[c], s);
+        }
+        for (; r < n; r += rs) s = fma(a[r * k + j], b[r * k + j], s);
+    }
     sm[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x < k) {
@@ -441,19 +528,22 @@ __device__ __forceinline__ double sum_col_warp(const double* __restrict__ partia
     return s;
 }
 
-// alpha_j = rr_j / (p_j . q_j)
-// one warp per column
+// alpha_j = rr_j / (p_j . q_j), one warp per column; the step runs (live)
+// exactly when the batch had not converged before it
 __global__ void alpha_cols_kernel(const double* __restrict__ partial_pq, ColState* __restrict__ st) {
-    if (st->done) return;
+    if (st->done) {
+        if (threadIdx.x == 0) st->live = 0;
+        return;
+    }
+    if (threadIdx.x == 0) st->live = 1;
     const int j = threadIdx.x >> 5;
     if (j >= st->k) return;
     const double pq = sum_col_warp(partial_pq, st->k, j);
     if ((threadIdx.x & 31) == 0) st->alpha[j] = (st->rr[j] > 0.0 && pq != 0.0) ? st->rr[j] / pq : 0.0;
 }
 
-// x += alpha p; r -= alpha q; partial sums of r.r per column
-__global__ void __launch_bounds__(kRedThreads) update_xr_cols_kernel(double* __restrict__ x, double* __restrict__ r,
-                                                                     const double* __restrict__ p,
+// r -= alpha q; partial sums of r.r per column
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_r_cols_kernel(double* __restrict__ r,
                                                                      const double* __restrict__ q, int64_t n,
                                                                      double* __restrict__ partial_rr,
                                                                      const ColState* __restrict__ st) {
@@ -462,14 +552,30 @@ __global__ void __launch_bounds__(kRedThreads) update_xr_cols_kernel(double* __r
     const int k = st->k, R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
     const double alpha = st->alpha[j];
     double s = 0.0;
-    if (sub < R)
-        for (int64_t row = blockIdx.x * int64_t(R) + sub; row < n; row += int64_t(gridDim.x) * R) {
+    if (sub < R) {
+        const int64_t rs = int64_t(gridDim.x) * R;
+        int64_t row = blockIdx.x * int64_t(R) + sub;
+        for (; row + 3 * rs < n; row += 4 * rs) {
+            double rv[4], qv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                rv[c] = r[(row + c * rs) * k + j];
+                qv[c] = q[(row + c * rs) * k + j];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const double ri = fma(-alpha, qv[c], rv[c]);
+                r[(row + c * rs) * k + j] = ri;
+                s = fma(ri, ri, s);
+            }
+        }
+        for (; row < n; row += rs) {
             const int64_t i = row * k + j;
-            x[i] = fma(alpha, p[i], x[i]);
             const double ri = fma(-alpha, q[i], r[i]);
             r[i] = ri;
             s = fma(ri, ri, s);
         }
+    }
     sm[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x < k) {
@@ -503,17 +609,44 @@ __global__ void beta_cols_kernel(const double* __restrict__ partial_rr, ColState
     }
 }
 
-__global__ void __launch_bounds__(kRedThreads) update_p_cols_kernel(double* __restrict__ p, const double* __restrict__ r,
-                                                                    int64_t n, const ColState* __restrict__ st) {
-    if (st->done) return;
-    const int k = st->k;
-    const int64_t total = n * k, stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += stride)
-        p[i] = fma(st->beta[i % k], p[i], r[i]);
+// x += alpha p; p = r + beta p (a step that ran: the beta kernel may have
+// just set the convergence flag, and x still takes this step's update)
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_xp_cols_kernel(double* __restrict__ x,
+                                                                     double* __restrict__ p,
+                                                                     const double* __restrict__ r, int64_t n,
+                                                                     const ColState* __restrict__ st) {
+    if (!st->live) return;
+    const int k = st->k, R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
+    if (sub >= R) return;
+    const double alpha = st->alpha[j], beta = st->beta[j];
+    const int64_t rs = int64_t(gridDim.x) * R;
+    int64_t row = blockIdx.x * int64_t(R) + sub;
+    for (; row + 3 * rs < n; row += 4 * rs) {
+        double xv[4], pv[4], rv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t i = (row + c * rs) * k + j;
+            xv[c] = x[i];
+            pv[c] = p[i];
+            rv[c] = r[i];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t i = (row + c * rs) * k + j;
+            x[i] = fma(alpha, pv[c], xv[c]);
+            p[i] = fma(beta, pv[c], rv[c]);
+        }
+    }
+    for (; row < n; row += rs) {
+        const int64_t i = row * k + j;
+        const double po = p[i];
+        x[i] = fma(alpha, po, x[i]);
+        p[i] = fma(beta, po, r[i]);
+    }
 }
 
 // r = b - q, partial sums of r.r per column
-__global__ void __launch_bounds__(kRedThreads) residual_cols_kernel(const double* __restrict__ b,
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) residual_cols_kernel(const double* __restrict__ b,
                                                                     const double* __restrict__ q,
                                                                     double* __restrict__ r, int64_t n, int k,
                                                                     double* __restrict__ partial) {
@@ -660,13 +793,13 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
         CG_ST(spmm_apply(A, k, p, k, q, k, s));
         dot_cols_kernel<<<G, T, 0, s>>>(p, q, n, k, part_a, d_st);
         alpha_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, d_st);
-        update_xr_cols_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_b, d_st);
+        update_r_cols_kernel<<<G, T, 0, s>>>(r, q, n, part_b, d_st);
         beta_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_b, d_st, d_hist);
-        update_p_cols_kernel<<<G, T, 0, s>>>(p, r, n, d_st);
+        update_xp_cols_kernel<<<G, T, 0, s>>>(x, p, r, n, d_st);
         CG_CUDA(cudaGetLastError());
         return SPMV_OK;
     };
-    // done flag is the same field position as in CgState? use ColState's own
+    // the columns' loop replays its own graph and polls ColState's flag
     int32_t done = hs.done;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
@@ -738,7 +871,7 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     if (o.tol <= 0) o.tol = 1e-10;
     if (o.max_iter <= 0) o.max_iter = 10000;
     if (o.check_every <= 0) o.check_every = 16;
-    if (o.inner_max_iter <= 0) o.inner_max_iter = 200;
+    if (o.inner_max_iter <= 0) o.inner_max_iter = 300;
     if (o.inner_tol <= 0) o.inner_tol = 1e-6;
     if (o.nrhs <= 0) o.nrhs = 1;
     if (o.nrhs < 1 || o.nrhs > kMaxCols) return fail(SPMV_EINVAL, "nrhs must be 1..32");
@@ -798,7 +931,7 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
     if (o.mode == SPMV_CG_FP64) {
         CG_ST(true_residual());
         const double rr0 = read_scalar(d_scalar, s);
-        CgState h{rr0, {rr0, 0.0}, rr0, bnorm, o.tol, 0, o.max_iter, 0, 0};
+        CgState h{rr0, {rr0, 0.0}, rr0, bnorm, o.tol, 0.0, 0, o.max_iter, 0, 0u};
         h.done = (std::sqrt(rr0) / bnorm <= o.tol) ? 1 : 0;
         CG_CUDA(cudaMemcpyAsync(d_st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
         const double h0 = std::sqrt(rr0) / bnorm;
@@ -810,10 +943,14 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
         int step = 0;
         auto body = [&]() -> int {
             const int par = step++ & 1;
-            CG_ST(api_apply_xmax(A, p, q, pmax, int(G), s));
-            dot_kernel<<<G, T, 0, s>>>(p, q, n, part_a, d_st);
-            update_xr_kernel<<<G, T, 0, s>>>(x, r, p, q, n, part_a, part_b, d_st, par);
-            update_p_kernel<<<G, T, 0, s>>>(p, r, n, part_b, d_st, d_hist, par, pmax);
+            int npq = 0;   // partial sums of p.q the product wrote (0: a dot kernel forms them)
+            CG_ST(api_apply_xmax(A, p, q, pmax, int(G), s, part_a, &npq));
+            if (npq == 0) {
+                dot_kernel<<<G, T, 0, s>>>(p, q, n, part_a, d_st);
+                npq = int(G);
+            }
+            update_r_kernel<<<G, T, 0, s>>>(r, q, n, part_a, npq, part_b, d_st, par);
+            update_xp_kernel<<<G, T, 0, s>>>(x, p, r, n, part_b, d_st, d_hist, par, pmax);
             CG_CUDA(cudaGetLastError());
             return SPMV_OK;
         };
@@ -844,16 +981,24 @@ extern "C" int cg_solve(spmv_mat_t A, const double* b, double* x, const spmv_cg_
             if (rel <= o.tol) { status = SPMV_OK; break; }
             if (total_inner >= o.max_iter) break;
             const double rnorm = std::sqrt(rr);
+            // the inner solve need not reduce its residual by more than a
+            // quarter of what the outer target still asks (tol / rel): the
+            // last one usually stops early
+            const double inner_tol = std::max(o.inner_tol, 0.25 * o.tol / rel);
             inner_start_kernel<<<G, T, 0, s>>>(r, 1.0 / rnorm, r32, p32, d32, n, part_a);
-            inner_init_state_kernel<<<1, 32, 0, s>>>(part_a, d_st, o.inner_tol,
+            inner_init_state_kernel<<<1, 32, 0, s>>>(part_a, d_st, inner_tol,
                                                      std::min(o.inner_max_iter, o.max_iter - total_inner));
             int step = 0;   // parity of r.r's slot, as in the FP64 loop
             auto body = [&]() -> int {
                 const int par = step++ & 1;
-                CG_ST(spmv_apply_f32(A, p32, q32, s));
-                dot32_kernel<<<G, T, 0, s>>>(p32, q32, n, part_a, d_st);
-                update_dr32_kernel<<<G, T, 0, s>>>(d32, r32, p32, q32, n, part_a, part_b, d_st, par);
-                update_p32_kernel<<<G, T, 0, s>>>(p32, r32, n, part_b, d_st, par);
+                int npq = 0;
+                CG_ST(api_apply_f32_dot(A, p32, q32, s, part_a, &npq));
+                if (npq == 0) {
+                    dot32_kernel<<<G, T, 0, s>>>(p32, q32, n, part_a, d_st);
+                    npq = int(G);
+                }
+                update_r32_kernel<<<G, T, 0, s>>>(r32, q32, n, part_a, npq, part_b, d_st, par);
+                update_dp32_kernel<<<G, T, 0, s>>>(d32, p32, r32, n, part_b, d_st, par);
                 CG_CUDA(cudaGetLastError());
                 return SPMV_OK;
             };

@@ -58,12 +58,15 @@ constexpr int kMaxBlockRows = 1536;             // C
 // e with e mod 4 = s at index e / 4: the six elements of a window line a
 // tile reads (its four columns and one each side) are six conflict-free
 // 8-byte loads at constant offsets.  Threads 0 .. C/K-1 compute; the last
-// warp is the producer.
-template <int TY>
+// warp is the producer.  With DOT the kernel also forms x.y (the p.q of a
+// CG step, Sec. II): every thread adds x[row]*y[row] of the rows it stores,
+// in binary64 in its own order, and the CTA's sum of those goes to
+// dot_part[blockIdx.x].
+template <int TY, bool DOT>
 __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
     pattern_fast_tma_kernel(const __grid_constant__ CUtensorMap xmap, const PatternView a, const TmaPlan tp,
                             const double* __restrict__ x, double* __restrict__ y,
-                            const uint32_t* __restrict__ xmax_part, int xmax_n) {
+                            const uint32_t* __restrict__ xmax_part, int xmax_n, double* __restrict__ dot_part) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int K = 4 * TY;                          // rows a compute thread
     constexpr int SUB = kSlotElems / 4;
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
     uint32_t nraw = 0, nrec = 0;   // windows / record planes consumed so far
     uint32_t it = 0;               // loop steps so far
     bool aborted = false;
+    double dacc = 0.0;             // this thread's part of x.y (DOT)
     // this thread's rows of the plane checked last step / this step had a
     // record off its expected one
     bool exc_now = false, exc_next = false;
@@ -244,6 +248,22 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
             const int j = w - z0 + 1;   // index of W(w) within this run: ring slot j & 3
             bool wait_ok = true;
             bool raises = false;        // this thread's part of W(w) raises the scale
+            const int q = w - 2;        // the plane summed this step
+            const bool have_q = q >= z0 && q < z1;
+            // x at the tile's rows of plane q, loaded now for x.y at the
+            // step's end (the window holds them in fixed point only)
+            double2 pv[TY][2];
+            if constexpr (DOT) {
+                if (have_q) {
+                    const double2* xr = reinterpret_cast<const double2*>(x + int64_t(q) * tp.S + blk0 +
+                                                                         int64_t(TY * ctl) * nx + cix);
+#pragma unroll
+                    for (int ry = 0; ry < TY; ++ry) {
+                        pv[ry][0] = __ldg(xr + int64_t(ry) * (nx >> 1));
+                        pv[ry][1] = __ldg(xr + int64_t(ry) * (nx >> 1) + 1);
+                    }
+                }
+            }
             exc_now = exc_next;
             exc_next = false;
             if (tid == 0) {
@@ -305,8 +325,6 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
             }
             // ---- sum the rows of plane q = w-2 and store those whose record
             // is the expected one
-            const int q = w - 2;
-            const bool have_q = q >= z0 && q < z1;
             const bool fast_q = E_true >= 64u && E_true < 2047u;
             if (have_q) {
                 const int64_t trow0 = int64_t(q) * tp.S + blk0 + int64_t(TY * ctl) * nx + cix;   // tile's first row
@@ -373,10 +391,22 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
                         if (mbits == 15u) {
                             reinterpret_cast<double2*>(yr)[0] = make_double2(o[0], o[1]);
                             reinterpret_cast<double2*>(yr)[1] = make_double2(o[2], o[3]);
+                            if constexpr (DOT) {
+                                dacc = fma(pv[ry][0].x, o[0], dacc);
+                                dacc = fma(pv[ry][0].y, o[1], dacc);
+                                dacc = fma(pv[ry][1].x, o[2], dacc);
+                                dacc = fma(pv[ry][1].y, o[3], dacc);
+                            }
                         } else {
 #pragma unroll
                             for (int rx = 0; rx < 4; ++rx)
-                                if ((mbits >> rx) & 1u) yr[rx] = o[rx];
+                                if ((mbits >> rx) & 1u) {
+                                    yr[rx] = o[rx];
+                                    if constexpr (DOT) {
+                                        const double2 h = pv[ry][rx >> 1];
+                                        dacc = fma((rx & 1) ? h.y : h.x, o[rx], dacc);
+                                    }
+                                }
                         }
                     }
                 } else {
@@ -394,6 +424,7 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
                             if ((mask >> uu) & 1u)
                                 acc = fma(__ldg(a.dict + (byte_of(w7, uu) & 7)), __ldg(x + row + a.uoff[uu]), acc);
                         y[row] = acc;
+                        if constexpr (DOT) dacc = fma(__ldg(x + row), acc, dacc);
                     }
                 }
             }
@@ -432,7 +463,9 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
                             ah += int64_t(m8) * xh;
                             al += int64_t(m8) * xl;
                         }
-                    y[row] = fixed_to_double(ah * (int64_t(1) << 26) + al, S);
+                    const double yv = fixed_to_double(ah * (int64_t(1) << 26) + al, S);
+                    y[row] = yv;
+                    if constexpr (DOT) dacc = fma(__ldg(x + row), yv, dacc);
                 }
             }
             // ---- the scale after W(w): a larger exponent re-converts W(w)
@@ -464,6 +497,20 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
             mbar_wait(raw_full + i % kRawStages, (i / kRawStages) & 1u);
         for (uint32_t i = ir > kRecStages ? ir - kRecStages : 0; i < ir; ++i)
             mbar_wait(rec_full + i % kRecStages, (i / kRecStages) & 1u);
+    }
+    if constexpr (DOT) {
+        // the CTA's x.y: warp sums, then the warps in order (the expected-record
+        // table is no longer read and holds them)
+        for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xFFFFFFFFu, dacc, o);
+        compute_sync(NC);
+        double* const sred = reinterpret_cast<double*>(sexp);
+        if (lane == 0) sred[tid >> 5] = dacc;
+        compute_sync(NC);
+        if (tid == 0) {
+            double s = 0.0;
+            for (int i = 0; i < (NC >> 5); ++i) s += sred[i];
+            dot_part[blockIdx.x] = s;
+        }
     }
 }
 
@@ -570,8 +617,11 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
 }
 
 cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, const double* x, double* y,
-                                    cudaStream_t s, const uint32_t* xmax_part, int xmax_n) {
+                                    cudaStream_t s, const uint32_t* xmax_part, int xmax_n, double* dot_part,
+                                    int* dot_n) {
+    if (dot_n) *dot_n = 0;
     if (a.n == 0 || tp.z_hi <= tp.z_lo) return cudaSuccess;
+    if (dot_part && (tp.z_lo != 0 || tp.z_hi != tp.nz)) return cudaErrorNotSupported;   // x.y of the whole vector
     if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) != 0) return cudaErrorNotSupported;
     if (tp.z_lo < 0 || tp.z_hi > tp.nz) return cudaErrorInvalidValue;
     const int64_t units = int64_t(tp.nblk) * (tp.z_hi - tp.z_lo);
@@ -587,24 +637,30 @@ cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, con
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    auto kernel = tp.ty == 2 ? pattern_fast_tma_kernel<2> : pattern_fast_tma_kernel<1>;
+    const int kind = (tp.ty == 2 ? 1 : 0) + (dot_part ? 2 : 0);
+    auto kernel = kind == 0   ? pattern_fast_tma_kernel<1, false>
+                  : kind == 1 ? pattern_fast_tma_kernel<2, false>
+                  : kind == 2 ? pattern_fast_tma_kernel<1, true>
+                              : pattern_fast_tma_kernel<2, true>;
     {
         static std::mutex mu;
-        static bool set[64][2] = {};
+        static bool set[64][4] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         std::lock_guard<std::mutex> g(mu);
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!set[dev][tp.ty == 2]) {
+        if (!set[dev][kind]) {
             e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return e;
-            set[dev][tp.ty == 2] = true;
+            set[dev][kind] = true;
         }
     }
-    kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y, xmax_part, xmax_n);
-    return cudaGetLastError();
+    kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y, xmax_part, xmax_n, dot_part);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && dot_n) *dot_n = int(grid);
+    return e;
 }
 
 }  // namespace spmvc

@@ -47,9 +47,15 @@ constexpr int kF32RawStages = 12;
 constexpr int kF32TypeStages = 8;
 constexpr int kF32MaxThreads = 384;   // compute threads (four rows each)
 
+// With DOT the kernel also forms x.y (the p.q of the inner CG step): each
+// thread sums its four rows' products x[row]*y[row] of a step in binary32
+// (x from the window's centre) and adds that chunk to a binary64 sum, one
+// conversion a step (binary64 work runs on a narrow pipe); the CTA's sum
+// goes to dot_part[blockIdx.x].
+template <bool DOT>
 __global__ void __launch_bounds__(kF32MaxThreads + 32, 1)
     pattern_f32_tma_kernel(const __grid_constant__ CUtensorMap xmap, const PatternView a, const TmaF32Plan tp,
-                           const float* __restrict__ x, float* __restrict__ y) {
+                           const float* __restrict__ x, float* __restrict__ y, double* __restrict__ dot_part) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31;
     const int NC = tp.threads, C = tp.C, nx = tp.nx, pitch = tp.pitch;
@@ -154,6 +160,7 @@ __global__ void __launch_bounds__(kF32MaxThreads + 32, 1)
     const uint32_t xcls = (ix > 0 ? 1u : 0u) | (ix < nx - 1 ? 2u : 0u);
     uint32_t nraw = 0, ntyp = 0;
     bool aborted = false;
+    double dacc = 0.0;   // this thread's part of x.y (DOT)
     auto wait_raw = [&](uint32_t& st) -> bool {
         st = nraw % kF32RawStages;
         const bool okw = mbar_wait(raw_full + st, (nraw / kF32RawStages) & 1u);
@@ -266,6 +273,12 @@ __global__ void __launch_bounds__(kF32MaxThreads + 32, 1)
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) y[row0 + int64_t(j) * nx] = acc[j];
+            if constexpr (DOT) {
+                float c = P[1][base + pitch] * acc[0];
+#pragma unroll
+                for (int j = 1; j < 4; ++j) c = fmaf(P[1][base + (j + 1) * pitch], acc[j], c);
+                dacc += double(c);
+            }
             release(raw_empty + sA);           // W(q-1) is no longer read
             release(typ_empty + stT);
             sA = sB;
@@ -289,6 +302,19 @@ __global__ void __launch_bounds__(kF32MaxThreads + 32, 1)
                 mbar_wait(raw_full + i % kF32RawStages, (i / kF32RawStages) & 1u);
             for (uint32_t i = it > kF32TypeStages ? it - kF32TypeStages : 0; i < it; ++i)
                 mbar_wait(typ_full + i % kF32TypeStages, (i / kF32TypeStages) & 1u);
+        }
+    }
+    if constexpr (DOT) {
+        // the CTA's x.y: warp sums, then the warps in order (the value table
+        // is no longer read and holds them)
+        for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xFFFFFFFFu, dacc, o);
+        double* const sred = reinterpret_cast<double*>(sdict);
+        if (lane == 0) sred[tid >> 5] = dacc;
+        compute_sync(NC);
+        if (tid == 0) {
+            double s = 0.0;
+            for (int i = 0; i < (NC >> 5); ++i) s += sred[i];
+            dot_part[blockIdx.x] = s;
         }
     }
 }
@@ -357,7 +383,8 @@ bool make_tma_f32_plan(const PatternFormat& p, const PatternView& v, int64_t n, 
 }
 
 cudaError_t launch_pattern_f32_tma(const PatternView& a, const TmaF32Plan& tp, const float* x, float* y,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, double* dot_part, int* dot_n) {
+    if (dot_n) *dot_n = 0;
     if (a.n == 0) return cudaSuccess;
     if (!a.rtype || !a.rtypes || a.ntypes < 1 || a.ntypes > 256 || a.dict_size > 256) return cudaErrorNotSupported;
     if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0 || (reinterpret_cast<uintptr_t>(a.rtype) & 15u) != 0)
@@ -373,25 +400,28 @@ cudaError_t launch_pattern_f32_tma(const PatternView& a, const TmaF32Plan& tp, c
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
+    auto kernel = dot_part ? pattern_f32_tma_kernel<true> : pattern_f32_tma_kernel<false>;
     {
         static std::mutex mu;
-        static bool set[64] = {};
+        static bool set[64][2] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         std::lock_guard<std::mutex> g(mu);
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!set[dev]) {
-            e = cudaFuncSetAttribute(reinterpret_cast<const void*>(pattern_f32_tma_kernel),
+        if (!set[dev][dot_part != nullptr]) {
+            e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return e;
-            set[dev] = true;
+            set[dev][dot_part != nullptr] = true;
         }
     }
     const int64_t units = int64_t(tp.nblk) * tp.nz;
     const unsigned grid = unsigned(std::min<int64_t>(units, tp.grid));
-    pattern_f32_tma_kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y);
-    return cudaGetLastError();
+    kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y, dot_part);
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && dot_n) *dot_n = int(grid);
+    return e;
 }
 
 }  // namespace spmvc

@@ -369,8 +369,10 @@ struct TmaF32Plan {
 bool make_tma_f32_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, TmaF32Plan* out);
 // cudaErrorNotSupported (nothing launched) without row types or when x is
 // not 16-byte aligned.
+// dot_part / dot_n as for launch_pattern_fast_tma (a thread's four rows of
+// a step summed in binary32, those chunks summed in binary64).
 cudaError_t launch_pattern_f32_tma(const PatternView& a, const TmaF32Plan& tp, const float* x, float* y,
-                                   cudaStream_t s);
+                                   cudaStream_t s, double* dot_part = nullptr, int* dot_n = nullptr);
 
 // The record each boundary class of grid position implies, 64 classes x 8
 // words (the TMA-fed kernels compare every row's record with it).
@@ -384,8 +386,12 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
 // need it).  xmax_part (optional): xmax_n words whose maximum is the largest
 // high word of |x_j| (sign cleared); the product then scales every run by
 // that exponent (the whole vector's) instead of the largest one it has met.
+// With dot_part (a whole-grid plan only) the kernel also writes, for each of
+// its CTAs, the binary64 sum of x[i]*y[i] over the rows that CTA stored into
+// dot_part[cta]; *dot_n receives the number of CTAs (0 when nothing ran).
 cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, const double* x, double* y,
-                                    cudaStream_t s, const uint32_t* xmax_part = nullptr, int xmax_n = 0);
+                                    cudaStream_t s, const uint32_t* xmax_part = nullptr, int xmax_n = 0,
+                                    double* dot_part = nullptr, int* dot_n = nullptr);
 bool stage_supported(int nu);  // union sizes with a compiled staged kernel
 bool rstage_supported(const StagePlan& sp);  // plans the register-staged kernel takes
 
