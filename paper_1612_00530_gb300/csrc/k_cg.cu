@@ -520,17 +520,19 @@ __global__ void __launch_bounds__(kRedThreads, kRedPerSm) dot_cols_kernel(const 
     }
 }
 
-// column j's partials summed by one warp in a fixed order (valid in every lane)
-__device__ __forceinline__ double sum_col_warp(const double* __restrict__ partial, int k, int j) {
+// column j's partials (nb blocks) summed by one warp in a fixed order (valid
+// in every lane)
+__device__ __forceinline__ double sum_col_warp(const double* __restrict__ partial, int k, int j,
+                                               int nb = kRedBlocks) {
     double s = 0.0;
-    for (int b = threadIdx.x & 31; b < kRedBlocks; b += 32) s += partial[b * k + j];
+    for (int b = threadIdx.x & 31; b < nb; b += 32) s += partial[b * k + j];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     return s;
 }
 
 // alpha_j = rr_j / (p_j . q_j), one warp per column; the step runs (live)
 // exactly when the batch had not converged before it
-__global__ void alpha_cols_kernel(const double* __restrict__ partial_pq, ColState* __restrict__ st) {
+__global__ void alpha_cols_kernel(const double* __restrict__ partial_pq, int npq, ColState* __restrict__ st) {
     if (st->done) {
         if (threadIdx.x == 0) st->live = 0;
         return;
@@ -538,7 +540,7 @@ __global__ void alpha_cols_kernel(const double* __restrict__ partial_pq, ColStat
     if (threadIdx.x == 0) st->live = 1;
     const int j = threadIdx.x >> 5;
     if (j >= st->k) return;
-    const double pq = sum_col_warp(partial_pq, st->k, j);
+    const double pq = sum_col_warp(partial_pq, st->k, j, npq);
     if ((threadIdx.x & 31) == 0) st->alpha[j] = (st->rr[j] > 0.0 && pq != 0.0) ? st->rr[j] / pq : 0.0;
 }
 
@@ -790,9 +792,12 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
     CG_CUDA(cudaMemcpyAsync(d_hist, &rel0, sizeof(double), cudaMemcpyHostToDevice, s));
     CG_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s));
     auto body = [&]() -> int {
+        // p.q stays a pass of its own here: inside the SpMM its binary64
+        // multiply a (row, column) would share the narrow FP64 pipe with
+        // the rounding of every output
         CG_ST(spmm_apply(A, k, p, k, q, k, s));
         dot_cols_kernel<<<G, T, 0, s>>>(p, q, n, k, part_a, d_st);
-        alpha_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, d_st);
+        alpha_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, int(G), d_st);
         update_r_cols_kernel<<<G, T, 0, s>>>(r, q, n, part_b, d_st);
         beta_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_b, d_st, d_hist);
         update_xp_cols_kernel<<<G, T, 0, s>>>(x, p, r, n, d_st);

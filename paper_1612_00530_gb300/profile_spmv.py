@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--cg", choices=("fp64", "ir_fp32"), default=None,
                     help="run one CG solve (b = A 1) instead of SpMV steps")
     ap.add_argument("--cg-iters", type=int, default=40)
+    ap.add_argument("--cg-rhs", type=int, default=1,
+                    help="FP64 CG on this many right-hand sides at once (b_j = A v_j, V seed 22)")
     ap.add_argument("--spmm", type=int, default=0, help="time Y = A X with K right-hand sides (X seed 3)")
     ap.add_argument("--f32", type=int, default=-1, choices=(-1, 0, 1, 2),
                     help="time the binary32 product with kernel 2 (TMA), 1 (row types) or 0 (records)")
@@ -46,6 +48,15 @@ def main():
     y = torch.empty_like(x)
     if args.variant >= 0:
         P.spmv_set_tile(M, args.variant, args.tile, args.threads)
+    if args.cg and args.cg_rhs > 1:
+        V = torch.from_numpy(spmv_inputs.uniform_matrix(n, args.cg_rhs, seed=22)).cuda()
+        B = torch.empty_like(V)
+        P.spmm_apply(A, V, B)
+        X0 = torch.zeros_like(B)
+        r = P.cg_solve(M, B, X0, tol=1e-30, max_iter=args.cg_iters, check_every=8)
+        print(f"cg fp64, {args.cg_rhs} right-hand sides: {r['iterations']} steps in {r['seconds'] * 1e3:.2f} ms "
+              f"({r['seconds'] / max(1, r['iterations']) * 1e6:.1f} us/step)")
+        return
     if args.cg:
         ones = torch.ones_like(x)
         P.spmv_apply(M, ones, y)
