@@ -343,12 +343,16 @@ int spmv_set_variant(spmv_mat_t A, int32_t variant, int32_t tile_rows);
  * for variants 1, 6, 7, 8 and 9 on the full 27-slot union of a 3-D
  * 27-point stencil, 256 (tile_rows 512, 1024 or 2048: two, four or eight
  * rows per thread); variant 10 takes 256 with tile_rows 1536 or 2048.
+ * Variant 11 (the TMA-fed kernel) takes tile_rows 1 or 2 (grid lines of a
+ * thread's tile; 0 keeps the current plan) and block_threads 2 for two
+ * CTAs an SM (column blocks of at most 768 rows, two record stages), any
+ * other value for one (at most 1536 rows).
  * Ignored for variants 0, 2, 4, 5.  SPMV_EINVAL for other block sizes,
  * SPMV_EUNSUPPORTED for shapes A has no kernel for. */
 int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t block_threads);
 
 /* The FAST-order SpMM kernel of a pattern-format handle.  kind 1, 2 or 3
- * (1 is the default): for k >= 4 on a 27-point grid stencil with uniform
+ * (3 is the default): for k >= 4 on a 27-point grid stencil with uniform
  * neighbour weights, the TMA-fed z-marching kernel (blocks of L lines by W
  * columns, 4 or 8 right-hand sides a pass, each row record read once a
  * pass, every window converted once a column) with `kind` CTAs an SM, each

@@ -363,7 +363,7 @@ def spmv_set_variant(A: SpmvMatrix, variant: int, tile_rows: int = 0) -> None:
 
 def spmv_set_spmm_kernel(A: SpmvMatrix, kind: int) -> None:
     """FAST SpMM kernel: 1, 2 or 3 the TMA-fed kernel with that many CTAs an
-    SM where it applies (1 by default), 0 one thread a (row, column) pair."""
+    SM where it applies (3 by default), 0 one thread a (row, column) pair."""
     _check(library().spmv_set_spmm_kernel(A, kind))
 
 
@@ -378,7 +378,8 @@ def spmv_set_tile(A: SpmvMatrix, variant: int, tile_rows: int, block_threads: in
     the full 27-slot union); variant 10, the z-block kernel, takes 256 with
     tile_rows = 512 x planes (1536 or 2048); variant 11 takes tile_rows 1 or 2
     (grid lines a thread's 4-column tile spans; 0 keeps the current one) and
-    ignores block_threads (its block is whole grid lines)."""
+    block_threads 2 for two CTAs an SM (blocks of at most 768 rows), any
+    other value for one (its block is whole grid lines)."""
     _check(library().spmv_set_tile(A, variant, tile_rows, block_threads))
 
 

@@ -302,17 +302,25 @@ int ensure_device(spmv_mat_s* m) {
         // TMA z-marching kernel: its plan and the table of the record each
         // boundary class of grid position implies
         m->tplan_ok = false;
+        m->tplan_cg_ok = false;
         {
             std::vector<uint32_t> tab;
-            // lines a compute thread's tile: the autotuner's pick for matrices
-            // of this shape, else 1
-            const int ty = m->fast_variant == 11 ? tuned_stage_shape(m, 0, 1).second : 1;
-            if (make_tma_plan(p, v, m->n, m->num_sms, ty, &m->tplan, &tab) ||
-                make_tma_plan(p, v, m->n, m->num_sms, 3 - ty, &m->tplan, &tab)) {
+            // lines a compute thread's tile and CTAs an SM: the autotuner's
+            // pick for matrices of this shape (ty + 4 (ctas - 1)), else 1 and 1
+            const int code = m->fast_variant == 11 ? tuned_stage_shape(m, 0, 1).second : 1;
+            const int ty = code & 3, ctas = 1 + (code >> 2);
+            if (make_tma_plan(p, v, m->n, m->num_sms, ty, ctas, &m->tplan, &tab) ||
+                make_tma_plan(p, v, m->n, m->num_sms, 1, 1, &m->tplan, &tab) ||
+                make_tma_plan(p, v, m->n, m->num_sms, 2, 1, &m->tplan, &tab)) {
                 uint32_t* dt;
                 if ((st = dev_copy(m, tab.data(), tab.size(), &dt))) return st;
                 m->tplan.expected = dt;
                 m->tplan_ok = true;
+                // the CG step's product, which also forms p.q, runs faster
+                // with two CTAs an SM (its binary64 work then overlaps the
+                // other CTA's steps); the plain product with one
+                m->tplan_cg_ok = make_tma_plan(p, v, m->n, m->num_sms, 1, 2, &m->tplan_cg, &tab);
+                m->tplan_cg.expected = dt;
             }
         }
         // TMA SpMM plans, sharing the expected-record table
@@ -1040,14 +1048,15 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
                     cands.push_back(Cand{10, {}, zp, {}});
             }
             if (A->tplan_ok && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0)
-                for (int ty : {1, 2}) {
-                    TmaPlan tp;
-                    std::vector<uint32_t> tab;
-                    if (make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, ty, &tp, &tab)) {
-                        tp.expected = A->tplan.expected;   // the same table for every shape
-                        cands.push_back(Cand{11, {}, {}, tp});
+                for (int ctas : {1, 2})
+                    for (int ty : {1, 2}) {
+                        TmaPlan tp;
+                        std::vector<uint32_t> tab;
+                        if (make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, ty, ctas, &tp, &tab)) {
+                            tp.expected = A->tplan.expected;   // the same table for every shape
+                            cands.push_back(Cand{11, {}, {}, tp});
+                        }
                     }
-                }
         }
     }
     if (cands.size() <= 1) return SPMV_OK;
@@ -1145,7 +1154,7 @@ int spmv_autotune(spmv_mat_t A, const double* x, double* y, int32_t reps, int32_
         else if (pick.variant == 10)
             g_tune[tune_key(A)] = pick.zplan.threads * 16 + pick.zplan.zc;
         else if (pick.variant == 11)
-            g_tune[tune_key(A)] = pick.tplan.ty;
+            g_tune[tune_key(A)] = pick.tplan.ty + 4 * (pick.tplan.ctas - 1);
         else if (staged_pick)
             g_tune[tune_key(A)] = (pick.plan.rows / pick.plan.rows_per_thread) * 16 + pick.plan.rows_per_thread;
     }
@@ -1214,7 +1223,7 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
     }
     if (variant == 11) {
         // tile_rows: lines of a compute thread's tile, 1 or 2 (0: keep the
-        // current plan's)
+        // current plan's); block_threads 2: two CTAs an SM, else one
         if (!A->tplan_ok)
             return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel for this matrix (the full 27-point box of an "
                                            "nx*ny*nz grid with uniform neighbour weights, nx a multiple of 4 up "
@@ -1223,7 +1232,8 @@ int spmv_set_tile(spmv_mat_t A, int32_t variant, int32_t tile_rows, int32_t bloc
             TmaPlan tp;
             std::vector<uint32_t> tab;
             if (tile_rows != 1 && tile_rows != 2) return fail(SPMV_EINVAL, "variant 11 takes tiles of 1 or 2 lines");
-            if (!make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, tile_rows, &tp, &tab))
+            const int ctas = block_threads == 2 ? 2 : 1;
+            if (!make_tma_plan(A->pat, A->pat_view, A->n, A->num_sms, tile_rows, ctas, &tp, &tab))
                 return fail(SPMV_EUNSUPPORTED, "no TMA z-marching kernel with that tile here");
             tp.expected = A->tplan.expected;
             A->tplan = tp;
@@ -1328,12 +1338,36 @@ int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xm
     if (st) return st;
     if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty() && A->fast_variant == 11 &&
         A->tplan_ok && A->n > 0 && x != y) {
-        const cudaError_t e =
-            launch_pattern_fast_tma(A->pat_view, A->tplan, x, y, s, xmax_part, xmax_n, dot_part, dot_n);
+        const TmaPlan& tp = dot_part && A->tplan_cg_ok ? A->tplan_cg : A->tplan;
+        const cudaError_t e = launch_pattern_fast_tma(A->pat_view, tp, x, y, s, xmax_part, xmax_n, dot_part, dot_n);
         if (e == cudaSuccess) return SPMV_OK;
         if (e != cudaErrorNotSupported) return cuda_fail(e, "spmv launch");
     }
     return spmv_apply(A, x, y, s);
+}
+
+// Y = A X where the caller also has partial maxima of the high words of
+// |X| by column (xmax_n rows of k words): the TMA-fed SpMM then scales each
+// column by its whole-vector exponent; other kernels ignore them.
+int api_spmm_xmax(spmv_mat_s* A, int32_t k, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s,
+                  const uint32_t* xmax_part, int xmax_n) {
+    if (!valid(A)) return fail(SPMV_EINVAL, "invalid matrix handle");
+    int st = ensure_device(A);
+    if (st) return st;
+    if (A->fmt == SPMV_FMT_PATTERN && A->order == SPMV_ORDER_FAST && A->perm.empty() && A->n > 0 && X && Y &&
+        k >= 1 && k <= 64 && ldx >= k && ldy >= k) {
+        const int c = A->spmm_kind - 1;
+        const TmaSpmmPlan* tp = c < 0 ? nullptr
+                                : k >= 8 && A->splan_ok[1][c] ? &A->splan[1][c]
+                                : k >= 4 && A->splan_ok[0][c] ? &A->splan[0][c]
+                                                              : nullptr;
+        if (tp) {
+            const cudaError_t e = launch_pattern_spmm_tma(A->pat_view, *tp, k, X, ldx, Y, ldy, s, xmax_part, xmax_n);
+            if (e == cudaSuccess) return SPMV_OK;
+            if (e != cudaErrorNotSupported) return cuda_fail(e, "spmm launch");
+        }
+    }
+    return spmm_apply(A, k, X, ldx, Y, ldy, s);
 }
 
 // The binary32 product with x.y as above (the TMA-fed kernel only).

@@ -30,6 +30,8 @@ int api_apply_xmax(spmv_mat_s* A, const double* x, double* y, const uint32_t* xm
                    cudaStream_t s, double* dot_part, int* dot_n);
 int api_apply_f32_dot(spmv_mat_s* A, const float* x, float* y, cudaStream_t s, double* dot_part, int* dot_n);
 int api_prepare_f32(spmv_mat_s* m);
+int api_spmm_xmax(spmv_mat_s* A, int32_t k, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s,
+                  const uint32_t* xmax_part, int xmax_n);
 
 namespace {
 
@@ -611,40 +613,79 @@ __global__ void beta_cols_kernel(const double* __restrict__ partial_rr, ColState
     }
 }
 
+// Per column j, the largest high word of |v| this block's threads of that
+// column saw (mx), into pmax[blockIdx.x * k + j] (the SpMM's scales).
+__device__ __forceinline__ void block_col_hi_max(uint32_t mx, int k, uint32_t* __restrict__ pmax) {
+    __shared__ uint32_t s_mx[kRedThreads];
+    const int R = kRedThreads / k;
+    s_mx[threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        uint32_t m = 0u;
+        for (int i = 0; i < R; ++i) m = max(m, s_mx[i * k + threadIdx.x]);
+        pmax[blockIdx.x * k + threadIdx.x] = m;
+    }
+}
+
 // x += alpha p; p = r + beta p (a step that ran: the beta kernel may have
-// just set the convergence flag, and x still takes this step's update)
+// just set the convergence flag, and x still takes this step's update);
+// per-block column maxima of |p| for the next SpMM
 __global__ void __launch_bounds__(kRedThreads, kRedPerSm) update_xp_cols_kernel(double* __restrict__ x,
                                                                      double* __restrict__ p,
                                                                      const double* __restrict__ r, int64_t n,
-                                                                     const ColState* __restrict__ st) {
+                                                                     const ColState* __restrict__ st,
+                                                                     uint32_t* __restrict__ pmax) {
     if (!st->live) return;
     const int k = st->k, R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
-    if (sub >= R) return;
-    const double alpha = st->alpha[j], beta = st->beta[j];
-    const int64_t rs = int64_t(gridDim.x) * R;
-    int64_t row = blockIdx.x * int64_t(R) + sub;
-    for (; row + 3 * rs < n; row += 4 * rs) {
-        double xv[4], pv[4], rv[4];
+    uint32_t mx = 0u;
+    if (sub < R) {
+        const double alpha = st->alpha[j], beta = st->beta[j];
+        const int64_t rs = int64_t(gridDim.x) * R;
+        int64_t row = blockIdx.x * int64_t(R) + sub;
+        for (; row + 3 * rs < n; row += 4 * rs) {
+            double xv[4], pv[4], rv[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int64_t i = (row + c * rs) * k + j;
-            xv[c] = x[i];
-            pv[c] = p[i];
-            rv[c] = r[i];
+            for (int c = 0; c < 4; ++c) {
+                const int64_t i = (row + c * rs) * k + j;
+                xv[c] = x[i];
+                pv[c] = p[i];
+                rv[c] = r[i];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t i = (row + c * rs) * k + j;
+                x[i] = fma(alpha, pv[c], xv[c]);
+                const double pn = fma(beta, pv[c], rv[c]);
+                p[i] = pn;
+                mx = max(mx, hi_abs(pn));
+            }
         }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int64_t i = (row + c * rs) * k + j;
-            x[i] = fma(alpha, pv[c], xv[c]);
-            p[i] = fma(beta, pv[c], rv[c]);
+        for (; row < n; row += rs) {
+            const int64_t i = row * k + j;
+            const double po = p[i];
+            x[i] = fma(alpha, po, x[i]);
+            const double pn = fma(beta, po, r[i]);
+            p[i] = pn;
+            mx = max(mx, hi_abs(pn));
         }
     }
-    for (; row < n; row += rs) {
-        const int64_t i = row * k + j;
-        const double po = p[i];
-        x[i] = fma(alpha, po, x[i]);
-        p[i] = fma(beta, po, r[i]);
-    }
+    block_col_hi_max(mx, k, pmax);
+}
+
+// dst = src (n x k) with per-block column maxima of |src| (the first SpMM's
+// scales)
+__global__ void __launch_bounds__(kRedThreads, kRedPerSm) copy_cols_kernel(double* __restrict__ dst,
+                                                                const double* __restrict__ src, int64_t n, int k,
+                                                                uint32_t* __restrict__ pmax) {
+    const int R = kRedThreads / k, j = threadIdx.x % k, sub = threadIdx.x / k;
+    uint32_t mx = 0u;
+    if (sub < R)
+        for (int64_t row = blockIdx.x * int64_t(R) + sub; row < n; row += int64_t(gridDim.x) * R) {
+            const double v = src[row * k + j];
+            dst[row * k + j] = v;
+            mx = max(mx, hi_abs(v));
+        }
+    block_col_hi_max(mx, k, pmax);
 }
 
 // r = b - q, partial sums of r.r per column
@@ -753,7 +794,9 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
     double* d_sums = ws.get<double>(k);
     ColState* d_st = ws.get<ColState>(1);
     double* d_hist = ws.get<double>(o.max_iter + 2);
-    if (!r || !q || !p || !part_a || !part_b || !d_sums || !d_st || !d_hist) return fail(SPMV_ENOMEM, "CG workspace");
+    uint32_t* pmax = ws.get<uint32_t>(size_t(kRedBlocks) * k);
+    if (!r || !q || !p || !part_a || !part_b || !d_sums || !d_st || !d_hist || !pmax)
+        return fail(SPMV_ENOMEM, "CG workspace");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -790,17 +833,17 @@ int cg_solve_cols(spmv_mat_t A, const double* b, double* x, const spmv_cg_opts& 
     hs.done = rel0 <= o.tol ? 1 : 0;
     CG_CUDA(cudaMemcpyAsync(d_st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     CG_CUDA(cudaMemcpyAsync(d_hist, &rel0, sizeof(double), cudaMemcpyHostToDevice, s));
-    CG_CUDA(cudaMemcpyAsync(p, r, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s));
+    copy_cols_kernel<<<G, T, 0, s>>>(p, r, n, k, pmax);
     auto body = [&]() -> int {
         // p.q stays a pass of its own here: inside the SpMM its binary64
         // multiply a (row, column) would share the narrow FP64 pipe with
         // the rounding of every output
-        CG_ST(spmm_apply(A, k, p, k, q, k, s));
+        CG_ST(api_spmm_xmax(A, k, p, k, q, k, s, pmax, int(G)));
         dot_cols_kernel<<<G, T, 0, s>>>(p, q, n, k, part_a, d_st);
         alpha_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_a, int(G), d_st);
         update_r_cols_kernel<<<G, T, 0, s>>>(r, q, n, part_b, d_st);
         beta_cols_kernel<<<1, 32 * kMaxCols, 0, s>>>(part_b, d_st, d_hist);
-        update_xp_cols_kernel<<<G, T, 0, s>>>(x, p, r, n, d_st);
+        update_xp_cols_kernel<<<G, T, 0, s>>>(x, p, r, n, d_st, pmax);
         CG_CUDA(cudaGetLastError());
         return SPMV_OK;
     };

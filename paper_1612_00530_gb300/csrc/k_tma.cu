@@ -48,10 +48,15 @@ namespace {
 #include "fast_fixed.cuh"
 #include "tma_ptx.cuh"
 
-constexpr int kSlotElems = 2048;                // elements a ring slot holds (16 KB)
 constexpr int kRawStages = 2;
-constexpr int kRecStages = 3;
-constexpr int kMaxBlockRows = 1536;             // C
+constexpr int kMaxBlockRows = 1536;             // C with one CTA an SM
+
+// With MINB CTAs an SM (1 or 2) each holds at most kMaxBlockRows / MINB
+// rows, a ring slot of slot_elems elements (16 KB, or 10 KB) and
+// rec_stages record stages (three, or two), so that two CTAs' shared
+// memory fits an SM.
+__host__ __device__ constexpr int slot_elems(int minb) { return minb == 1 ? 2048 : 1280; }
+__host__ __device__ constexpr int rec_stages(int minb) { return minb == 1 ? 3 : 2; }
 
 // A compute thread sums a tile of TY grid lines by four columns (K = 4 TY
 // rows).  A ring slot holds four sub-arrays, sub-array s the window elements
@@ -62,13 +67,15 @@ constexpr int kMaxBlockRows = 1536;             // C
 // CG step, Sec. II): every thread adds x[row]*y[row] of the rows it stores,
 // in binary64 in its own order, and the CTA's sum of those goes to
 // dot_part[blockIdx.x].
-template <int TY, bool DOT>
-__global__ void __launch_bounds__(kMaxBlockRows / (4 * TY) + 32, 1)
+template <int TY, bool DOT, int MINB>
+__global__ void __launch_bounds__(kMaxBlockRows / (4 * TY * MINB) + 32, MINB)
     pattern_fast_tma_kernel(const __grid_constant__ CUtensorMap xmap, const PatternView a, const TmaPlan tp,
                             const double* __restrict__ x, double* __restrict__ y,
                             const uint32_t* __restrict__ xmax_part, int xmax_n, double* __restrict__ dot_part) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int K = 4 * TY;                          // rows a compute thread
+    constexpr int kSlotElems = slot_elems(MINB);
+    constexpr int kRecStages = rec_stages(MINB);
     constexpr int SUB = kSlotElems / 4;
     constexpr uint32_t SUBB = uint32_t(SUB) * 8u;     // bytes of a sub-array
     constexpr uint32_t SLOTB = 4u * SUBB;              // bytes of a ring slot
@@ -563,9 +570,11 @@ void expected_records(const PatternFormat& p, const PatternView& v, std::vector<
     *out = std::move(tab);
 }
 
-bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
-                   std::vector<uint32_t>* expected) {
+bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, int ctas,
+                   TmaPlan* out, std::vector<uint32_t>* expected) {
     if (ty != 1 && ty != 2) return false;
+    if (ctas != 1 && ctas != 2) return false;
+    const int kSlotElems = slot_elems(ctas), kRecStages = rec_stages(ctas);
     if (!p.fast_ok || v.nu != 27 || v.words != 7 || v.run_len != 3 || !v.dom_ok || !v.dom_uni) return false;
     const std::vector<int32_t>& U = p.uoff;
     if (U.size() != 27) return false;
@@ -581,7 +590,7 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
     // the most lines a block (whole warps of ty-by-4 tiles) whose window fits
     // a ring slot
     int L = 0;
-    for (int64_t l = ty; l <= ny && l * nx <= kMaxBlockRows; l += ty)
+    for (int64_t l = ty; l <= ny && l * nx <= kMaxBlockRows / ctas; l += ty)
         if (ny % l == 0 && (l * nx) % (128 * ty) == 0 && (l + 2) * (nx + 4) <= kSlotElems) L = int(l);
     if (L == 0) return false;
     TmaPlan t{};
@@ -596,7 +605,8 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
     t.win_elems = (L + 2) * t.pitch;
     t.nblk = int32_t(ny / L);
     t.S = S;
-    t.grid = std::max(num_sms, 1);
+    t.grid = std::max(num_sms, 1) * ctas;
+    t.ctas = ctas;
     t.z_lo = 0;
     t.z_hi = t.nz;
     auto up = [](int64_t v_, int64_t a_) { return (v_ + a_ - 1) / a_ * a_; };
@@ -608,7 +618,7 @@ bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int 
     t.off_words = t.off_flags + int32_t(up(3 * (t.C / 32) * 4, 16));
     t.off_mbar = t.off_words + 64;
     t.smem_bytes = int32_t(up(t.off_mbar + 8 * 2 * (kRawStages + kRecStages), 128));
-    if (t.smem_bytes > 227 * 1024) return false;
+    if (t.smem_bytes > (ctas == 1 ? 227 * 1024 : 227 * 1024 / ctas - 1024)) return false;
     std::vector<uint32_t> tab;
     expected_records(p, v, &tab);
     *out = t;
@@ -637,24 +647,29 @@ cudaError_t launch_pattern_fast_tma(const PatternView& a, const TmaPlan& tp, con
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const int kind = (tp.ty == 2 ? 1 : 0) + (dot_part ? 2 : 0);
-    auto kernel = kind == 0   ? pattern_fast_tma_kernel<1, false>
-                  : kind == 1 ? pattern_fast_tma_kernel<2, false>
-                  : kind == 2 ? pattern_fast_tma_kernel<1, true>
-                              : pattern_fast_tma_kernel<2, true>;
+    if (tp.ctas != 1 && tp.ctas != 2) return cudaErrorInvalidValue;
+    using Kernel = void (*)(CUtensorMap, PatternView, TmaPlan, const double*, double*, const uint32_t*, int, double*);
+    static const Kernel kernels[2][2][2] = {   // [ctas - 1][dot][ty - 1]
+        {{pattern_fast_tma_kernel<1, false, 1>, pattern_fast_tma_kernel<2, false, 1>},
+         {pattern_fast_tma_kernel<1, true, 1>, pattern_fast_tma_kernel<2, true, 1>}},
+        {{pattern_fast_tma_kernel<1, false, 2>, pattern_fast_tma_kernel<2, false, 2>},
+         {pattern_fast_tma_kernel<1, true, 2>, pattern_fast_tma_kernel<2, true, 2>}}};
+    const int ci = tp.ctas - 1, di = dot_part ? 1 : 0, ti = tp.ty == 2 ? 1 : 0;
+    const Kernel kernel = kernels[ci][di][ti];
     {
         static std::mutex mu;
-        static bool set[64][4] = {};
+        static bool set[64][2][2][2] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         std::lock_guard<std::mutex> g(mu);
         if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!set[dev][kind]) {
+        if (!set[dev][ci][di][ti]) {
             e = cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel),
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tp.ctas == 1 ? 227 * 1024 : 227 * 1024 / tp.ctas - 1024);
             if (e != cudaSuccess) return e;
-            set[dev][kind] = true;
+            set[dev][ci][di][ti] = true;
         }
     }
     kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, x, y, xmax_part, xmax_n, dot_part);

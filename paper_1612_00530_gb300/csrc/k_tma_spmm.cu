@@ -60,7 +60,8 @@ template <int KC, int MINB>
 __global__ void __launch_bounds__(kSpMaxOutputs / (4 * MINB) + 32, MINB)
     pattern_spmm_tma_kernel(const __grid_constant__ CUtensorMap xmap, const PatternView a, const TmaSpmmPlan tp,
                             const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy,
-                            int c_base, int kcols) {
+                            int c_base, int kcols, const uint32_t* __restrict__ xmax_part, int xmax_n,
+                            int xmax_ld) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int KP = KC / 2;                          // column pairs a window element
     const int tid = threadIdx.x, lane = tid & 31;
@@ -85,7 +86,20 @@ __global__ void __launch_bounds__(kSpMaxOutputs / (4 * MINB) + 32, MINB)
     const int ncheck = C >> 5;                          // warps that check records (rows 0 .. C-1)
 
     for (int i = tid; i < 64 * 8; i += blockDim.x) sexp[i] = __ldg(tp.expected + i);
-    for (int i = tid; i < 4 * KC + 4; i += blockDim.x) swmax[i] = 0u;
+    for (int i = tid; i < 5 * KC + 4; i += blockDim.x) swmax[i] = 0u;
+    // a caller that knows each column's largest |x| (partial maxima of the
+    // high words, xmax_part[b * xmax_ld + column], sign cleared) fixes the
+    // columns' scales for every run: no window ever raises them
+    uint32_t* const sgiven = swmax + 4 * KC + 4;        // [KC]
+    __syncthreads();
+    if (xmax_part) {
+        uint32_t m = 0u;
+        for (int i = tid; i < xmax_n * KC; i += blockDim.x)   // blockDim.x is a multiple of KC
+            if (i % KC < kcols) m = max(m, __ldg(xmax_part + int64_t(i / KC) * xmax_ld + c_base + i % KC));
+#pragma unroll
+        for (int o = KC; o < 32; o <<= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if (lane < KC) atomicMax(sgiven + lane, m);
+    }
     if (tid == 0) {
         for (int i = 0; i < kSpRawStages; ++i) {
             mbar_init(raw_full + i, 1);
@@ -177,7 +191,8 @@ __global__ void __launch_bounds__(kSpMaxOutputs / (4 * MINB) + 32, MINB)
         int cz_cached = -1;
         uint32_t ex[7];
         // scales: own column (sums) and the two converted columns
-        uint32_t Et = 0u, Er = 64u, Et0 = 0u, Er0 = 64u, Et1 = 0u, Er1 = 64u;
+        const uint32_t G = sgiven[c] >> 20, G0 = sgiven[2 * cp] >> 20, G1 = sgiven[2 * cp + 1] >> 20;
+        uint32_t Et = G, Er = max(G, 64u), Et0 = G0, Er0 = max(G0, 64u), Et1 = G1, Er1 = max(G1, 64u);
         // box sums: after step w, B2(w-2) in p2*, B2(w-1) in p1*, centres of
         // plane w-1 in c1* (|sum| < 9 * 2^27 fits int32)
         int32_t p2h[4], p2l[4], p1h[4], p1l[4], c1h[4], c1l[4];
@@ -512,7 +527,7 @@ bool make_tma_spmm_plan(const PatternFormat& p, const PatternView& v, int64_t n,
     t.off_exp = t.off_rec + kSpRecStages * 28 * t.C;
     t.off_flags = t.off_exp + 64 * 8 * 4;
     t.off_words = t.off_flags + int32_t(up(3 * (t.C / 32) * 4, 16));
-    t.off_mbar = t.off_words + int32_t(up((4 * kc + 4) * 4, 16));
+    t.off_mbar = t.off_words + int32_t(up((5 * kc + 4) * 4, 16));
     t.smem_bytes = int32_t(up(t.off_mbar + 8 * 2 * (kSpRawStages + kSpRecStages), 128));
     if (t.smem_bytes > 227 * 1024 / ctas - 1024) return false;
     *out = t;
@@ -520,7 +535,7 @@ bool make_tma_spmm_plan(const PatternFormat& p, const PatternView& v, int64_t n,
 }
 
 cudaError_t launch_pattern_spmm_tma(const PatternView& a, const TmaSpmmPlan& tp, int k, const double* X, int64_t ldx,
-                                    double* Y, int64_t ldy, cudaStream_t s) {
+                                    double* Y, int64_t ldy, cudaStream_t s, const uint32_t* xmax_part, int xmax_n) {
     if (a.n == 0) return cudaSuccess;
     // the 4-D view needs 16-byte aligned rows of X; Y is written by element
     if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0 || (ldx & 1) != 0 || k < tp.kc || k > ldx || k > ldy)
@@ -537,7 +552,8 @@ cudaError_t launch_pattern_spmm_tma(const PatternView& a, const TmaSpmmPlan& tp,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorNotSupported;
-    using Kernel = void (*)(CUtensorMap, PatternView, TmaSpmmPlan, const double*, int64_t, double*, int64_t, int, int);
+    using Kernel = void (*)(CUtensorMap, PatternView, TmaSpmmPlan, const double*, int64_t, double*, int64_t, int, int,
+                            const uint32_t*, int, int);
     static const Kernel kernels[2][3] = {
         {pattern_spmm_tma_kernel<4, 1>, pattern_spmm_tma_kernel<4, 2>, pattern_spmm_tma_kernel<4, 3>},
         {pattern_spmm_tma_kernel<8, 1>, pattern_spmm_tma_kernel<8, 2>, pattern_spmm_tma_kernel<8, 3>}};
@@ -564,7 +580,8 @@ cudaError_t launch_pattern_spmm_tma(const PatternView& a, const TmaSpmmPlan& tp,
     // one pass a group of kc columns; the last may be partial (its columns
     // past k read zeros from the box and store nothing)
     for (int c0 = 0; c0 < k; c0 += tp.kc) {
-        kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, X, ldx, Y, ldy, c0, std::min(tp.kc, k - c0));
+        kernel<<<grid, tp.threads + 32, tp.smem_bytes, s>>>(map, a, tp, X, ldx, Y, ldy, c0, std::min(tp.kc, k - c0),
+                                                            xmax_part, xmax_part ? xmax_n : 0, k);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

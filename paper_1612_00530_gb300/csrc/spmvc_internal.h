@@ -310,16 +310,17 @@ struct TmaPlan {
     int32_t pitch;                  // nx + 4: elements of a window line
     int32_t win_elems;              // (L + 2) * pitch
     int32_t nblk;                   // column blocks a plane (ny / L)
-    int32_t grid;                   // persistent CTAs at most (the SM count)
+    int32_t grid;                   // persistent CTAs at most (the SM count times ctas)
+    int32_t ctas;                   // CTAs an SM: 1, or 2 (half the rows a block, smaller ring and record stages)
     int32_t z_lo, z_hi;             // planes a launch computes (0 and nz: all)
     int64_t S;                      // plane stride nx*ny
     // dynamic shared memory: ring of 4 converted windows at 0, then
     int32_t off_raw, raw_bytes;     // 2 raw window stages
-    int32_t off_rec;                // 3 record stages of 28*C bytes
+    int32_t off_rec;                // 3 record stages of 28*C bytes (2 with two CTAs an SM)
     int32_t off_exp;                // 64 expected records x 8 words
     int32_t off_flags;              // 3 x C/32 words of per-row match bits
     int32_t off_words;              // exponent words, mismatch counts, abort and producer words
-    int32_t off_mbar;               // full and empty mbarriers of the 2 raw and 3 record stages
+    int32_t off_mbar;               // full and empty mbarriers of the raw and record stages
     int32_t smem_bytes;
     const uint32_t* expected;       // device copy of the 64 x 8-word table
 };
@@ -340,7 +341,7 @@ struct TmaSpmmPlan {
     int32_t off_rec;                // 3 record stages of 28*C bytes
     int32_t off_exp;                // 64 expected records x 8 words
     int32_t off_flags;              // 3 x C/32 words of per-row match bits
-    int32_t off_words;              // per-column exponent words, abort and producer words
+    int32_t off_words;              // per-column exponent words, abort and producer words, given scales
     int32_t off_mbar;
     int32_t smem_bytes;
     const uint32_t* expected;       // device copy of the 64 x 8-word table
@@ -350,8 +351,11 @@ bool make_tma_spmm_plan(const PatternFormat& p, const PatternView& v, int64_t n,
 // Y = A X with the plan's kernel, ceil(k / kc) passes; cudaErrorNotSupported
 // (nothing launched) when X is not 16-byte aligned, ldx is odd (the 4-D
 // tensor view needs both) or k < kc.
+// xmax_part (optional): xmax_n rows of k words, the partial maxima of the
+// high words of |X| by column (b * k + j); they fix each column's scale.
 cudaError_t launch_pattern_spmm_tma(const PatternView& a, const TmaSpmmPlan& tp, int k, const double* X, int64_t ldx,
-                                    double* Y, int64_t ldy, cudaStream_t s);
+                                    double* Y, int64_t ldy, cudaStream_t s, const uint32_t* xmax_part = nullptr,
+                                    int xmax_n = 0);
 
 // Binary32 product fed by TMA (k_tma_f32.cu): blocks of L lines (a multiple
 // of four), a compute thread four vertically consecutive rows of a column,
@@ -379,8 +383,8 @@ cudaError_t launch_pattern_f32_tma(const PatternView& a, const TmaF32Plan& tp, c
 void expected_records(const PatternFormat& p, const PatternView& v, std::vector<uint32_t>* out);
 // Builds the plan and the expected-record table (64 classes x 8 words);
 // false when the matrix or its grid has no compiled shape for variant 11.
-bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, TmaPlan* out,
-                   std::vector<uint32_t>* expected);
+bool make_tma_plan(const PatternFormat& p, const PatternView& v, int64_t n, int num_sms, int ty, int ctas,
+                   TmaPlan* out, std::vector<uint32_t>* expected);
 // Launches variant 11; returns cudaErrorNotSupported (nothing launched)
 // when x or y is not 16-byte aligned (the TMA box and the vector stores
 // need it).  xmax_part (optional): xmax_n words whose maximum is the largest
@@ -506,10 +510,12 @@ struct spmv_mat_s {
     bool zbplan_ok = false;
     spmvc::TmaPlan tplan{};            // FAST order, TMA z-marching kernel (variant 11)
     bool tplan_ok = false;
+    spmvc::TmaPlan tplan_cg{};         // the CG product (with p.q): tiles of one line, two CTAs an SM
+    bool tplan_cg_ok = false;
     // FAST order, TMA SpMM: [4 or 8 columns a pass][1 to 3 CTAs an SM]
     spmvc::TmaSpmmPlan splan[2][3]{};
     bool splan_ok[2][3] = {};
-    int32_t spmm_kind = 1;             // 0 per-(row, column) kernel, 1 to 3: TMA kernel, CTAs an SM
+    int32_t spmm_kind = 3;             // 0 per-(row, column) kernel, 1 to 3: TMA kernel, CTAs an SM
     int32_t f32_kind = 2;              // binary32 kernel: 0 records, 1 row types, 2 TMA-fed with row types
     spmvc::TmaF32Plan f32plan{};
     bool f32plan_ok = false;

@@ -36,7 +36,7 @@ def main():
     ap.add_argument("--spmm", type=int, default=0, help="time Y = A X with K right-hand sides (X seed 3)")
     ap.add_argument("--f32", type=int, default=-1, choices=(-1, 0, 1, 2),
                     help="time the binary32 product with kernel 2 (TMA), 1 (row types) or 0 (records)")
-    ap.add_argument("--spmm-kernel", type=int, default=1, choices=(0, 1, 2, 3),
+    ap.add_argument("--spmm-kernel", type=int, default=3, choices=(0, 1, 2, 3),
                     help="FAST SpMM kernel: 1-3 TMA-fed with that many CTAs an SM, 0 one thread a (row, column)")
     args = ap.parse_args()
     g = args.grid

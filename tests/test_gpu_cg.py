@@ -75,9 +75,13 @@ def test_cg_reports_not_converged():
     assert res["iterations"] == 5
 
 
-@pytest.mark.parametrize("k,order", [(4, "fast"), (8, "column"), (3, "fast")])
-def test_batched_cg_columns_match_oracle(k, order):
-    g = (14, 13, 12)
+@pytest.mark.parametrize("k,order,g", [(4, "fast", (14, 13, 12)), (8, "column", (14, 13, 12)),
+                                       (3, "fast", (14, 13, 12)), (8, "fast", (32, 24, 10)),
+                                       (12, "fast", (32, 24, 10))])
+def test_batched_cg_columns_match_oracle(k, order, g):
+    """k right-hand sides at once against the oracle's CG column by column;
+    on the 32 x 24 grid the products run through the TMA-fed SpMM with the
+    columns' scales fixed from the update kernel's maxima of |p|."""
     rowptr, col, val = oracle.hpcg_csr(*g)
     n = len(rowptr) - 1
     import spmv_inputs

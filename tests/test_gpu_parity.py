@@ -886,20 +886,21 @@ def test_spmm_tma_kernel(g, k):
     P.spmv_set_spmm_kernel(C, 0)
     Y3 = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
     P.spmm_apply(C, X, Y3)
-    P.spmv_set_spmm_kernel(C, 1)
+    P.spmv_set_spmm_kernel(C, 3)
     torch.cuda.synchronize()
     # column 3 grows 4x a plane: the per-(row, column) kernel scales it by its
     # largest entry, so early planes get only the first bound
     spmm_fast_check(rowptr, col, val, X_np, Y2.cpu().numpy(), whole_scale_cols=(3,))
     spmm_fast_check(rowptr, col, val, X_np, Y3.cpu().numpy(), whole_scale_cols=(3,))
-    # two and three CTAs an SM (smaller blocks): the same rule
-    for kind in (2, 3):
+    # one and two CTAs an SM (larger blocks; the default takes three): the
+    # same rule
+    for kind in (1, 2):
         P.spmv_set_spmm_kernel(C, kind)
         Y4 = torch.full((n, k), float("nan"), dtype=torch.float64, device="cuda")
         P.spmm_apply(C, X, Y4)
         torch.cuda.synchronize()
         spmm_fast_check(rowptr, col, val, X_np, Y4.cpu().numpy())
-    P.spmv_set_spmm_kernel(C, 1)
+    P.spmv_set_spmm_kernel(C, 3)
     assert P.spmv_device_error(C) == 0
     with pytest.raises(P.SpmvError):
         P.spmv_set_spmm_kernel(C, 4)
@@ -1217,6 +1218,21 @@ def test_tma_kernel_shapes_and_refusals():
                 (11, rows, rows // (4 * ty)), (g, ty)
         with pytest.raises(P.SpmvError):
             P.spmv_set_tile(C, 11, 3, 0)
+    # two CTAs an SM: blocks of at most 768 rows whose window fits a 1280-
+    # element ring slot (none for tiles of two lines at 160 columns)
+    for g, rows in [((192, 192, 3), {1: 768, 2: 768}), ((160, 160, 3), {1: 640, 2: None}),
+                    ((64, 48, 3), {1: 768, 2: 768}), ((32, 64, 3), {1: 512, 2: 512}),
+                    ((96, 96, 3), {1: 768, 2: 768}), ((16, 16, 16), {1: 256, 2: 256})]:
+        C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+        for ty in (1, 2):
+            if rows[ty] is None:
+                with pytest.raises(P.SpmvError):
+                    P.spmv_set_tile(C, 11, ty, 2)
+                continue
+            P.spmv_set_tile(C, 11, ty, 2)
+            info = P.spmv_info(C)
+            assert (info["fast_variant"], info["fast_tile_rows"], info["fast_block_threads"]) == \
+                (11, rows[ty], rows[ty] // (4 * ty)), (g, ty)
     # nx not a multiple of 4; no block of whole lines that divides ny; nx
     # above 252; no interior row (nz = 2: no dominant record without an
     # absent slot)
@@ -1228,6 +1244,34 @@ def test_tma_kernel_shapes_and_refusals():
     C = P.spmv_compress(P.spmv_build_csr(rowptr, col, val), format="pattern", order="fast")
     with pytest.raises(P.SpmvError):
         P.spmv_set_tile(C, 11, 0, 0)
+
+
+@pytest.mark.parametrize("ty", [1, 2])
+def test_tma_kernel_two_ctas_an_sm(ty):
+    """Variant 11 with two CTAs an SM (half-height blocks, two record
+    stages): the exact model of FAST order on uniform x over several blocks
+    and planes, the order's bound when the scale rises plane by plane, and a
+    CG solve whose product also forms p.q."""
+    g = (64, 48, 20)
+    rowptr, col, val = oracle.hpcg_csr(*g)
+    n = len(rowptr) - 1
+    C = P.spmv_compress(P.spmv_build("hpcg", *g), format="pattern", order="fast")
+    P.spmv_set_tile(C, 11, ty, 2)
+    assert P.spmv_info(C)["fast_tile_rows"] == 768
+    x = spmv_inputs.uniform_vector(n, seed=52)
+    check_fast(run(C, x), oracle.spmv(rowptr, col, val, x), abs_row_sums(rowptr, col, val, x))
+    xs = x * np.repeat(2.0 ** (3 * (np.arange(20) % 7)), 64 * 48)
+    check_fast_order_bound(rowptr, col, val, xs, run(C, xs), uncovered_above_tol=False)
+    b_np = oracle.spmv(rowptr, col, val, np.ones(n))
+    b = torch.from_numpy(b_np).cuda()
+    xx = torch.zeros_like(b)
+    r = P.cg_solve(C, b, xx, tol=1e-10, mode="fp64", check_every=8)
+    assert r["status"] == P.SPMV_OK and r["rel_residual"] <= 1.5e-10
+    _, it_ref, hist_ref = oracle.cg(rowptr, col, val, b_np, tol=1e-10, maxit=2000)
+    assert abs(r["iterations"] - it_ref) <= 1
+    m = min(30, len(r["history"]), len(hist_ref))
+    assert np.max(np.abs(np.array(r["history"][:m]) / hist_ref[:m] - 1)) < 1e-8
+    assert P.spmv_device_error(C) == 0
 
 
 def test_tma_kernel_misaligned_vectors_and_scale_changes():
