@@ -51,8 +51,10 @@ extern "C" {
 #define SPMV_ECORRUPT 4        /* compressed stream fails its checksum/bounds check */
 #define SPMV_EUNSUPPORTED 5    /* matrix does not fit the requested format */
 #define SPMV_ENOTCONVERGED 6   /* cg_solve hit max_iter before the tolerance */
-#define SPMV_ETIMEOUT 7        /* reserved, never returned: no kernel of the
-                                  library waits on a device-side condition */
+#define SPMV_ETIMEOUT 7        /* reserved, never returned as a status: a
+                                  TMA-fed kernel whose bounded wait for its
+                                  copies gives up (about a second) sets 16 in
+                                  the matrix's device error word instead */
 #define SPMV_EDEVICE 8         /* a kernel reported a decoding error */
 
 typedef struct spmv_mat_s *spmv_mat_t;
@@ -454,8 +456,11 @@ int spmv_free(spmv_mat_t A);
 const char *spmv_strerror(int status);
 /* The calling thread's last detailed error message ("" if none). */
 const char *spmv_last_error(void);
-/* Reads and clears A's sticky device error word (0 = none); waits for the
- * device. */
+/* Reads and clears A's sticky device error word (0 = none; an OR of 1: a
+ * pattern number out of range, 2: a decoded column or value code out of
+ * range, 4: a delta slice longer than its width, 16: a TMA-fed kernel's
+ * bounded wait for its copies gave up and the kernel stopped early); waits
+ * for the device. */
 int spmv_device_error(spmv_mat_t A, int32_t *code);
 /* Library version string. */
 const char *spmv_version(void);
