@@ -400,10 +400,21 @@ typedef struct spmv_batch_s *spmv_batch_t;
 
 /* Plans y_b = A_b x_b for count pattern-format matrices of any sizes (their
  * records must have equal record_bytes).  xs/ys: host arrays of count device
- * pointers, fixed for the plan's lifetime.  The work list (matrix, row range)
- * is uploaded once and the launch is captured in a CUDA graph. */
+ * pointers, fixed for the plan's lifetime.  The work list (matrix, row range
+ * of 256 rows) is uploaded once and the launch is captured in a CUDA graph.
+ * Order: when every matrix is in FAST order (spmv_set_order), each row is
+ * the exact fixed-point sum rounded once, at the scale of the largest
+ * exponent of its x_b (a pass over the x_b inside the same graph; a
+ * matrix whose x is zero/subnormal only or not finite takes the COLUMN
+ * order); otherwise every row is the COLUMN order's fma chain (bit-exact
+ * with the CSR product). */
 int spmv_batch_create(int32_t count, const spmv_mat_t *mats, const double *const *xs,
                       double *const *ys, spmv_batch_t *out);
+/* Times the plan with work items of 64, 128, 256, 512 and 1024 rows (reps
+ * graph launches each, default 10 when <= 0; this writes the plan's ys),
+ * keeps the fastest and re-captures the plan's graph with it; *item_rows
+ * (may be NULL) receives it.  Synchronous. */
+int spmv_batch_autotune(spmv_batch_t plan, int32_t reps, int32_t *item_rows);
 /* Replays the plan's graph on stream (one persistent kernel launch).  Each
  * replay resets and then draws from the plan's one work counter, so two
  * launches of the same plan must not overlap on the GPU. */

@@ -9,7 +9,7 @@ the current stream through the C ABI.
 The functions keep the C names: spmv_build, spmv_build_csr, spmv_compress,
 spmv_set_order, spmv_info, spmv_decompress, spmv_export, spmv_import,
 spmv_apply, spmv_apply_host, spmv_apply_f32, spmm_apply, spmv_batch_create,
-spmv_batch_launch, spmv_batch_free, spmv_apply_batched, cg_solve,
+spmv_batch_launch, spmv_batch_autotune, spmv_batch_free, spmv_apply_batched, cg_solve,
 spmv_device_error, spmv_autotune, spmv_set_variant, spmv_set_tile,
 spmv_set_spmm_kernel, spmv_set_f32_kernel, spmv_permutation, spmm_apply_noalloc, spmv_version.
 """
@@ -93,6 +93,7 @@ def library() -> ctypes.CDLL:
             "spmm_apply": [_p, _i32, _p, _i64, _p, _i64, _p],
             "spmv_batch_create": [_i32, _p, _p, _p, ctypes.POINTER(_p)],
             "spmv_batch_launch": [_p, _p],
+            "spmv_batch_autotune": [_p, _i32, ctypes.POINTER(_i32)],
             "spmv_batch_free": [_p],
             "spmv_apply_batched": [_i32, _p, _p, _p, _p],
             "cg_solve": [_p, _p, _p, ctypes.POINTER(spmv_cg_opts), ctypes.POINTER(spmv_cg_result)],
@@ -307,6 +308,14 @@ def spmv_batch_create(mats, xs, ys) -> SpmvBatch:
 
 def spmv_batch_launch(plan: SpmvBatch, stream=None) -> None:
     _check(library().spmv_batch_launch(plan.handle, _stream(stream)))
+
+
+def spmv_batch_autotune(plan: SpmvBatch, reps: int = 10) -> int:
+    """Times work items of 64..1024 rows (writes the plan's ys), keeps the
+    fastest; returns its rows an item."""
+    r = _i32(0)
+    _check(library().spmv_batch_autotune(plan.handle, reps, ctypes.byref(r)))
+    return r.value
 
 
 def spmv_batch_free(plan: SpmvBatch) -> None:

@@ -465,6 +465,12 @@ struct BatchItem {
 cudaError_t launch_pattern_batch(const PatternView* mats_dev, const double* const* xs_dev,
                                  double* const* ys_dev, const BatchItem* items, int64_t nitems,
                                  uint32_t* counter, int words, int grid, cudaStream_t s);
+// FAST order: zeroes the counter and the count exponent words, runs the
+// exponent pass, then the batch kernel.
+cudaError_t launch_pattern_batch_fast(const PatternView* mats_dev, const double* const* xs_dev,
+                                      double* const* ys_dev, const BatchItem* items, int64_t nitems,
+                                      uint32_t* counter, uint32_t* mat_max, int count, int words, int grid,
+                                      cudaStream_t s);
 
 // Utility kernels.
 cudaError_t launch_fill_u32(uint32_t* p, uint32_t v, int64_t n, cudaStream_t s);

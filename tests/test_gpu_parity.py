@@ -422,6 +422,57 @@ def test_spmm_160_k32_sampled():
         assert np.array_equal(Yh[rows, j], oracle.hpcg_spmv_rows(nx, nx, nx, rows, np.ascontiguousarray(X_np[:, j])))
 
 
+def test_ragged_batch_fast_order_and_item_tuning():
+    """A batch of FAST-order matrices: every row within FAST order's bound
+    of the exact product (x of each matrix at its own scale); a matrix with
+    an all-zero x and one with an infinity take the COLUMN order (bit-exact
+    with the oracle); the item-size tuner keeps results; a batch mixing
+    orders runs in COLUMN order."""
+    edges = [17, 24, 9, 31, 16]
+    mats, xs, ys, ref = [], [], [], []
+    for b, e in enumerate(edges):
+        mats.append(P.spmv_compress(P.spmv_build("hpcg", e, e, e), format="pattern", order="fast"))
+        x_np = spmv_inputs.uniform_vector(e ** 3, seed=200 + b) * 10.0 ** (b - 2)
+        if b == 2:
+            x_np[:] = 0.0
+        if b == 4:
+            x_np[e ** 3 // 2] = np.inf
+        xs.append(torch.from_numpy(x_np).cuda())
+        ys.append(torch.full_like(xs[-1], float("nan")))
+        ref.append(oracle.hpcg_csr(e, e, e) + (x_np,))
+    plan = P.spmv_batch_create(mats, xs, ys)
+
+    def check():
+        for b, (rp, c, v, x_np) in enumerate(ref):
+            got = ys[b].cpu().numpy()
+            want = oracle.spmv(rp, c, v, x_np)
+            if b in (2, 4):
+                assert np.array_equal(got, want, equal_nan=True), b
+            else:
+                check_fast(got, want, abs_row_sums(rp, c, v, x_np))
+
+    P.spmv_batch_launch(plan)
+    torch.cuda.synchronize()
+    check()
+    rows = P.spmv_batch_autotune(plan, reps=3)
+    assert rows in (64, 128, 256, 512, 1024)
+    for y in ys:
+        y.fill_(float("nan"))
+    P.spmv_batch_launch(plan)
+    torch.cuda.synchronize()
+    check()
+    P.spmv_batch_free(plan)
+    for M in mats:
+        assert P.spmv_device_error(M) == 0
+    # one matrix in COLUMN order: the whole batch is the COLUMN order
+    P.spmv_set_order(mats[0], "column")
+    for y in ys:
+        y.fill_(float("nan"))
+    P.spmv_apply_batched(mats, xs, ys)
+    for b, (rp, c, v, x_np) in enumerate(ref):
+        assert np.array_equal(ys[b].cpu().numpy(), oracle.spmv(rp, c, v, x_np), equal_nan=True), b
+
+
 def test_ragged_batch_exact():
     edges = spmv_inputs.grid_edges(24, seed=4)
     mats, xs, ys, refs = [], [], [], []
