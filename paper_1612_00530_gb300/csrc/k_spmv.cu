@@ -1392,14 +1392,25 @@ __global__ void __launch_bounds__(kBlock) pattern_f32_kernel(PatternView a, cons
 }
 
 // ------------------------------------------------------------ delta ------
+// A load of the slice payload: from shared memory (SH, the slice staged
+// there) or streamed from global memory.
+template <bool SH, typename V>
+__device__ __forceinline__ V ldp(const V* p) {
+    if constexpr (SH) return *p;
+    else return __ldcs(p);
+}
+
 // One row of a delta slice.  CM: column encoding (0 int16 delta, 1 24-bit
 // delta, 2 raw int32); VM: value encoding (0 code, 1 code into the global
 // table or, from dict_size up, into the slice's own table, 2 raw double).
-template <typename T, int CM, int VM>
-__device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, uint32_t w, uint32_t flags, int64_t r,
-                                       int l, int len, const T* sdict, const T* __restrict__ x, int64_t ldx, int j) {
+// base: the slice payload (in shared memory when SH), gbase: the same in
+// global memory (the slice's own value table is read from there).
+template <typename T, int CM, int VM, bool SH>
+__device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, const uint8_t* gbase, uint32_t w,
+                                       uint32_t flags, int64_t r, int l, int len, const T* sdict,
+                                       const T* __restrict__ x, int64_t ldx, int j) {
     const DeltaParts pt = delta_parts(w, flags);
-    const double* local = reinterpret_cast<const double*>(base + pt.local) + 2;   // after its 16-byte count
+    const double* local = reinterpret_cast<const double*>(gbase + pt.local) + 2;   // after its 16-byte count
     T acc = T(0);
     // the slice's full width, the same for every lane of the warp, so the
     // loop unrolls and independent loads overlap; a lane's slots past its
@@ -1410,20 +1421,20 @@ __device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, 
         const int64_t slot = int64_t(t) * 32 + l;
         int64_t c;
         if constexpr (CM == 2) {
-            c = __ldcs(reinterpret_cast<const int32_t*>(base + pt.cols) + slot);
+            c = ldp<SH>(reinterpret_cast<const int32_t*>(base + pt.cols) + slot);
         } else {
-            const int16_t lo = __ldcs(reinterpret_cast<const int16_t*>(base + pt.cols) + slot);
+            const int16_t lo = ldp<SH>(reinterpret_cast<const int16_t*>(base + pt.cols) + slot);
             if constexpr (CM == 1)
-                c = r + int64_t(int8_t(__ldcs(base + pt.hi + slot))) * 65536 + int64_t(uint16_t(lo));
+                c = r + int64_t(int8_t(ldp<SH>(base + pt.hi + slot))) * 65536 + int64_t(uint16_t(lo));
             else
                 c = r + lo;
         }
         bool ok = on;
         T v = T(0);
         if constexpr (VM == 2) {
-            v = T(__ldcs(reinterpret_cast<const double*>(base + pt.vals) + slot));
+            v = T(ldp<SH>(reinterpret_cast<const double*>(base + pt.vals) + slot));
         } else {
-            const uint32_t code = __ldcs(base + pt.vals + slot);
+            const uint32_t code = ldp<SH>(base + pt.vals + slot);
             if (code < uint32_t(a.dict_size)) {
                 v = sdict[code];
             } else if (VM == 1) {
@@ -1443,14 +1454,15 @@ __device__ __forceinline__ T delta_row(const DeltaView& a, const uint8_t* base, 
     return acc;
 }
 
-template <typename T>
-__device__ __forceinline__ T delta_row_any(const DeltaView& a, const uint8_t* base, const DeltaSlice& h, int64_t r,
-                                           int l, int len, const T* sdict, const T* __restrict__ x, int64_t ldx,
-                                           int j) {
+template <typename T, bool SH = false>
+__device__ __forceinline__ T delta_row_any(const DeltaView& a, const uint8_t* base, const uint8_t* gbase,
+                                           const DeltaSlice& h, int64_t r, int l, int len, const T* sdict,
+                                           const T* __restrict__ x, int64_t ldx, int j) {
     const int cm = (h.flags & kSliceColRaw) ? 2 : (h.flags & kSliceCol24) ? 1 : 0;
     const int vm = (h.flags & kSliceValRaw) ? 2 : (h.flags & kSliceValLocal) ? 1 : 0;
 #define SPMVC_DELTA_ROW(C_, V_) \
-    if (cm == C_ && vm == V_) return delta_row<T, C_, V_>(a, base, h.w, h.flags, r, l, len, sdict, x, ldx, j);
+    if (cm == C_ && vm == V_)   \
+        return delta_row<T, C_, V_, SH>(a, base, gbase, h.w, h.flags, r, l, len, sdict, x, ldx, j);
     SPMVC_DELTA_ROW(0, 0) SPMVC_DELTA_ROW(0, 1) SPMVC_DELTA_ROW(0, 2)
     SPMVC_DELTA_ROW(1, 0) SPMVC_DELTA_ROW(1, 1) SPMVC_DELTA_ROW(1, 2)
     SPMVC_DELTA_ROW(2, 0) SPMVC_DELTA_ROW(2, 1) SPMVC_DELTA_ROW(2, 2)
@@ -1459,10 +1471,16 @@ __device__ __forceinline__ T delta_row_any(const DeltaView& a, const uint8_t* ba
 }
 
 // y[r] = row r, or y[scatter[r]] = row r for a reordered handle (the
-// scatter of P^T folded into the product)
+// scatter of P^T folded into the product).  A warp first copies its slice's
+// row lengths, columns and codes (everything before the slice's own value
+// table, when at most kDeltaStage bytes) into its part of shared memory with
+// 16-byte loads, so that the slot loop's only global loads are the x
+// gathers (and the rare slice-local values).
+constexpr int kDeltaStage = 5632;   // bytes a warp: 8 warps plus the value table stay under 48 KB
 template <typename T>
 __global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __restrict__ x, T* __restrict__ y,
                                                      const int32_t* __restrict__ scatter) {
+    __shared__ uint4 sstage[kBlock / 32][kDeltaStage / 16];
     __shared__ T sdict[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
         T v = T(0);
@@ -1479,9 +1497,22 @@ __global__ void __launch_bounds__(kBlock) delta_kernel(DeltaView a, const T* __r
     const DeltaSlice h = a.hdr[s];
     const uint8_t* base = a.payload + h.off;
     const int64_t r = s * 32 + l;
-    int len = r < a.n ? int(base[l]) : 0;
-    if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
-    const T acc = delta_row_any<T>(a, base, h, r, l, len, sdict, x, 1, 0);
+    const uint64_t sb = delta_parts(h.w, h.flags).local;   // a multiple of 16: every part is 16-byte aligned
+    T acc;
+    if (sb <= uint64_t(kDeltaStage)) {
+        uint4* st = sstage[threadIdx.x >> 5];
+        const uint4* src = reinterpret_cast<const uint4*>(base);
+        for (int i = l; i < int(sb >> 4); i += 32) st[i] = __ldcs(src + i);
+        __syncwarp();
+        const uint8_t* sbase = reinterpret_cast<const uint8_t*>(st);
+        int len = r < a.n ? int(sbase[l]) : 0;
+        if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
+        acc = delta_row_any<T, true>(a, sbase, base, h, r, l, len, sdict, x, 1, 0);
+    } else {
+        int len = r < a.n ? int(base[l]) : 0;
+        if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
+        acc = delta_row_any<T, false>(a, base, base, h, r, l, len, sdict, x, 1, 0);
+    }
     if (r < a.n) y[scatter ? int64_t(__ldg(scatter + r)) : r] = acc;
 }
 
@@ -1621,7 +1652,7 @@ __global__ void __launch_bounds__(kBlock) delta_spmm_kernel(DeltaView a, int k, 
     const uint8_t* base = a.payload + h.off;
     int len = base[l];
     if (uint32_t(len) > h.w) { raise_error(a.err, 4); len = 0; }
-    Y[r * ldy + j] = delta_row_any<double>(a, base, h, r, l, len, sdict, X, ldx, j);
+    Y[r * ldy + j] = delta_row_any<double>(a, base, base, h, r, l, len, sdict, X, ldx, j);
 }
 
 __global__ void fill_u32_kernel(uint32_t* p, uint32_t v, int64_t n) {
