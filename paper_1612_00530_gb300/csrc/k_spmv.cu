@@ -1664,7 +1664,7 @@ unsigned grid_of(int64_t threads) { return unsigned((threads + kBlock - 1) / kBl
 
 // Opens a kernel's dynamic shared memory to the device's per-block limit and
 // prefers the largest shared-memory carveout, once per kernel and device:
-// the two driver calls cost more than a launch, and a pipelined product
+// the two attribute calls cost more than a launch, and a pipelined product
 // launches a kernel many times.
 cudaError_t prepare_kernel(const void* kernel) {
     int dev = 0;
