@@ -48,6 +48,9 @@ def test_invalid_arguments_rejected_before_device_work():
     lib = P.library()
     assert lib.spmv_apply(None, None, None, None) == P.SPMV_EINVAL
     assert lib.spmv_build(None, None) == P.SPMV_EINVAL
+    assert lib.spmv_batch_autotune(None, 1, None) == P.SPMV_EINVAL
+    assert lib.spmv_batch_launch(None, None) == P.SPMV_EINVAL
+    assert lib.spmv_batch_create(0, None, None, None, None) == P.SPMV_EINVAL
     # columns out of order
     with pytest.raises(P.SpmvError) as e:
         P.spmv_build_csr(np.array([0, 2]), np.array([0, 0]), np.array([1.0, 2.0]))
