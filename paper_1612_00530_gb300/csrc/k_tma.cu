@@ -207,8 +207,12 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY * MINB) + 32, MINB)
             const int iy = b * tp.L + ckl[k];
             cxy[k] = ckx[k] | ((iy > 0 ? 1 : 0) | (iy < tp.ny - 1 ? 2 : 0)) << 2;
         }
-        int cz_cached = -1;
-        uint32_t ex[K][7];
+        // the record of an interior row (class 63: every neighbour in the
+        // grid), kept in registers; a warp with a boundary row reads its
+        // rows' expected records from shared memory instead
+        uint32_t exi[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) exi[i] = sexp[63 * 8 + i];
         uint32_t E_true = E_given;       // largest biased exponent seen in this run of planes
         uint32_t E_ring = max(E_given, 64u);   // scale of the converted windows: max(E_true, 64)
 
@@ -284,13 +288,6 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY * MINB) + 32, MINB)
                 const uint32_t st = nrec % kRecStages;
                 if (!mbar_wait(rec_full + st, (nrec / kRecStages) & 1u)) wait_ok = false;
                 const int cz = (p > 0 ? 1 : 0) | (p < tp.nz - 1 ? 2 : 0);
-                if (cz != cz_cached) {
-#pragma unroll
-                    for (int k = 0; k < K; ++k)
-#pragma unroll
-                        for (int i = 0; i < 7; ++i) ex[k][i] = sexp[(cxy[k] | (cz << 4)) * 8 + i];
-                    cz_cached = cz;
-                }
                 const unsigned char* rs = rec + st * 28u * uint32_t(C);
                 uint32_t nbad = 0;
 #pragma unroll
@@ -299,8 +296,17 @@ __global__ void __launch_bounds__(kMaxBlockRows / (4 * TY * MINB) + 32, MINB)
                     const uint4 v16 = *reinterpret_cast<const uint4*>(rs + 16 * rho);
                     const uint2 v8 = *reinterpret_cast<const uint2*>(rs + 16 * C + 8 * rho);
                     const uint32_t v4 = *reinterpret_cast<const uint32_t*>(rs + 24 * C + 4 * rho);
-                    const uint32_t diff = (v16.x ^ ex[k][0]) | (v16.y ^ ex[k][1]) | (v16.z ^ ex[k][2]) |
-                                          (v16.w ^ ex[k][3]) | (v8.x ^ ex[k][4]) | (v8.y ^ ex[k][5]) | (v4 ^ ex[k][6]);
+                    const int cls = cxy[k] | (cz << 4);
+                    uint32_t ex[7];
+                    if (__any_sync(0xFFFFFFFFu, cls != 63)) {
+#pragma unroll
+                        for (int i = 0; i < 7; ++i) ex[i] = sexp[cls * 8 + i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 7; ++i) ex[i] = exi[i];
+                    }
+                    const uint32_t diff = (v16.x ^ ex[0]) | (v16.y ^ ex[1]) | (v16.z ^ ex[2]) | (v16.w ^ ex[3]) |
+                                          (v8.x ^ ex[4]) | (v8.y ^ ex[5]) | (v4 ^ ex[6]);
                     const uint32_t match = __ballot_sync(0xFFFFFFFFu, diff == 0u);
                     if (lane == 0) sflags[(it % 3) * fw + (tid >> 5) + k * (NC >> 5)] = match;
                     nbad += 32u - __popc(match);
